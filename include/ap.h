@@ -1,0 +1,276 @@
+/*
+ * ap.h -- C ABI of the GB300 analytic-pulse gather + relativistic Boris push.
+ *
+ * Method: Weichman et al., "Analytic pulse technique for computational
+ * electromagnetics" (arXiv:2307.04843).  The fields are split into an
+ * analytic vacuum part E1/B1 and a grid part E2/B2 (Sec. 2, Eqs. E_1, E_2);
+ * here each macroparticle evaluates E1/B1 in closed form at its own position
+ * and time, adds the trilinearly gathered grid field (Sec. 2.1, Fig. 1: "the
+ * total fields are then interpolated to the particle position"), and takes a
+ * relativistic Boris step.
+ *
+ * Units are normalised: c = omega0 = k0 = 1 (lambda = 2 pi), fields in
+ * m c omega0 / e so that the field amplitude is a0 (Sec. 2.2, definition of
+ * a0 under Fig. 3).  The particles are electrons, charge -1 and mass 1:
+ *     du/dt = -(E + u x B / gamma),  dx/dt = u / gamma,  u = gamma beta.
+ * The laser propagates along +z (the paper uses x):
+ *     E_perp = Re[ Gamma(eta) u(x,y,z) p e^{i psi} ],
+ *     psi    = omega (t - t_focus) - k (z - z_focus) + phase0,  k = omega / v_phi,
+ *     eta    = (t - t_focus) - (z - z_focus) / v_g,
+ *     B_perp = (B0/E0) z_hat x E_perp                      (Eqs. plane_func, plane_b).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: AP_OK (0) or a negative AP_ERR_*.
+ *     The library never aborts, never prints and never traps the GPU.
+ *   - All device memory passed in is owned and allocated by the caller; the
+ *     library allocates only its handle and the handle's small parameter
+ *     buffers (in ap_init_pulse), never on the push path.
+ *   - Calls that take a stream are asynchronous and stream-ordered.  Errors
+ *     found on the device (non-finite state, exhausted bounded wait) are
+ *     recorded in the handle's device status word and reported by
+ *     ap_sync_status.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Particle state semantics (leapfrog): on entry x is at t0 and u at
+ *     t0 - dt/2; after n_steps steps x is at t0 + n_steps dt and u at
+ *     t0 + (n_steps - 1/2) dt.  The given u is taken as u^{-1/2} (no
+ *     half-step back push).  Fields are sampled at t_n = t0 + n dt (computed,
+ *     not accumulated) at the integer-step position x^n.
+ */
+#ifndef AP_H
+#define AP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AP_ABI_VERSION 1
+
+/* ------------------------------------------------------------ status codes */
+#define AP_OK 0
+#define AP_ERR_ARG -1        /* invalid argument (NULL pointer, bad size, bad enum) */
+#define AP_ERR_ALIGN -2      /* a device pointer is not 16-byte aligned */
+#define AP_ERR_CUDA -3       /* a CUDA runtime call failed */
+#define AP_ERR_NONFINITE -4  /* a particle state or field became NaN/Inf */
+#define AP_ERR_TIMEOUT -5    /* a bounded device-side wait gave up */
+#define AP_ERR_WORKSPACE -6  /* caller workspace too small */
+#define AP_ERR_UNSUPPORTED -7 /* combination not built (e.g. Yee dispersion with a flying focus) */
+
+/* ------------------------------------------------------------------ enums */
+/* pulse kinds */
+#define AP_PLANE 0        /* plane wave with envelope, Eqs. plane_func / plane_b (Sec. 2.1) */
+#define AP_GAUSS 1        /* paraxial Gaussian beam, Eq. paraxial with D = 3 (Sec. 3.1) */
+#define AP_LG 2           /* Laguerre-Gaussian LG_pl, named in Sec. 3.1 (textbook form) */
+#define AP_FLYING_SUM 3   /* flying focus as a linear superposition of Gaussian spectral
+                             components (Sec. 3.3) */
+/* polarisation vector p */
+#define AP_LIN_X 0        /* p = (1, 0) */
+#define AP_LIN_Y 1        /* p = (0, 1) */
+#define AP_CIRC_P 2       /* p = (1, -i): |E_perp| = a0 |u| Gamma, rotating */
+#define AP_CIRC_M 3       /* p = (1, +i) */
+/* temporal envelopes Gamma(eta) */
+#define AP_ENV_SIN2 0     /* cos^2(pi eta / T) for |eta| <= T/2, T = 2 pi N / omega, N = env_len cycles */
+#define AP_ENV_GAUSS 1    /* exp(-2 ln2 eta^2 / T^2), T = env_len = intensity FWHM */
+#define AP_ENV_SGAUSS 2   /* exp(-(eta / tau)^(2 g)), tau = env_len, g = sg_order (Sec. 2.3) */
+#define AP_ENV_CW 3       /* 1 */
+/* flags */
+#define AP_F_LONGITUDINAL 1u /* add E_z, B_z from div E = 0, div B = 0 (Sec. 3.1) */
+#define AP_F_YEE_DISP 2u     /* second-order Yee v_phi, v_g, B0/E0 (Eqs. vphi, vg, e_amp) */
+/* arithmetic of the push */
+#define AP_FP64 0            /* everything in double; u arrays are double */
+#define AP_FP32_PHASE64 1    /* fields and Boris in float; phase argument and position
+                                accumulation in native double; u arrays are float */
+#define AP_FP32_PHASEFF 2    /* as AP_FP32_PHASE64 but the phase argument and the position
+                                are carried as float-float pairs (about 48-bit significand,
+                                Dekker 1971 / Knuth TwoSum), so no FP64 instruction runs in
+                                the step loop; u arrays are float, x arrays stay double */
+/* adjoint objectives */
+#define AP_OBJ_MEAN_GAMMA 0  /* J_s = (1/N_s) sum_{i in set s} gamma_i(T) */
+/* differentiable parameters, in the order of dJ_dparams rows */
+#define AP_NPARAM 4          /* d/d(a0, w0, z_focus, beta_f); beta_f is 0 except for flying focus */
+
+/* -------------------------------------------------------------- structures */
+
+/* Physical description of one pulse (one "pulse-parameter set").  The paper's
+ * run-time parameters (Sec. 2.3: E0, omega, super-Gaussian order g, duration
+ * tau, envelope delay, initial phase at a reference position) plus the beam
+ * and flying-focus parameters of Secs. 3.1 and 3.3.  Host memory. */
+typedef struct {
+  int32_t kind;       /* AP_PLANE | AP_GAUSS | AP_LG | AP_FLYING_SUM */
+  int32_t pol;        /* AP_LIN_X | AP_LIN_Y | AP_CIRC_P | AP_CIRC_M */
+  int32_t env;        /* AP_ENV_*; ignored (CW) for AP_FLYING_SUM */
+  int32_t sg_order;   /* super-Gaussian order g >= 1 */
+  int32_t lg_p, lg_l; /* LG radial and azimuthal indices, 0 <= p <= 8, |l| <= 8 */
+  int32_t n_comp;     /* flying focus: number of spectral components, 2..AP_MAX_COMP */
+  uint32_t flags;     /* AP_F_* */
+  double a0;          /* peak field amplitude: focal-plane peak of |u| for beams; for the
+                         flying focus the peak on-axis envelope at mid-range (see kind) */
+  double omega;       /* carrier frequency (1 = omega0) */
+  double w0;          /* beam waist */
+  double z_focus;     /* focal plane; flying focus: start z_a of the focal range */
+  double t_focus;     /* time at which the envelope peak crosses z_focus; flying focus:
+                         time t_a at which the focus is at z_a */
+  double env_len;     /* see AP_ENV_* */
+  double phase0;      /* carrier phase at (t_focus, z_focus) */
+  double beta_f;      /* flying focus: focal velocity v_f / c (nonzero) */
+  double bw_frac;     /* flying focus: frequencies span omega (1 +- bw_frac) */
+  double ff_length;   /* flying focus: length L of the focal range */
+  double yee_dx, yee_dt; /* AP_F_YEE_DISP: cell size and time step of the Yee solver */
+} ap_pulse_desc;
+
+#define AP_MAX_COMP 128
+#define AP_MAX_SETS 4096
+
+/* Particle arrays (structure of arrays), device memory, caller-owned.
+ * x, y, z: double in every precision.  ux, uy, uz: double for AP_FP64, float
+ * otherwise.  Every pointer must be 16-byte aligned (AP_ERR_ALIGN otherwise).
+ * The arrays are updated in place. */
+typedef struct {
+  double *x, *y, *z;
+  void *ux, *uy, *uz;
+  int64_t n;
+  /* batched calls only: set s owns particles [set_offsets[s], set_offsets[s+1]);
+   * device memory, n_sets + 1 non-decreasing entries, set_offsets[0] = 0,
+   * set_offsets[n_sets] = n. */
+  const int64_t *set_offsets;
+  int32_t n_sets;
+} ap_particles;
+
+/* Static node-centred grid field E2/B2 (Eqs. E_2, Sec. 2.1), device memory,
+ * caller-owned.  Six float arrays f[0..5] = Ex, Ey, Ez, Bx, By, Bz, each
+ * [nz][ny][nx] with x fastest; nodes at lo + i (hi - lo)/(n - 1).  Positions
+ * outside [lo, hi] are clamped to the box.  n >= 2 along every axis. */
+typedef struct {
+  const float *f[6];
+  int32_t nx, ny, nz;
+  double lo[3], hi[3];
+} ap_grid;
+
+/* Optional diagnostics, device memory, caller-owned; every pointer nullable.
+ * Unless `accumulate` is nonzero the call zeroes the buffers it writes first. */
+typedef struct {
+  double *lightfront_max; /* [n_steps]: max over particles of |(gamma - u_z) - h0| after
+                             each step, h0 = gamma - u_z on entry (plane-wave invariant) */
+  uint32_t *gamma_hist;   /* [hist_bins]: final gamma, computed in double from the stored
+                             u; bin = floor((gamma - lo) * (bins / (hi - lo))) clamped to
+                             [0, bins - 1]; non-finite gamma not counted */
+  int32_t hist_bins;
+  double hist_lo, hist_hi;
+  double *set_gamma_sum;  /* [n_sets] (batched) or [1]: sum of final gamma per set */
+  int32_t accumulate;
+} ap_diag;
+
+/* Launch shape, chosen by the autotuner (0 = library default). */
+typedef struct {
+  int32_t block;          /* threads per block, multiple of 32, <= 1024 */
+  int32_t blocks_per_sm;  /* persistent kernels: resident blocks per SM */
+  int32_t ppt;            /* particles per thread (1 or 2) */
+} ap_launch_cfg;
+
+typedef struct ap_handle_s *ap_handle;
+typedef struct ap_graph_s *ap_graph;
+
+/* ------------------------------------------------------------- entry points */
+
+/* ABI version (AP_ABI_VERSION). */
+int ap_version(void);
+
+/* Human-readable text of a status code; static storage, never NULL. */
+const char *ap_status_string(int status);
+
+/* Pulse setup (host, once; row a1 of the hot path).  Validates `descs`
+ * (host array of n_sets descriptions, 1 <= n_sets <= AP_MAX_SETS) and derives
+ * every constant in FP64: Rayleigh range k w0^2/2, LG normalisation, the
+ * flying-focus component table, and optionally the Yee v_phi, v_g, B0/E0 of
+ * Eqs. vphi, vg, e_amp.  Allocates the handle and a device copy of the
+ * derived parameters on the current device.  *out receives the handle (NULL
+ * on error).  Errors: AP_ERR_ARG (bad description), AP_ERR_UNSUPPORTED,
+ * AP_ERR_CUDA. */
+int ap_init_pulse(const ap_pulse_desc *descs, int32_t n_sets, ap_handle *out);
+
+/* Releases the handle and its device buffers (synchronises the device). */
+void ap_destroy(ap_handle h);
+
+/* Sets the launch shape used by later calls on this handle (NULL restores
+ * the defaults).  Errors: AP_ERR_ARG for an invalid shape. */
+int ap_set_launch(ap_handle h, const ap_launch_cfg *cfg);
+
+/* Evaluates the analytic E1/B1 of set `set` at n points (test and
+ * inspection hook; Eqs. plane_func, plane_b, paraxial and the divergence
+ * conditions of Sec. 3.1).  xyzt: device double [4][n] (x, y, z, t rows).
+ * EB_out: device double [6][n] (Ex, Ey, Ez, Bx, By, Bz rows).  precision:
+ * AP_FP64 evaluates in double; AP_FP32_* in the float arithmetic of the push
+ * with the given phase arithmetic.  Errors: AP_ERR_ARG, AP_ERR_CUDA. */
+int ap_eval_fields(ap_handle h, int32_t set, const double *xyzt, int64_t n, double *EB_out,
+                   int32_t precision, void *stream);
+
+/* Gather + push (rows a2-a11): advances every particle n_steps steps under
+ * the analytic field of set 0 plus the gathered grid field `g` (nullable),
+ * all steps fused in one launch with the particle held in registers.
+ * p: see ap_particles (set_offsets ignored).  diag: nullable.
+ * Errors: AP_ERR_ARG, AP_ERR_ALIGN, AP_ERR_CUDA (launch). */
+int ap_gather_push(ap_handle h, const ap_particles *p, const ap_grid *g, double t0, double dt,
+                   int64_t n_steps, int32_t precision, const ap_diag *diag, void *stream);
+
+/* Scratch needed by ap_gather_push_batched (bytes; the tile-queue counter). */
+size_t ap_batch_workspace_bytes(ap_handle h);
+
+/* Batched persistent gather + push (row a12): set s of the handle drives
+ * particles [set_offsets[s], set_offsets[s+1]).  One persistent launch of
+ * (SM count x blocks_per_sm) blocks pops fixed-size particle tiles from a
+ * global atomic counter kept in `workspace` (device, >= ap_batch_workspace_bytes,
+ * 16-byte aligned, zeroed by the call on `stream`); the loop is bounded by the
+ * tile count, no block waits on another.  p->n_sets must equal the handle's
+ * set count.  diag->set_gamma_sum receives per-set sums of final gamma.
+ * Calls sharing one workspace must not overlap on the GPU.
+ * Errors: AP_ERR_ARG, AP_ERR_ALIGN, AP_ERR_WORKSPACE, AP_ERR_CUDA. */
+int ap_gather_push_batched(ap_handle h, const ap_particles *p, const ap_grid *g, double t0,
+                           double dt, int64_t n_steps, int32_t precision, const ap_diag *diag,
+                           void *workspace, size_t ws_bytes, void *stream);
+
+/* Captures ap_gather_push_batched (its memsets and the persistent launch)
+ * into a CUDA graph on `stream` (which must not be the legacy default
+ * stream); every pointer is baked into the graph and must stay valid.
+ * ap_graph_launch replays it on a stream.  Errors: as the batched call. */
+int ap_batch_graph_create(ap_handle h, const ap_particles *p, const ap_grid *g, double t0,
+                          double dt, int64_t n_steps, int32_t precision, const ap_diag *diag,
+                          void *workspace, size_t ws_bytes, void *stream, ap_graph *out);
+int ap_graph_launch(ap_graph gr, void *stream);
+void ap_graph_destroy(ap_graph gr);
+
+/* Workspace for ap_push_adjoint: one checkpoint of the state (36 B per
+ * particle) every ckpt_every steps plus the per-particle tape of the
+ * recomputed segment.  Returns 0 for invalid arguments. */
+size_t ap_adjoint_workspace_bytes(ap_handle h, int64_t n, int64_t n_steps, int32_t ckpt_every);
+
+/* Discrete adjoint of the gather + push (row a13): gradient of the per-set
+ * objective J_s = (1/N_s) sum_i gamma_i(T) (AP_OBJ_MEAN_GAMMA) with respect to
+ * the pulse parameters (a0, w0, z_focus, beta_f) of every set.  p0 holds the
+ * initial state (unchanged by the call).  Runs the forward push storing
+ * checkpoints every ckpt_every steps in `workspace`, then sweeps the segments
+ * backwards, recomputing each from its checkpoint and back-propagating
+ * through the Boris step and the analytic fields.  Per-set gradients are
+ * reduced warp -> block -> FP64 atomics into dJ_dparams (device double
+ * [n_sets][AP_NPARAM]) and J into J_out (device double [n_sets], nullable).
+ * The call zeroes both.  The grid, if given, enters the forward trajectory
+ * and the position adjoint.  precision: AP_FP32_PHASEFF or AP_FP64.
+ * Errors: AP_ERR_ARG, AP_ERR_ALIGN, AP_ERR_WORKSPACE, AP_ERR_CUDA. */
+int ap_push_adjoint(ap_handle h, const ap_particles *p0, const ap_grid *g, double t0, double dt,
+                    int64_t n_steps, int32_t ckpt_every, int32_t objective, int32_t precision,
+                    double *dJ_dparams, double *J_out, void *workspace, size_t ws_bytes,
+                    void *stream);
+
+/* Waits for `stream`, then returns and clears the handle's device status
+ * word: AP_OK, AP_ERR_NONFINITE or AP_ERR_TIMEOUT; AP_ERR_CUDA if the wait
+ * itself failed. */
+int ap_sync_status(ap_handle h, void *stream);
+
+/* Number of sets in the handle, or AP_ERR_ARG. */
+int ap_num_sets(ap_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,30 @@
+"""Plain FP64 CPU oracle for the analytic-pulse push (arXiv:2307.04843).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it; the product package never imports it.
+The C core (``oracle.c``) is built with plain gcc, no fast-math, no FMA
+contraction (``build()``), and wrapped with ctypes here.  Pulses are plain
+dicts of physical parameters (the same dicts the product binding takes); this
+module maps them onto the oracle's own structure.
+
+Functions: ``fields``, ``push``, ``boris``, ``grid_sample``, ``gamma_hist``,
+``set_gamma_sums``, ``profile``, ``envelope``, ``state`` and
+``grad_fd`` (FP64 central finite differences with Richardson extrapolation of
+the per-set mean final gamma).
+"""
+from .core import (  # noqa: F401
+    build,
+    lib,
+    prepare,
+    state,
+    fields,
+    profile,
+    envelope,
+    grid_sample,
+    boris,
+    push,
+    gamma_hist,
+    set_gamma_sums,
+    mean_gamma,
+    grad_fd,
+)

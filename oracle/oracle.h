@@ -1,0 +1,134 @@
+/*
+ * oracle.h -- plain, slow FP64 CPU oracle for the analytic-pulse field
+ * evaluation + relativistic Boris push (Weichman et al., "Analytic pulse
+ * technique for computational electromagnetics", arXiv:2307.04843).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes
+ * or calls this code.  Only the tests, the package's smoke check and the
+ * CPU-baseline leg of the benchmark use it.  It shares no header, helper,
+ * table or constant generator with the CUDA path: every derived constant
+ * (Rayleigh range, Laguerre-Gaussian normalisation, flying-focus component
+ * table, numerical-dispersion factors) is recomputed here from the physical
+ * pulse description.
+ *
+ * Conventions (normalised units, c = omega0 = k0 = 1, lambda = 2 pi; fields in
+ * m c omega0 / e so that the field amplitude is a0, Sec. 3.1 below Fig. 3):
+ *   - propagation along +z (the paper propagates along x, Sec. 2.1);
+ *   - E_perp = Re[ Gamma(eta) u(x,y,z) p e^{i psi} ],
+ *     psi = omega (t - t_f) - k (z - z_f) + phase0  (Eq. plane_func),
+ *     eta = (t - t_f) - (z - z_f) / v_g            (envelope argument);
+ *   - B_perp = (B0/E0) z_hat x E_perp              (Eq. plane_b);
+ *   - electron: q = -1, m = 1, du/dt = -(E + u x B / gamma), dx/dt = u/gamma.
+ *
+ * Formulas are written in the textbook (w, R, atan Gouy) form with explicit
+ * Laguerre sums; the longitudinal components come from 4th-order central
+ * finite differences of the complex transverse profile (Sec. 3.1, the
+ * divergence conditions below Eq. paraxial).
+ *
+ * Parity pins: none of the functions here is unpinned; the pinning tests are
+ * tests/test_oracle_*.py.
+ */
+#ifndef APT_ORACLE_H
+#define APT_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* pulse kinds */
+#define OR_PLANE 0   /* plane wave with envelope, Eq. plane_func / plane_b */
+#define OR_GAUSS 1   /* paraxial Gaussian (LG_00), Eq. paraxial, D = 3 */
+#define OR_LG 2      /* Laguerre-Gaussian LG_pl (named in Sec. 3.1, textbook form) */
+#define OR_FLYING 3  /* flying focus as a sum of Gaussian spectral components (Sec. 3.3) */
+
+/* polarisations: p = (1,0), (0,1), (1,-i), (1,+i) */
+#define OR_LIN_X 0
+#define OR_LIN_Y 1
+#define OR_CIRC_P 2
+#define OR_CIRC_M 3
+
+/* temporal envelopes Gamma(eta) */
+#define OR_ENV_SIN2 0    /* cos^2(pi eta / T), |eta| <= T/2, T = 2 pi N / omega */
+#define OR_ENV_GAUSS 1   /* exp(-2 ln2 eta^2 / T^2), T = intensity FWHM */
+#define OR_ENV_SGAUSS 2  /* exp(-(eta/tau)^(2g)), Sec. 2.3 run-time parameters */
+#define OR_ENV_CW 3      /* 1 */
+
+#define OR_MAX_COMP 256
+
+typedef struct {
+  int kind, pol, env, sg_order;
+  int lg_p, lg_l;
+  int n_comp;        /* flying focus: number of spectral components */
+  int longitudinal;  /* nonzero: add E_z, B_z from the divergence conditions */
+  int yee;           /* nonzero: second-order Yee v_phi, v_g, B0/E0 (Eqs. vphi, vg, e_amp) */
+  double a0, omega, w0;
+  double z_focus, t_focus;  /* focus position; time at which the envelope peak is there.
+                               flying focus: start z_a of the focal range and its time t_a */
+  double env_len;           /* SIN2: cycles N; GAUSS: intensity FWHM; SGAUSS: tau */
+  double phase0;
+  double beta_f;            /* flying focus: focal velocity v_f / c */
+  double bw_frac;           /* flying focus: half-width of the frequency spread / omega */
+  double ff_length;         /* flying focus: length L of the focal range */
+  double yee_dx, yee_dt;    /* cell size and time step entering Eqs. vphi, vg, e_amp */
+} or_pulse;
+
+typedef struct {
+  or_pulse p;
+  double k, vphi, vg, bratio;  /* wavenumber, phase/group velocity, B0/E0 */
+  double zR;                   /* Rayleigh range k w0^2 / 2 */
+  double amp;                  /* amplitude coefficient of the transverse profile */
+  int n;                       /* flying focus: component count */
+  double fw[OR_MAX_COMP], fk[OR_MAX_COMP], fz[OR_MAX_COMP], ft[OR_MAX_COMP];
+  double fphi[OR_MAX_COMP], fzR[OR_MAX_COMP];
+  double z_mid, t_mid;         /* flying focus: middle of the focal range and its time */
+} or_state;
+
+/* Derive all constants from the physical description.  Returns 0, or -1 for
+ * an invalid description. */
+int or_prepare(const or_pulse *p, or_state *s);
+
+/* Envelope Gamma(eta). */
+double or_envelope(const or_state *s, double eta);
+
+/* Complex transverse profile u of one beam (component j for the flying focus,
+ * ignored otherwise) at (x, y, z), returned as re/im. */
+void or_profile(const or_state *s, int j, double x, double y, double z, double *re, double *im);
+
+/* Analytic E1, B1 at (x, y, z, t): EB = {Ex, Ey, Ez, Bx, By, Bz}. */
+void or_fields(const or_state *s, double x, double y, double z, double t, double EB[6]);
+
+/* Trilinear gather of a static node-centred grid, layout [6][nz][ny][nx]
+ * (x fastest), nodes at lo + i (hi - lo)/(n - 1); positions outside the box
+ * are clamped to it. */
+void or_grid_sample(const float *grid, int nx, int ny, int nz, const double lo[3],
+                    const double hi[3], double x, double y, double z, double out[6]);
+
+/* One relativistic Boris step of an electron (q = -1, m = 1) in E, B:
+ * u is u^{n-1/2} on entry and u^{n+1/2} on exit. */
+void or_boris(double u[3], const double E[3], const double B[3], double dt);
+
+/* Push n particles for n_steps steps.  On entry x is at t0 and u at
+ * t0 - dt/2; on exit x is at t0 + n_steps dt and u at t0 + (n_steps - 1/2) dt.
+ * grid may be NULL.  lf_max (nullable, length n_steps) receives per step the
+ * maximum over particles of |(gamma - u_z) - h0|, h0 = gamma - u_z on entry
+ * (it is max-accumulated, the caller initialises it).  Returns 0. */
+int or_push(const or_state *s, const float *grid, int nx, int ny, int nz, const double *glo,
+            const double *ghi, int64_t n, double *x, double *y, double *z, double *ux,
+            double *uy, double *uz, double t0, double dt, int64_t n_steps, double *lf_max);
+
+/* Histogram of gamma = sqrt(((ux ux + uy uy) + uz uz) + 1) into nbins bins of
+ * [lo, hi): bin = floor((gamma - lo) * (nbins / (hi - lo))), clamped to
+ * [0, nbins - 1]; non-finite gamma is not counted.  Accumulates into counts. */
+void or_gamma_hist(int64_t n, const double *ux, const double *uy, const double *uz, int nbins,
+                   double lo, double hi, uint32_t *counts);
+
+/* Sum of gamma over each set s of particles [off[s], off[s+1]). */
+void or_set_gamma_sums(int n_sets, const int64_t *off, const double *ux, const double *uy,
+                       const double *uz, double *sums);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,436 @@
+"""Pins of the FP64 CPU oracle against what the physics and mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, an invariant, a convergence order, a library routine or a value the
+paper prints.  A plausible slip anywhere in the oracle (a dropped term, a
+wrong sign of the Gouy phase or curvature, a transposed cross product, a
+wrong envelope width) fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+L = 2.0 * math.pi
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _one(x=0.0, y=0.0, z=0.0, ux=0.0, uy=0.0, uz=0.0):
+    return {k: np.array([v], dtype=np.float64) for k, v in
+            dict(x=x, y=y, z=z, ux=ux, uy=uy, uz=uz).items()}
+
+
+# --------------------------------------------------------------- Boris push
+
+def test_boris_gyration_closed_form():
+    """Uniform B = B0 z_hat, E = 0 (a0 = 0 pulse plus a constant grid): the
+    Boris map is an exact rotation.  |u| is conserved, u_perp turns by
+    theta = 2 atan(dt B0 / (2 gamma)) per step, counter-clockwise for an
+    electron, and the positions lie on a circle of radius
+    rho = dt |u_perp| / (2 gamma sin(theta/2))."""
+    B0, dt, n_steps = 0.75, 0.05, 10_000  # B0 exactly representable in the float32 grid
+    grid = np.zeros((6, 2, 2, 2), dtype=np.float32)
+    grid[5] = B0
+    lo, hi = (-1e9, -1e9, -1e9), (1e9, 1e9, 1e9)
+    u0 = np.array([1.3, -0.4, 0.25])
+    gamma = math.sqrt(1.0 + u0 @ u0)
+    theta = 2.0 * math.atan(dt * B0 / (2.0 * gamma))
+    pulse = dict(kind="plane", a0=0.0)
+    p = _one(ux=u0[0], uy=u0[1], uz=u0[2])
+    xs, ys, angles = [], [], []
+    chunk = 1000
+    for c in range(n_steps // chunk):
+        p = oracle.push(pulse, p, c * chunk * dt, dt, chunk, grid=(grid, lo, hi))
+        xs.append(p["x"][0]); ys.append(p["y"][0])
+        angles.append(math.atan2(p["uy"][0], p["ux"][0]))
+    u = np.array([p["ux"][0], p["uy"][0], p["uz"][0]])
+    assert abs(np.linalg.norm(u) - np.linalg.norm(u0)) <= 1e-12 * np.linalg.norm(u0)
+    assert abs(u[2] - u0[2]) <= 1e-12
+    # angle after N steps: atan2(u0) + N theta (counter-clockwise)
+    for c, ang in enumerate(angles):
+        expect = math.atan2(u0[1], u0[0]) + (c + 1) * chunk * theta
+        d = (ang - expect + math.pi) % (2 * math.pi) - math.pi
+        assert abs(d) <= 1e-10, (c, d)
+    # circle: the centre from three vertices, all vertices at radius rho
+    uperp = math.hypot(u0[0], u0[1])
+    rho = dt * uperp / (2.0 * gamma * math.sin(theta / 2.0))
+    P = np.array(list(zip(xs, ys)))
+    a, b, c_ = P[0], P[3], P[6]
+    d = 2 * (a[0] * (b[1] - c_[1]) + b[0] * (c_[1] - a[1]) + c_[0] * (a[1] - b[1]))
+    ux_ = ((a @ a) * (b[1] - c_[1]) + (b @ b) * (c_[1] - a[1]) + (c_ @ c_) * (a[1] - b[1])) / d
+    uy_ = ((a @ a) * (c_[0] - b[0]) + (b @ b) * (a[0] - c_[0]) + (c_ @ c_) * (b[0] - a[0])) / d
+    r = np.hypot(P[:, 0] - ux_, P[:, 1] - uy_)
+    assert np.max(np.abs(r - rho)) <= 1e-9 * rho
+
+
+def test_boris_pure_electric_kick():
+    """B = 0: the Boris step reduces to u -> u - dt E (two half kicks)."""
+    u = oracle.boris([0.1, -0.2, 0.3], [0.5, 1.0, -2.0], [0.0, 0.0, 0.0], 0.01)
+    np.testing.assert_allclose(u, [0.1 - 0.005, -0.2 - 0.01, 0.3 + 0.02], rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------------ plane wave (config 1)
+
+N_CYC = 10
+PLANE = dict(kind="plane", pol="x", env="sin2", env_len=N_CYC, a0=1.0, omega=1.0,
+             z_focus=0.0, t_focus=N_CYC * math.pi)
+
+
+def ux_exact(phi, a0=1.0, N=N_CYC):
+    """Exact continuum solution for an electron at rest ahead of the pulse:
+    du_x/dphi = -E_x(phi) with phi = t - z, E_x = a0 sin^2(phi/2N) cos(phi)."""
+    return -a0 * (0.5 * np.sin(phi) - np.sin((1 + 1 / N) * phi) / (4 * (1 + 1 / N))
+                  - np.sin((1 - 1 / N) * phi) / (4 * (1 - 1 / N)))
+
+
+def test_sin2_envelope_shape():
+    """The N-cycle sin^2 envelope of the config-1 pulse: Gamma(phi) =
+    sin^2(phi / 2N) on 0 <= phi <= 2 pi N (head at z = t), 0 outside."""
+    phi = np.linspace(-5, 2 * math.pi * N_CYC + 5, 400)
+    eta = phi - N_CYC * math.pi
+    g = oracle.envelope(PLANE, eta)
+    expect = np.where((phi >= 0) & (phi <= 2 * math.pi * N_CYC), np.sin(phi / (2 * N_CYC)) ** 2, 0.0)
+    np.testing.assert_allclose(g, expect, atol=1e-14)
+
+
+def test_plane_wave_exact_solution_dt2():
+    """Oracle trajectory vs the exact solution u_x(phi), u_z = u_x^2/2:
+    the error is O(dt^2), ratio ~4 on halving dt."""
+    errs = []
+    for dt in (0.04, 0.02, 0.01):
+        n = int(round(30.0 / dt))
+        a = oracle.push(PLANE, _one(), 0.0, dt, n - 1)
+        b = oracle.push(PLANE, a, (n - 1) * dt, dt, 1)
+        phi = (n - 0.5) * dt - 0.5 * (a["z"][0] + b["z"][0])
+        ex = ux_exact(phi)
+        errs.append(abs(b["ux"][0] - ex))
+        assert abs(b["uz"][0] - 0.5 * b["ux"][0] ** 2) < 1e-4
+        assert abs(b["uy"][0]) == 0.0
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.6 < r1 < 4.4 and 3.6 < r2 < 4.4, errs
+    assert errs[1] < 1e-5
+
+
+def test_lightfront_invariant_order_two():
+    """gamma - u_z is conserved by the exact motion in a plane wave; the
+    Boris scheme keeps max |h - 1| = C dt^2 (slope 2 +- 0.1)."""
+    devs = []
+    dts = (0.04, 0.02, 0.01)
+    for dt in dts:
+        n = int(round(60.0 / dt))
+        _, lf = oracle.push(PLANE, _one(z=1.0), 0.0, dt, n, lf=True)
+        devs.append(lf.max())
+    slope = np.polyfit(np.log(dts), np.log(devs), 1)[0]
+    assert abs(slope - 2.0) < 0.1, (slope, devs)
+
+
+def test_zero_net_energy_after_pulse():
+    """u_x(2 pi N) = 0 exactly for integer N >= 2 and any phase0, so the
+    particle is left at rest after a complete plane-wave pulse.  Residual is
+    O(dt^2): |u_x| shrinks ~4x per halving of dt."""
+    pulse = dict(PLANE, env_len=4, t_focus=4 * math.pi, phase0=0.3)
+    rng = np.random.default_rng(7)
+    res = []
+    for dt in (0.04, 0.02):
+        n = int(round(45.0 / dt))
+        z = rng.random(8) * L
+        p = dict(x=np.zeros(8), y=np.zeros(8), z=z, ux=np.zeros(8), uy=np.zeros(8), uz=np.zeros(8))
+        out = oracle.push(pulse, p, 0.0, dt, n)
+        assert np.all(45.0 - out["z"] > 8 * math.pi)  # the whole pulse has passed
+        g = np.sqrt(1 + out["ux"] ** 2 + out["uy"] ** 2 + out["uz"] ** 2)
+        assert np.max(g - 1.0) < 1e-10
+        res.append(np.max(np.abs(out["ux"])))
+    assert res[1] < 1e-5 and 3.0 < res[0] / res[1] < 5.0, res
+
+
+def test_fd_gradient_small_amplitude_closed_form():
+    """For a0 -> 0 the particle barely moves: gamma(T) - 1 = a0^2 I(phi)^2 / 2
+    with I the closed-form integral above, so dJ/da0 = a0 I(T - z0)^2 (1 + O(a0^2, dt^2))."""
+    a0, dt, n = 0.01, 0.01, 3000
+    pulse = dict(PLANE, a0=a0)
+    p = _one(z=0.5)
+    g = oracle.grad_fd(pulse, p, 0.0, dt, n, names=("a0",))["a0"]
+    I = ux_exact(n * dt - 0.5 - 0.5 * dt, a0=1.0)
+    assert abs(g - a0 * I * I) < 2e-3 * abs(a0 * I * I)
+
+
+# ------------------------------------------------------------------ grid
+
+def test_grid_trilinear_exact_for_multilinear():
+    """Trilinear interpolation reproduces node values and any multilinear
+    function (a + b x + c y + d z + e xy + f xz + g yz + h xyz) exactly;
+    positions outside the box clamp to the boundary."""
+    nx, ny, nz = 5, 4, 6
+    lo, hi = np.array([-1.0, 0.0, 2.0]), np.array([3.0, 3.0, 7.0])
+    X = np.linspace(lo[0], hi[0], nx)[None, None, :]
+    Y = np.linspace(lo[1], hi[1], ny)[None, :, None]
+    Z = np.linspace(lo[2], hi[2], nz)[:, None, None]
+    coef = np.array([[1, 2, -1, 3, 0.5, 0.25, -0.5, 0.125], [0, 1, 1, 1, 0, 0, 0, 0],
+                     [2, 0, 0, 0, 1, 0, 0, 0], [0, 0, 0, 0, 0, 0, 0, 1],
+                     [-3, 0.5, 0.5, -0.5, 0, 1, 1, 0], [7, 0, 0, 0, 0, 0, 0, 0]])
+
+    def f(c, x, y, z):
+        return (c[0] + c[1] * x + c[2] * y + c[3] * z + c[4] * x * y + c[5] * x * z
+                + c[6] * y * z + c[7] * x * y * z)
+
+    grid = np.stack([np.broadcast_to(f(c, X, Y, Z), (nz, ny, nx)) for c in coef]).astype(np.float32)
+    # every node value is exactly representable (multiples of 1/8 of small size)
+    assert np.all(grid.astype(np.float64) == np.stack([np.broadcast_to(f(c, X, Y, Z), (nz, ny, nx)) for c in coef]))
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        x, y, z = lo + rng.random(3) * (hi - lo)
+        got = oracle.grid_sample(grid, lo, hi, x, y, z)
+        np.testing.assert_allclose(got, [f(c, x, y, z) for c in coef], rtol=1e-13, atol=1e-12)
+    # nodes
+    got = oracle.grid_sample(grid, lo, hi, X[0, 0, 2], Y[0, 3, 0], Z[4, 0, 0])
+    np.testing.assert_array_equal(got, grid[:, 4, 3, 2].astype(np.float64))
+    # clamping
+    got = oracle.grid_sample(grid, lo, hi, -10.0, 1.5, 100.0)
+    np.testing.assert_allclose(got, [f(c, lo[0], 1.5, hi[2]) for c in coef], rtol=1e-13, atol=1e-12)
+
+
+# ------------------------------------------------------------------ beams
+
+def test_lg_normalisation_closed_form():
+    """LG_{1,2}: f(s) = s (3 - s) e^{-s/2} peaks at s = 1 with f = 2/sqrt(e),
+    so the amplitude coefficient is a0 sqrt(e)/2; LG_{0,1}: a0 sqrt(e);
+    LG_00 (Gaussian) and LG_{2,0}: a0 (peak on axis)."""
+    base = dict(kind="lg", pol="cp", env="cw", a0=3.0, w0=2 * L)
+    assert oracle.state(dict(base, lg_p=1, lg_l=2))["amp"] == pytest.approx(3.0 * math.sqrt(math.e) / 2, rel=1e-13)
+    assert oracle.state(dict(base, lg_p=1, lg_l=-2))["amp"] == pytest.approx(3.0 * math.sqrt(math.e) / 2, rel=1e-13)
+    assert oracle.state(dict(base, lg_p=0, lg_l=1))["amp"] == pytest.approx(3.0 * math.sqrt(math.e), rel=1e-13)
+    assert oracle.state(dict(base, lg_p=0, lg_l=0))["amp"] == pytest.approx(3.0, rel=1e-15)
+    assert oracle.state(dict(base, lg_p=2, lg_l=0))["amp"] == pytest.approx(3.0, rel=1e-15)
+
+
+def test_lg_profile_matches_scipy_laguerre_at_focus():
+    """At the focal plane the LG profile is A (sqrt(2) r / w0)^{|l|}
+    L_p^{|l|}(2 r^2 / w0^2) e^{-r^2/w0^2} e^{i l theta} (Gouy and curvature
+    vanish); the Laguerre factor is checked against scipy."""
+    special = pytest.importorskip("scipy.special")
+    w0 = 2 * L
+    for (pp, ll) in ((1, 2), (2, 1), (3, -2), (0, 3)):
+        pulse = dict(kind="lg", pol="x", env="cw", a0=1.0, w0=w0, lg_p=pp, lg_l=ll)
+        A = oracle.state(pulse)["amp"]
+        for (x, y) in ((0.3 * w0, 0.1 * w0), (-0.8 * w0, 0.5 * w0), (0.05, -1.2 * w0)):
+            r2 = x * x + y * y
+            s = 2 * r2 / w0 ** 2
+            expect = (A * s ** (abs(ll) / 2) * special.eval_genlaguerre(pp, abs(ll), s)
+                      * math.exp(-r2 / w0 ** 2) * np.exp(1j * ll * math.atan2(y, x)))
+            got = oracle.profile(pulse, x, y, 0.0)
+            assert abs(got - expect) < 1e-12 * max(1.0, abs(expect))
+
+
+def test_gaussian_beam_reduces_to_plane_wave_for_huge_waist():
+    """w0 -> infinity: zeta -> 0, w -> w0, no curvature or Gouy phase, so the
+    Gaussian beam near the axis is the plane wave."""
+    gauss = dict(kind="gauss", pol="x", env="gauss", env_len=30.0, a0=2.0, w0=1e7, longitudinal=True)
+    plane = dict(kind="plane", pol="x", env="gauss", env_len=30.0, a0=2.0)
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        x, y, z, t = rng.uniform(-20, 20, 4)
+        np.testing.assert_allclose(oracle.fields(gauss, x, y, z, t), oracle.fields(plane, x, y, z, t),
+                                   atol=1e-9)
+
+
+def test_gaussian_beam_textbook_values():
+    """Spot size, curvature and Gouy phase of the Gaussian beam at one z:
+    |u| = a0 (w0/w) e^{-r^2/w^2} and arg u = -k r^2/(2R) + atan(zeta) with
+    R = z (1 + z_R^2 / z^2) (the standard e^{i(omega t - k z)} form)."""
+    w0 = 3 * L
+    zR = 0.5 * w0 * w0
+    pulse = dict(kind="gauss", pol="x", env="cw", a0=1.5, w0=w0)
+    z = 0.6 * zR
+    w = w0 * math.sqrt(1 + (z / zR) ** 2)
+    R = z * (1 + (zR / z) ** 2)
+    for r in (0.0, 0.4 * w0, 1.1 * w0):
+        u = oracle.profile(pulse, r, 0.0, z)
+        assert abs(abs(u) - 1.5 * (w0 / w) * math.exp(-r * r / w / w)) < 1e-13
+        ph = -r * r / (2 * R) + math.atan(z / zR)
+        d = (np.angle(u) - ph + math.pi) % (2 * math.pi) - math.pi
+        assert abs(d) < 1e-12
+
+
+def test_circular_polarisation_rotates_with_constant_magnitude():
+    """CP plane wave: |E_perp| = a0 Gamma at every phase, |B_perp| = |E_perp|,
+    E perp B, and the helicities rotate in opposite senses."""
+    for pol, sense in (("cp", 1.0), ("cm", -1.0)):
+        pulse = dict(kind="plane", pol=pol, env="cw", a0=1.7)
+        ts = np.linspace(0, 2 * math.pi, 17)
+        F = np.array([oracle.fields(pulse, 0.3, -0.2, 1.1, t) for t in ts])
+        np.testing.assert_allclose(np.hypot(F[:, 0], F[:, 1]), 1.7, rtol=1e-14)
+        np.testing.assert_allclose(np.hypot(F[:, 3], F[:, 4]), 1.7, rtol=1e-14)
+        np.testing.assert_allclose(F[:, 0] * F[:, 3] + F[:, 1] * F[:, 4], 0.0, atol=1e-13)
+        ang = np.unwrap(np.arctan2(F[:, 1], F[:, 0]))
+        assert sense * (ang[-1] - ang[0]) == pytest.approx(2 * math.pi, rel=1e-12)
+
+
+# ------------------------------------------------------- Maxwell residuals
+
+def _residuals(pulse, pts, h=L / 200):
+    """Max over points of |dB/dt + curl E|, |dE/dt - curl B|, |div E|,
+    |div B| from 4th-order central differences, divided by k a0."""
+    def d(axis, x, y, z, t):
+        off = np.zeros(4)
+        off[axis] = h
+        P = lambda s: oracle.fields(pulse, x + s * off[0], y + s * off[1], z + s * off[2], t + s * off[3])
+        return (P(-2) - 8 * P(-1) + 8 * P(1) - P(2)) / (12 * h)
+
+    R = np.zeros(4)
+    for (x, y, z, t) in pts:
+        dx, dy, dz, dt = [d(a, x, y, z, t) for a in range(4)]
+        curlE = np.array([dy[2] - dz[1], dz[0] - dx[2], dx[1] - dy[0]])
+        curlB = np.array([dy[5] - dz[4], dz[3] - dx[5], dx[4] - dy[3]])
+        R = np.maximum(R, [np.linalg.norm(dt[3:6] + curlE), np.linalg.norm(dt[0:3] - curlB),
+                           abs(dx[0] + dy[1] + dz[2]), abs(dx[3] + dy[4] + dz[5])])
+    return R / pulse["a0"]
+
+
+def test_maxwell_residual_plane_wave_exact():
+    """The vacuum plane wave (v_phi = v_g = c, B0 = E0) solves Maxwell's
+    equations exactly (Eqs. E_1, b_corr_full with v_phi = v_g): residuals are
+    finite-difference error only."""
+    rng = np.random.default_rng(0)
+    pts = [tuple(rng.uniform(-5, 5, 4)) for _ in range(4)]
+    for pol in ("x", "y", "cp"):
+        R = _residuals(dict(kind="plane", pol=pol, env="cw", a0=1.0), pts)
+        assert np.all(R < 1e-7), R
+
+
+@pytest.mark.parametrize("kind,extra", [("gauss", {}), ("lg", dict(lg_p=1, lg_l=2, pol="cp"))])
+def test_maxwell_residual_scaling_paraxial(kind, extra):
+    """Paraxial beams with the first-order longitudinal fields (Sec. 3.1)
+    satisfy Maxwell's equations to O(eps^2), eps = 1/(k w0); dropping the
+    longitudinal fields leaves div E = O(eps).  Slopes are fitted over
+    w0 in {4, 8, 16, 32} lambda at fixed normalised sample points.  A wrong
+    sign of the curvature or Gouy term leaves O(eps) residuals and fails."""
+    C = np.random.default_rng(5).uniform(-1, 1, (6, 4))
+    ws = np.array([4, 8, 16, 32])
+    res = {True: [], False: []}
+    for lon in (True, False):
+        for w in ws:
+            w0 = w * L
+            zR = 0.5 * w0 * w0
+            p = dict(kind=kind, pol="x", env="cw", a0=1.0, w0=w0, longitudinal=lon, z_focus=0.0)
+            p.update(extra)
+            pts = [(0.7 * w0 * c[0], 0.7 * w0 * c[1], zR * c[2], 3 * c[3]) for c in C]
+            res[lon].append(_residuals(p, pts))
+    eps = 1.0 / (ws * L)
+    on, off = np.array(res[True]), np.array(res[False])
+    slope = lambda col: np.polyfit(np.log(eps), np.log(col), 1)[0]
+    assert 1.75 < slope(on[:, 0]) < 2.3 and 1.75 < slope(on[:, 1]) < 2.3
+    assert slope(on[:, 2]) > 1.75 and slope(on[:, 3]) > 1.75
+    assert 0.7 < slope(off[:, 2]) < 1.35
+    assert np.all(on[:, 2] < 0.1 * off[:, 2])
+
+
+# ------------------------------------------------------------ Yee dispersion
+
+def test_yee_expansions_against_exact_dispersion():
+    """Eqs. vphi, vg, e_amp are the second-order expansions of the exact Yee
+    relations (Eq. dispersion: sin^2(omega dt/2) = (dt/dx)^2 sin^2(k dx/2) and
+    Eq. e_amp_full: B0 = cos(omega dt/2) E0): their error is fourth order in
+    omega dx (slope 4 on halving dx at fixed Courant number)."""
+    cr = 0.95 / math.sqrt(3.0)
+    errs = []
+    dxs = np.array([0.2, 0.1, 0.05])
+    for dx in dxs:
+        dt = cr * dx
+        st = oracle.state(dict(kind="plane", a0=1.0, yee=True, yee_dx=dx, yee_dt=dt))
+        k = 2.0 / dx * math.asin(math.sin(dt / 2.0) / cr)
+        vphi = 1.0 / k
+        dkdw = math.cos(dt / 2) / math.sqrt(1 - (math.sin(dt / 2) / cr) ** 2)  # dk/domega at omega = 1
+        vg = 1.0 / dkdw
+        errs.append([abs(st["vphi"] - vphi), abs(st["vg"] - vg), abs(st["bratio"] - math.cos(dt / 2))])
+    errs = np.array(errs)
+    for c in range(3):
+        s = np.polyfit(np.log(dxs), np.log(errs[:, c]), 1)[0]
+        assert 3.7 < s < 4.3, (c, s, errs[:, c])
+
+
+def test_yee_coefficients_printed_in_paper():
+    """The printed coefficients of Eqs. vphi, vg, e_amp and the Courant
+    number of Sec. 2.1 (tests/golden/paper_yee.json)."""
+    gold = json.load(open(os.path.join(GOLDEN, "paper_yee.json")))
+    dx = 1e-2
+    cr = gold["courant_numerator"] / math.sqrt(3)
+    st = oracle.state(dict(kind="plane", a0=1.0, yee=True, yee_dx=dx, yee_dt=cr * dx))
+    x2 = dx * dx
+    assert (1 - st["vphi"]) / ((1 - cr * cr) * x2) == pytest.approx(gold["vphi_coeff"], rel=1e-8)
+    assert (1 - st["vg"]) / ((1 - cr * cr) * x2) == pytest.approx(gold["vg_coeff"], rel=1e-8)
+    assert (1 - st["bratio"]) / ((cr * dx) ** 2) == pytest.approx(gold["bratio_coeff"], rel=1e-8)
+
+
+# ------------------------------------------------------------- flying focus
+
+def _ff_pulse():
+    from paper_2307_04843_gb300 import workloads
+    p = dict(workloads.config(4)["pulse"])
+    p["longitudinal"] = False
+    return p
+
+
+def test_flying_focus_peak_moves_at_focal_velocity():
+    """The on-axis intensity peak of the 64-component superposition moves at
+    v_f = 0.99 (fitted over 400 time units, +-0.01), and the normalisation
+    puts the peak on-axis envelope at t_mid equal to a0."""
+    p = _ff_pulse()
+    st = oracle.state(p)
+    ts = np.linspace(st["t_mid"] - 200, st["t_mid"] + 200, 5)
+    peaks = []
+    for t in ts:
+        zc = st["z_mid"] + 0.99 * (t - st["t_mid"])
+        zs = np.arange(zc - 120, zc + 60, 1.0)
+        I = np.array([oracle.fields(p, 0.0, 0.0, z, t)[0] ** 2 +
+                      oracle.fields(p, 0.0, 0.0, z, t + math.pi / 2)[0] ** 2 for z in zs])
+        k = int(np.argmax(I))
+        assert 0 < k < len(zs) - 1
+        a, b, c = I[k - 1], I[k], I[k + 1]
+        peaks.append(zs[k] + 0.5 * (a - c) / (a - 2 * b + c))
+        if t == st["t_mid"]:
+            assert math.sqrt(b) == pytest.approx(p["a0"], rel=0.02)
+    v = np.polyfit(ts, peaks, 1)[0]
+    assert abs(v - 0.99) < 0.01, v
+
+
+def test_flying_focus_table_group_delay():
+    """Component table: equally spaced frequencies over omega (1 +- 5%), foci
+    equally spaced over [z_a, z_a + L], arrival times t_j = t_a + (z_j - z_a)/v_f,
+    and the spectral phase a trapezoid integral of tau = t - z, so that
+    dPhi/domega between neighbours equals the mean group delay."""
+    p = _ff_pulse()
+    st = oracle.state(p)
+    n = p["n_comp"]
+    np.testing.assert_allclose(st["fw"], np.linspace(0.95, 1.05, n), rtol=1e-14)
+    np.testing.assert_allclose(st["fz"], np.linspace(0.0, p["ff_length"], n), rtol=1e-14, atol=1e-12)
+    np.testing.assert_allclose(st["ft"], st["fz"] / 0.99, rtol=1e-14)
+    tau = st["ft"] - st["fz"]
+    np.testing.assert_allclose(np.diff(st["fphi"]) / np.diff(st["fw"]), 0.5 * (tau[1:] + tau[:-1]), rtol=1e-10)
+    # total tilt L (1/v_f - 1)
+    assert tau[-1] - tau[0] == pytest.approx(p["ff_length"] * (1 / 0.99 - 1), rel=1e-12)
+
+
+# ------------------------------------------------------------ diagnostics
+
+def test_gamma_histogram_binning_rule():
+    """bin = floor((gamma - lo) * bins/(hi - lo)), clamped; NaN not counted."""
+    ux = np.array([0.0, 0.0, 0.0, 0.0, np.nan, 0.0])
+    uz = np.array([math.sqrt(940.0 ** 2 - 1), math.sqrt(1000.05 ** 2 - 1), 0.0,
+                   math.sqrt(2000.0 ** 2 - 1), 0.0, math.sqrt(1059.99 ** 2 - 1)])
+    h = oracle.gamma_hist(ux, np.zeros(6), uz, 1024, 940.0, 1060.0)
+    assert h.sum() == 5
+    assert h[0] == 2  # gamma = 940 (edge) and gamma = 1 (clamped)
+    assert h[1023] == 2  # 2000 (clamped) and 1059.99
+    assert h[512] == 1  # (1000.05 - 940) * 1024 / 120 = 512.43
+
+
+def test_set_gamma_sums():
+    off = np.array([0, 2, 2, 5])
+    ux = np.array([0.0, 1.0, 0.0, 0.0, 3.0])
+    uz = np.array([0.0, 0.0, 2.0, 0.0, 4.0])
+    s = oracle.set_gamma_sums(off, ux, np.zeros(5), uz)
+    np.testing.assert_allclose(s, [1 + math.sqrt(2), 0.0, math.sqrt(5) + 1 + math.sqrt(26)], rtol=1e-15)
