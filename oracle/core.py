@@ -184,10 +184,24 @@ def boris(u, E, B, dt):
     return u
 
 
-def push(pulse, particles, t0, dt, n_steps, grid=None, lf=False):
+def push(pulse, particles, t0, dt, n_steps, grid=None, lf=False, threads=1):
     """Push copies of the particle arrays (dict with x, y, z, ux, uy, uz).
     grid: None or (array [6, nz, ny, nx] float32, lo, hi).  Returns the new
-    arrays as a dict (and the per-step light-front deviation if lf)."""
+    arrays as a dict (and the per-step light-front deviation if lf).
+    threads > 1 runs contiguous chunks of particles concurrently (the C call
+    releases the GIL); each particle is still pushed by the same plain loop."""
+    if threads > 1 and np.asarray(particles["x"]).size > 1:
+        import concurrent.futures
+        n = np.asarray(particles["x"]).size
+        bounds = np.linspace(0, n, min(threads, n) + 1).astype(int)
+        chunks = [{k: np.asarray(particles[k])[a:b] for k in ("x", "y", "z", "ux", "uy", "uz")}
+                  for a, b in zip(bounds[:-1], bounds[1:])]
+        with concurrent.futures.ThreadPoolExecutor(max_workers=len(chunks)) as ex:
+            res = list(ex.map(lambda c: push(pulse, c, t0, dt, n_steps, grid=grid, lf=lf), chunks))
+        if lf:
+            out = {k: np.concatenate([r[0][k] for r in res]) for k in res[0][0]}
+            return out, np.max(np.stack([r[1] for r in res]), axis=0)
+        return {k: np.concatenate([r[k] for r in res]) for k in res[0]}
     st = prepare(pulse)
     out = {k: np.array(particles[k], dtype=np.float64, copy=True) for k in ("x", "y", "z", "ux", "uy", "uz")}
     n = out["x"].size

@@ -1,0 +1,631 @@
+// ap_device.cuh -- device code of the analytic-pulse gather + Boris push.
+//
+// Everything a particle needs for one step, templated on the arithmetic of
+// the push:
+//   PREC = AP_FP64          double everywhere (the plain FP64 GPU path);
+//   PREC = AP_FP32_PHASE64  float fields and Boris, native double phase and
+//                           position accumulation;
+//   PREC = AP_FP32_PHASEFF  float fields and Boris, phase and position as
+//                           float-float pairs (no FP64 instruction in the
+//                           step loop; the FP64 pipe of this GPU issues at
+//                           about 1/70 of the FP32 rate).
+//
+// Method references (arXiv:2307.04843): field split E = E1 + E2 (Sec. 2,
+// Eqs. E_1, E_2); plane-wave pulse (Eqs. plane_func, plane_b); paraxial
+// Gaussian beam (Eq. paraxial, rewritten for +z and D = 3) in the complex
+// beam-parameter form q = 1 / (1 - i zeta); longitudinal components from the
+// divergence conditions (Sec. 3.1); flying focus as a linear superposition of
+// spectral components (Sec. 3.3).  The Boris step is the textbook relativistic
+// scheme (Boris 1970); the paper does not specify a pusher.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "ap_internal.h"
+
+namespace apt {
+
+template <int PREC>
+using Real = typename std::conditional<PREC == AP_FP64, double, float>::type;
+
+// ------------------------------------------------------------ float-float
+// Error-free transformations (Knuth TwoSum, Dekker/FMA TwoProd).  The _rn
+// intrinsics keep the compiler from contracting or reassociating them.
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ FF two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  return {p, e};
+}
+
+__device__ __forceinline__ FF split_double(double v) {
+  float hi = __double2float_rn(v);
+  float lo = __double2float_rn(v - (double)hi);
+  return {hi, lo};
+}
+
+// 2 pi = P1 + P2 (+ ~2e-15): Cody & Waite (1980) two-constant split.
+constexpr float kTwoPiHi = 6.28318548202514648f;
+constexpr float kTwoPiLo = -1.74845553e-07f;
+constexpr float kInvTwoPi = 0.159154943091895336f;
+
+// (hi + lo) reduced modulo 2 pi to about [-pi, pi], rounded to float.
+// m = rint(hi / 2 pi); hi - m P1 is exact (Sterbenz) with m P1 split by
+// TwoProd; the low-order parts are summed in float.
+__device__ __forceinline__ float reduce_ff(float hi, float lo) {
+  float m = rintf(__fmul_rn(hi, kInvTwoPi));
+  FF p = two_prod(m, kTwoPiHi);
+  float r = __fsub_rn(hi, p.hi);
+  float t = __fsub_rn(__fsub_rn(lo, p.lo), __fmul_rn(m, kTwoPiLo));
+  return __fadd_rn(r, t);
+}
+
+// float argument reduction for moderate |x| (a few times 2 pi).
+__device__ __forceinline__ float reduce_f(float x) {
+  float m = rintf(x * kInvTwoPi);
+  x = fmaf(-m, kTwoPiHi, x);
+  return fmaf(-m, kTwoPiLo, x);
+}
+
+__device__ __forceinline__ void sincos_r(float x, float *s, float *c) { __sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
+__device__ __forceinline__ float exp2_r(float x) { return exp2f(x); }
+__device__ __forceinline__ double exp2_r(double x) { return exp2(x); }
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rcp_r(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_r(double x) { return 1.0 / x; }
+__device__ __forceinline__ float cos_r(float x) { return __cosf(x); }
+__device__ __forceinline__ double cos_r(double x) { return cos(x); }
+
+template <typename R>
+struct Cx {
+  R re, im;
+};
+template <typename R>
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cadd(Cx<R> a, Cx<R> b) {
+  return {a.re + b.re, a.im + b.im};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cscale(Cx<R> a, R s) {
+  return {a.re * s, a.im * s};
+}
+
+constexpr double kLog2e = 1.4426950408889634;
+
+// ------------------------------------------------------------ positions
+// Position of one particle in the arithmetic of PREC.
+template <int PREC>
+struct Pos;
+
+template <>
+struct Pos<AP_FP64> {
+  double x, y, z;
+  __device__ void load(double X, double Y, double Z) { x = X; y = Y; z = Z; }
+  __device__ void store(double *X, double *Y, double *Z) const { *X = x; *Y = y; *Z = z; }
+  __device__ void advance(double vx, double vy, double vz, double dt) {
+    x += dt * vx; y += dt * vy; z += dt * vz;
+  }
+  __device__ double xr() const { return x; }
+  __device__ double yr() const { return y; }
+  __device__ double zr() const { return z; }
+};
+
+template <>
+struct Pos<AP_FP32_PHASE64> {
+  double x, y, z;
+  __device__ void load(double X, double Y, double Z) { x = X; y = Y; z = Z; }
+  __device__ void store(double *X, double *Y, double *Z) const { *X = x; *Y = y; *Z = z; }
+  // dt u / gamma in float, accumulated in double
+  __device__ void advance(float vx, float vy, float vz, float dt) {
+    x += (double)(dt * vx); y += (double)(dt * vy); z += (double)(dt * vz);
+  }
+  __device__ float xr() const { return (float)x; }
+  __device__ float yr() const { return (float)y; }
+  __device__ float zr() const { return (float)z; }
+};
+
+template <>
+struct Pos<AP_FP32_PHASEFF> {
+  FF x, y, z;
+  __device__ void load(double X, double Y, double Z) {
+    x = split_double(X); y = split_double(Y); z = split_double(Z);
+  }
+  __device__ void store(double *X, double *Y, double *Z) const {
+    *X = (double)x.hi + (double)x.lo;
+    *Y = (double)y.hi + (double)y.lo;
+    *Z = (double)z.hi + (double)z.lo;
+  }
+  // TwoSum of the high part with the float increment; the rounding error
+  // goes to the low part (no renormalisation needed: |lo| stays far below
+  // ulp(hi) times the step count).
+  __device__ __forceinline__ static void acc(FF &p, float d) {
+    FF s = two_sum(p.hi, d);
+    p.hi = s.hi;
+    p.lo = __fadd_rn(p.lo, s.lo);
+  }
+  __device__ void advance(float vx, float vy, float vz, float dt) {
+    acc(x, __fmul_rn(dt, vx)); acc(y, __fmul_rn(dt, vy)); acc(z, __fmul_rn(dt, vz));
+  }
+  __device__ float xr() const { return __fadd_rn(x.hi, x.lo); }
+  __device__ float yr() const { return __fadd_rn(y.hi, y.lo); }
+  __device__ float zr() const { return __fadd_rn(z.hi, z.lo); }
+};
+
+// ------------------------------------------------------------ time base
+// Per-thread constants of the time stepping, made once from (t0, dt) in
+// double: t_n = t0 + n dt is recomputed each step, never accumulated.
+template <int PREC>
+struct TimeBase;
+
+template <>
+struct TimeBase<AP_FP64> {
+  double t0, dt;
+  template <typename P>
+  __device__ void init(const P &, double T0, double DT) { t0 = T0; dt = DT; }
+};
+template <>
+struct TimeBase<AP_FP32_PHASE64> {
+  double t0, dt;
+  template <typename P>
+  __device__ void init(const P &, double T0, double DT) { t0 = T0; dt = DT; }
+};
+template <>
+struct TimeBase<AP_FP32_PHASEFF> {
+  // C_n = omega (t_n - t_f) + phase0 = Om0 + n Del (mod 2 pi), both reduced on
+  // entry; T_n = t_n - t_f = T0 + n DT.
+  FF om0, del, T0, DT;
+  template <typename P>
+  __device__ void init(const P &pp, double t0, double dt) {
+    const double twopi = 2.0 * CUDART_PI;
+    double c0 = pp.omega * (t0 - pp.t_f) + pp.phase0;
+    c0 -= twopi * rint(c0 / twopi);
+    double d = pp.omega * dt;
+    d -= twopi * rint(d / twopi);
+    om0 = split_double(c0);
+    del = split_double(d);
+    T0 = split_double(t0 - pp.t_f);
+    DT = split_double(dt);
+  }
+};
+
+// Local coordinates of one particle at step n, relative to the focus:
+// transverse x, y; dz = z - z_f; the reduced carrier phase psi; envelope
+// argument eta = (t - t_f) - (z - z_f)/v_g; and for the flying focus the
+// light-front coordinate phi' = (t - t_f) - (z - z_f) split in two parts.
+template <typename R>
+struct Local {
+  R x, y, dz, psi, eta;
+  R phi_hi, phi_lo;  // flying focus only (float-float, or double in phi_hi)
+};
+
+template <int PREC>
+__device__ __forceinline__ Local<Real<PREC>> local_coords(const Pulse<Real<PREC>> &P,
+                                                          const TimeBase<PREC> &tb, long long n,
+                                                          const Pos<PREC> &pos) {
+  Local<Real<PREC>> L;
+  if constexpr (PREC == AP_FP64) {
+    double T = (tb.t0 + (double)n * tb.dt) - P.t_f;
+    double dz = pos.z - P.z_f;
+    L.x = pos.x;
+    L.y = pos.y;
+    L.dz = dz;
+    L.psi = P.omega * T - P.k * dz + P.phase0;
+    L.eta = T - dz * P.inv_vg;
+    L.phi_hi = T - dz;
+    L.phi_lo = 0.0;
+  } else if constexpr (PREC == AP_FP32_PHASE64) {
+    double T = (tb.t0 + (double)n * tb.dt) - P.t_f;
+    double dz = pos.z - P.z_f;
+    double psi = P.omega * T - P.k * dz + P.phase0;
+    const double twopi = 2.0 * CUDART_PI;
+    psi = fma(-rint(psi * (1.0 / twopi)), twopi, psi);
+    L.x = (float)pos.x;
+    L.y = (float)pos.y;
+    L.dz = (float)dz;
+    L.psi = (float)psi;
+    L.eta = (float)(T - dz * (double)P.inv_vg);
+    double phi = T - dz;
+    L.phi_hi = (float)phi;
+    L.phi_lo = (float)(phi - (double)L.phi_hi);
+  } else {
+    // C_n = Om0 + n Del, reduced to one float
+    float nf = (float)n;  // exact for n < 2^24
+    FF nd = two_prod(nf, tb.del.hi);
+    FF c = two_sum(tb.om0.hi, nd.hi);
+    float clo = __fadd_rn(__fadd_rn(c.lo, nd.lo), __fmaf_rn(nf, tb.del.lo, tb.om0.lo));
+    float C = reduce_ff(c.hi, clo);
+    // T_n = T0 + n DT
+    FF nt = two_prod(nf, tb.DT.hi);
+    FF T = two_sum(tb.T0.hi, nt.hi);
+    T.lo = __fadd_rn(T.lo, __fadd_rn(nt.lo, __fmaf_rn(nf, tb.DT.lo, tb.T0.lo)));
+    // dz = z - z_f
+    FF dz = two_sum(pos.z.hi, -P.zf_hi);
+    dz.lo = __fadd_rn(dz.lo, __fsub_rn(pos.z.lo, P.zf_lo));
+    // psi = C - k dz
+    FF kd = two_prod(P.k_hi, dz.hi);
+    kd.lo = __fadd_rn(kd.lo, __fmaf_rn(P.k_hi, dz.lo, __fmul_rn(P.k_lo, dz.hi)));
+    FF ps = two_sum(C, -kd.hi);
+    L.psi = reduce_ff(ps.hi, __fsub_rn(ps.lo, kd.lo));
+    L.x = pos.xr();
+    L.y = pos.yr();
+    L.dz = __fadd_rn(dz.hi, dz.lo);
+    float Tf = __fadd_rn(T.hi, T.lo);
+    L.eta = fmaf(-L.dz, P.inv_vg, Tf);
+    // phi' = T - dz as float-float
+    FF ph = two_sum(T.hi, -dz.hi);
+    L.phi_hi = ph.hi;
+    L.phi_lo = __fadd_rn(ph.lo, __fsub_rn(T.lo, dz.lo));
+  }
+  return L;
+}
+
+// ------------------------------------------------------------ envelope
+// Gamma(eta) split into a multiplicative factor `mul` and an additive
+// base-2 exponent `l2` (Gaussian and super-Gaussian envelopes share the
+// beam's exp2).  SIN2: env_a = pi/T, env_b = T/2; GAUSS: env_a = 2 ln2 log2e
+// / T^2; SGAUSS: env_a = 1/tau, env_b = log2e; CW: 1.
+template <typename R>
+__device__ __forceinline__ void envelope(const Pulse<R> &P, R eta, R &mul, R &l2) {
+  mul = R(1);
+  l2 = R(0);
+  switch (P.env) {
+    case AP_ENV_SIN2: {
+      if (fabs(eta) > P.env_b) {
+        mul = R(0);
+      } else {
+        R c = cos_r(eta * P.env_a);
+        mul = c * c;
+      }
+      break;
+    }
+    case AP_ENV_GAUSS:
+      l2 = -P.env_a * eta * eta;
+      break;
+    case AP_ENV_SGAUSS: {
+      R s = eta * P.env_a;
+      s = s * s;
+      R p = s;
+      for (int i = 1; i < P.sg_order; ++i) p *= s;
+      l2 = -P.env_b * p;
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// --------------------------------------------------------- field assembly
+// E_perp = Re[p U], B_perp = (B0/E0) Re[(z x p) U];
+// E_z = Re[-i (v_phi/omega) DE], B_z = (B0/E0) Re[-i (c/omega) DB] with
+// DE = p_x dU/dx + p_y dU/dy and DB = -p_y dU/dx + p_x dU/dy (Sec. 3.1).
+template <typename R>
+__device__ __forceinline__ void assemble(const Pulse<R> &P, Cx<R> U, Cx<R> DE, Cx<R> DB, bool lon,
+                                         R E[3], R B[3]) {
+  R pxU = P.px_re * U.re - P.px_im * U.im;
+  R pyU = P.py_re * U.re - P.py_im * U.im;
+  E[0] = pxU;
+  E[1] = pyU;
+  B[0] = -P.bratio * pyU;
+  B[1] = P.bratio * pxU;
+  if (lon) {
+    E[2] = P.lonE * DE.im;
+    B[2] = P.bratio * P.lonB * DB.im;
+  } else {
+    E[2] = R(0);
+    B[2] = R(0);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R reduce_angle(R a) {
+  if constexpr (std::is_same<R, float>::value) return reduce_f(a);
+  return a;
+}
+
+// Plane wave (Eqs. plane_func, plane_b): U = A Gamma e^{i psi}.
+template <typename R>
+__device__ __forceinline__ void fields_plane(const Pulse<R> &P, const Local<R> &L, R E[3], R B[3]) {
+  R mul, l2;
+  envelope(P, L.eta, mul, l2);
+  R a = P.amp * mul;
+  if (l2 != R(0)) a *= exp2_r(l2);
+  R s, c;
+  sincos_r(L.psi, &s, &c);
+  Cx<R> U{a * c, a * s};
+  Cx<R> Z{R(0), R(0)};
+  assemble(P, U, Z, Z, false, E, B);
+}
+
+// Paraxial Gaussian beam (Eq. paraxial, D = 3, +z):
+//   u = A q exp(-r^2 q / w0^2),  q = 1/(1 - i zeta),  zeta = (z - z_f)/z_R,
+// which equals A (w0/w) e^{-r^2/w^2} e^{-i k r^2/(2R)} e^{i atan zeta}.
+// du/dx = -2 x q / w0^2 u.
+template <typename R>
+__device__ __forceinline__ void fields_gauss(const Pulse<R> &P, const Local<R> &L, R E[3], R B[3]) {
+  R mul, l2;
+  envelope(P, L.eta, mul, l2);
+  R zeta = L.dz * P.inv_zR;
+  R inv = rcp_r(fma(zeta, zeta, R(1)));
+  Cx<R> q{inv, zeta * inv};
+  R a = (L.x * L.x + L.y * L.y) * P.inv_w0sq;
+  R mag = P.amp * mul * exp2_r(fma(-a * q.re, R(kLog2e), l2));
+  R ang = reduce_angle<R>(L.psi - a * q.im);
+  R s, c;
+  sincos_r(ang, &s, &c);
+  Cx<R> U = cmul(q, Cx<R>{mag * c, mag * s});
+  Cx<R> DE{R(0), R(0)}, DB{R(0), R(0)};
+  if (P.lon) {
+    Cx<R> W = cmul(q, U);
+    R g = R(-2) * P.inv_w0sq;
+    // p_x x + p_y y and -p_y x + p_x y (complex)
+    Cx<R> se{P.px_re * L.x + P.py_re * L.y, P.px_im * L.x + P.py_im * L.y};
+    Cx<R> sb{-P.py_re * L.x + P.px_re * L.y, -P.py_im * L.x + P.px_im * L.y};
+    DE = cscale(cmul(se, W), g);
+    DB = cscale(cmul(sb, W), g);
+  }
+  assemble(P, U, DE, DB, P.lon != 0, E, B);
+}
+
+// Laguerre-Gaussian LG_pl (textbook; the paper names the family in Sec. 3.1):
+//   u = A (sqrt2/w0)^{|l|} (x + i sgn(l) y)^{|l|} L_p^{|l|}(s) q^{|l|+1} (q/q*)^p e^{-r^2 q/w0^2},
+// s = 2 r^2 |q|^2 / w0^2; the longitudinal terms use the product rule.
+template <typename R>
+__device__ __forceinline__ void fields_lg(const Pulse<R> &P, const Local<R> &L, R E[3], R B[3]) {
+  R mul, l2;
+  envelope(P, L.eta, mul, l2);
+  R zeta = L.dz * P.inv_zR;
+  R inv = rcp_r(fma(zeta, zeta, R(1)));
+  Cx<R> q{inv, zeta * inv};
+  R a = (L.x * L.x + L.y * L.y) * P.inv_w0sq;
+  R s = R(2) * a * q.re;
+  // Laguerre polynomial and derivative by Horner
+  R Lp = P.lg_c[P.lg_p], dL = R(0);
+  for (int i = P.lg_p - 1; i >= 0; --i) {
+    dL = fma(dL, s, Lp);
+    Lp = fma(Lp, s, P.lg_c[i]);
+  }
+  // (x + i sgn y)^{|l|} and its (|l| - 1)th power
+  Cx<R> xi{L.x, P.lg_sgn >= 0 ? L.y : -L.y};
+  Cx<R> pw{R(1), R(0)}, pwm{R(1), R(0)};
+  for (int i = 0; i < P.lg_al; ++i) {
+    pwm = pw;
+    pw = cmul(pw, xi);
+  }
+  // K = A pref q^{|l|+1} (q/q*)^p
+  Cx<R> K{P.amp * P.lg_pref, R(0)};
+  for (int i = 0; i <= P.lg_al; ++i) K = cmul(K, q);
+  Cx<R> g{(R(1) - zeta * zeta) * inv, R(2) * zeta * inv};
+  for (int i = 0; i < P.lg_p; ++i) K = cmul(K, g);
+  R mag = mul * exp2_r(fma(-a * q.re, R(kLog2e), l2));
+  R ang = reduce_angle<R>(L.psi - a * q.im);
+  R sn, cs;
+  sincos_r(ang, &sn, &cs);
+  Cx<R> base = cmul(K, Cx<R>{mag * cs, mag * sn});
+  Cx<R> U = cmul(base, cscale(pw, Lp));
+  Cx<R> DE{R(0), R(0)}, DB{R(0), R(0)};
+  if (P.lon) {
+    // dU/dx = base (T1 + x T2), dU/dy = base (i sgn T1 + y T2)
+    Cx<R> T1 = cscale(pwm, R(P.lg_al) * Lp);
+    Cx<R> T2 = cmul(pw, Cx<R>{R(4) * q.re * P.inv_w0sq * dL - R(2) * P.inv_w0sq * Lp * q.re,
+                              -R(2) * P.inv_w0sq * Lp * q.im});
+    R sg = P.lg_sgn >= 0 ? R(1) : R(-1);
+    Cx<R> dx = cmul(base, Cx<R>{T1.re + L.x * T2.re, T1.im + L.x * T2.im});
+    Cx<R> dy = cmul(base, Cx<R>{-sg * T1.im + L.y * T2.re, sg * T1.re + L.y * T2.im});
+    Cx<R> px{P.px_re, P.px_im}, py{P.py_re, P.py_im};
+    DE = cadd(cmul(px, dx), cmul(py, dy));
+    DB = cadd(cmul(Cx<R>{-py.re, -py.im}, dx), cmul(px, dy));
+  }
+  assemble(P, U, DE, DB, P.lon != 0, E, B);
+}
+
+// Flying focus: linear superposition of Gaussian spectral components
+// (Sec. 3.3).  omega_j = w_first + j dw, vacuum k_j = omega_j, so
+// e^{i omega_j phi'} = e^{i w_first phi'} (e^{i dw phi'})^j: two reduced
+// base angles and one complex rotation per component.
+template <int PREC>
+__device__ __forceinline__ void fields_flying(const Pulse<Real<PREC>> &P, const Local<Real<PREC>> &L,
+                                              Real<PREC> E[3], Real<PREC> B[3]) {
+  using R = Real<PREC>;
+  R A1, B1;
+  if constexpr (PREC == AP_FP64) {
+    A1 = P.ff_w * L.phi_hi;
+    B1 = P.ff_dw * L.phi_hi;
+  } else {
+    // (w_first + 0) * phi' and dw * phi' in float-float, reduced mod 2 pi
+    const FF w{P.ffw_hi, P.ffw_lo}, d{P.ffd_hi, P.ffd_lo};
+    FF a = two_prod(w.hi, L.phi_hi);
+    float alo = __fmaf_rn(w.hi, L.phi_lo, __fmaf_rn(w.lo, L.phi_hi, a.lo));
+    A1 = reduce_ff(a.hi, alo);
+    FF b = two_prod(d.hi, L.phi_hi);
+    float blo = __fmaf_rn(d.hi, L.phi_lo, __fmaf_rn(d.lo, L.phi_hi, b.lo));
+    B1 = reduce_ff(b.hi, blo);
+  }
+  R sa, ca, sb, cb;
+  sincos_r(A1, &sa, &ca);
+  sincos_r(B1, &sb, &cb);
+  Cx<R> rot{ca, sa};
+  const Cx<R> step{cb, sb};
+  const R a = (L.x * L.x + L.y * L.y) * P.inv_w0sq;
+  const R ak = -a * R(kLog2e);
+  Cx<R> S0{R(0), R(0)}, S1{R(0), R(0)};
+  const int nc = P.n_comp;
+  for (int j = 0; j < nc; ++j) {
+    const Comp<R> &cj = P.comp[j];
+    R zeta = fma(L.dz, cj.inv_zR, -cj.zoff);
+    R inv = rcp_r(fma(zeta, zeta, R(1)));
+    Cx<R> q{inv, zeta * inv};
+    R mag = exp2_r(ak * q.re);
+    R s, c;
+    sincos_r(-a * q.im, &s, &c);
+    Cx<R> U = cmul(cmul(q, Cx<R>{mag * c, mag * s}), cmul(rot, Cx<R>{cj.c_re, cj.c_im}));
+    S0 = cadd(S0, U);
+    if (P.lon) S1 = cadd(S1, cscale(cmul(q, U), cj.inv_k));
+    rot = cmul(rot, step);
+  }
+  Cx<R> DE{R(0), R(0)}, DB{R(0), R(0)};
+  if (P.lon) {
+    R g = R(-2) * P.inv_w0sq;
+    Cx<R> se{P.px_re * L.x + P.py_re * L.y, P.px_im * L.x + P.py_im * L.y};
+    Cx<R> sb2{-P.py_re * L.x + P.px_re * L.y, -P.py_im * L.x + P.px_im * L.y};
+    DE = cscale(cmul(se, S1), g);
+    DB = cscale(cmul(sb2, S1), g);
+  }
+  // the 1/k_j factors are inside S1: lonE = lonB = 1 for this kind
+  assemble(P, S0, DE, DB, P.lon != 0, E, B);
+}
+
+template <int KIND, int PREC>
+__device__ __forceinline__ void analytic_fields(const Pulse<Real<PREC>> &P,
+                                                const Local<Real<PREC>> &L, Real<PREC> E[3],
+                                                Real<PREC> B[3]) {
+  if constexpr (KIND == AP_PLANE) fields_plane(P, L, E, B);
+  else if constexpr (KIND == AP_GAUSS) fields_gauss(P, L, E, B);
+  else if constexpr (KIND == AP_LG) fields_lg(P, L, E, B);
+  else fields_flying<PREC>(P, L, E, B);
+}
+
+// ------------------------------------------------------------ grid gather
+// Trilinear gather of the static node-centred grid (E = E1 + E2, Sec. 2).
+// Because the grid is static, the 8 corner values of the particle's current
+// cell are kept in registers as trilinear coefficients and refetched only
+// when the particle changes cell; the result equals a gather every step.
+template <typename R>
+struct GridCache {
+  int cell;
+  R c[6][8];
+};
+
+template <typename R>
+__device__ __forceinline__ R grid_coord(R v, R lo, R inv_d, int n, int &i) {
+  R f = (v - lo) * inv_d;
+  f = fmin(fmax(f, R(0)), R(n - 1));
+  int ii = (int)f;
+  if (ii > n - 2) ii = n - 2;
+  i = ii;
+  return f - R(ii);
+}
+
+template <typename R>
+__device__ __forceinline__ void grid_gather(const GridView &g, GridCache<R> &gc, R x, R y, R z,
+                                            R E[3], R B[3]) {
+  int ix, iy, iz;
+  R wx, wy, wz;
+  if constexpr (std::is_same<R, double>::value) {
+    wx = grid_coord<R>(x, g.lo_d[0], g.inv_d_d[0], g.nx, ix);
+    wy = grid_coord<R>(y, g.lo_d[1], g.inv_d_d[1], g.ny, iy);
+    wz = grid_coord<R>(z, g.lo_d[2], g.inv_d_d[2], g.nz, iz);
+  } else {
+    wx = grid_coord<R>(x, g.lo[0], g.inv_d[0], g.nx, ix);
+    wy = grid_coord<R>(y, g.lo[1], g.inv_d[1], g.ny, iy);
+    wz = grid_coord<R>(z, g.lo[2], g.inv_d[2], g.nz, iz);
+  }
+  const int cell = (iz * g.ny + iy) * g.nx + ix;
+  if (cell != gc.cell) {
+    gc.cell = cell;
+    const size_t sx = 1, sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
+    const size_t b = (size_t)cell;
+#pragma unroll
+    for (int comp = 0; comp < 6; ++comp) {
+      const float *f = g.f[comp] + b;
+      R v000 = __ldg(f), v100 = __ldg(f + sx), v010 = __ldg(f + sy), v110 = __ldg(f + sy + sx);
+      R v001 = __ldg(f + sz), v101 = __ldg(f + sz + sx), v011 = __ldg(f + sz + sy),
+        v111 = __ldg(f + sz + sy + sx);
+      R *c = gc.c[comp];
+      c[0] = v000;
+      c[1] = v100 - v000;
+      c[2] = v010 - v000;
+      c[3] = v001 - v000;
+      c[4] = (v110 - v100) - (v010 - v000);
+      c[5] = (v101 - v100) - (v001 - v000);
+      c[6] = (v011 - v010) - (v001 - v000);
+      c[7] = ((v111 - v110) - (v101 - v100)) - ((v011 - v010) - (v001 - v000));
+    }
+  }
+  R out[6];
+#pragma unroll
+  for (int comp = 0; comp < 6; ++comp) {
+    const R *c = gc.c[comp];
+    R t = fma(wz, c[7], c[4]);
+    t = fma(wy, t, c[1]);
+    t = fma(wz, c[5], t);
+    R u = fma(wz, c[6], c[2]);
+    R r = fma(wx, t, c[0]);
+    r = fma(wy, u, r);
+    out[comp] = fma(wz, c[3], r);
+  }
+  E[0] += out[0]; E[1] += out[1]; E[2] += out[2];
+  B[0] += out[3]; B[1] += out[4]; B[2] += out[5];
+}
+
+// ------------------------------------------------------------ Boris push
+// Relativistic Boris step (Boris 1970) for charge -1, mass 1: half electric
+// kick, rotation about B with tan(angle/2) = |tau|, half electric kick.
+// Returns 1/gamma of the new momentum.
+template <typename R>
+__device__ __forceinline__ R boris(R u[3], const R E[3], const R B[3], R dt) {
+  const R h = R(-0.5) * dt;
+  R um0 = fma(h, E[0], u[0]), um1 = fma(h, E[1], u[1]), um2 = fma(h, E[2], u[2]);
+  R ig = rsqrt_r(fma(um0, um0, fma(um1, um1, fma(um2, um2, R(1)))));
+  R hg = h * ig;
+  R t0 = hg * B[0], t1 = hg * B[1], t2 = hg * B[2];
+  R tt = fma(t0, t0, fma(t1, t1, t2 * t2));
+  R sc = R(2) * rcp_r(R(1) + tt);
+  R s0 = sc * t0, s1 = sc * t1, s2 = sc * t2;
+  R p0 = um0 + (um1 * t2 - um2 * t1);
+  R p1 = um1 + (um2 * t0 - um0 * t2);
+  R p2 = um2 + (um0 * t1 - um1 * t0);
+  R q0 = um0 + (p1 * s2 - p2 * s1);
+  R q1 = um1 + (p2 * s0 - p0 * s2);
+  R q2 = um2 + (p0 * s1 - p1 * s0);
+  u[0] = fma(h, E[0], q0);
+  u[1] = fma(h, E[1], q1);
+  u[2] = fma(h, E[2], q2);
+  return rsqrt_r(fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], R(1)))));
+}
+
+__device__ __forceinline__ bool all_finite(double a, double b, double c, double d, double e,
+                                           double f) {
+  return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d) && isfinite(e) && isfinite(f);
+}
+
+// warp max of a non-negative float, one atomic per warp into a double slot
+__device__ __forceinline__ void warp_max_to(double *slot, float v, unsigned mask) {
+  unsigned bits = __float_as_uint(v);
+  bits = __reduce_max_sync(mask, bits);
+  if ((threadIdx.x & 31) == (__ffs(mask) - 1)) {
+    double d = (double)__uint_as_float(bits);
+    atomicMax(reinterpret_cast<unsigned long long *>(slot),
+              (unsigned long long)__double_as_longlong(d));
+  }
+}
+__device__ __forceinline__ void warp_max_to(double *slot, double v, unsigned mask) {
+  unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long other = __shfl_xor_sync(mask, bits, o);
+    // lanes outside the mask return their own value; max is unaffected
+    if (other > bits) bits = other;
+  }
+  if ((threadIdx.x & 31) == (__ffs(mask) - 1))
+    atomicMax(reinterpret_cast<unsigned long long *>(slot), bits);
+}
+
+}  // namespace apt

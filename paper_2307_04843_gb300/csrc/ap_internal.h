@@ -1,0 +1,136 @@
+// ap_internal.h -- structures shared by the host layer and the kernels of the
+// analytic-pulse library (not part of the public C ABI in include/ap.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/ap.h"
+
+namespace apt {
+
+constexpr int kMaxComp = AP_MAX_COMP;
+constexpr int kLgMaxP = 8;
+constexpr int kLgMaxL = 8;
+
+// Per-component constants of the flying-focus superposition (Sec. 3.3).
+// Component j: zeta_j = (z - z_ref) / zR_j - zoff_j,
+//   u_j = c_j q_j exp(-r^2 q_j / w0^2) e^{i omega_j phi'},  phi' = (t - t_ref) - (z - z_ref),
+// with c_j = A e^{i (omega_j t_ref - k_j z_ref - Phi_j + phase0)} folded in on the host.
+template <typename R>
+struct Comp {
+  R inv_zR;  // 1 / zR_j
+  R zoff;    // (z_j - z_ref) / zR_j
+  R inv_k;   // 1 / k_j (longitudinal terms)
+  R c_re, c_im;
+};
+
+// Device-side description of one pulse, derived on the host in FP64 (row a1)
+// and rounded once to the arithmetic type R of the push.
+template <typename R>
+struct Pulse {
+  int32_t kind, pol, env, lon;
+  int32_t lg_p, lg_al, lg_sgn, n_comp;
+  int32_t sg_order, yee, pad0, pad1;
+  R amp;            // amplitude coefficient A of the profile
+  R inv_vg;         // 1 / v_g
+  R bratio;         // B0 / E0 (Eq. e_amp; 1 in vacuum)
+  R lonE, lonB;     // v_phi / omega and c / omega: d/dz -> -i omega / v, Sec. 3.1
+  R inv_w0sq;       // 1 / w0^2
+  R inv_zR;         // 1 / z_R
+  R env_a, env_b;   // envelope constants (see ap_device.cuh)
+  R px_re, px_im, py_re, py_im;  // polarisation vector p
+  R lg_c[kLgMaxP + 1];           // L_p^{|l|}(s) = sum_i lg_c[i] s^i
+  R lg_pref;                     // (sqrt(2) / w0)^{|l|}
+  // carrier phase psi = omega (t - t_f) - k (z - z_f) + phase0 (double, host-exact)
+  double omega, k, t_f, z_f, phase0;
+  // float-float copies for AP_FP32_PHASEFF
+  float k_hi, k_lo, zf_hi, zf_lo;
+  // flying focus: omega_j = ff_w + j ff_dw (vacuum k_j = omega_j), with
+  // float-float copies for AP_FP32_PHASEFF
+  double ff_w, ff_dw;
+  float ffw_hi, ffw_lo, ffd_hi, ffd_lo;
+  Comp<R> comp[kMaxComp];
+};
+
+// Grid view passed to kernels (device pointers, caller-owned).
+struct GridView {
+  const float *f[6];
+  int nx, ny, nz;
+  float lo[3], inv_d[3];  // node spacing d = (hi - lo)/(n - 1)
+  double lo_d[3], inv_d_d[3];
+};
+
+// Diagnostics view.
+struct DiagView {
+  double *lf;            // [n_steps] or null
+  uint32_t *hist;        // [bins] or null
+  int bins;
+  double hist_lo, hist_scale;
+  double *set_sum;       // [n_sets] or null
+};
+
+struct LaunchShape {
+  int block;
+  int blocks_per_sm;
+  int ppt;
+};
+
+// Host-side launchers implemented in the per-kind translation units.
+struct PushArgs {
+  double *x, *y, *z;
+  void *ux, *uy, *uz;
+  long long n;
+  double t0, dt;
+  long long n_steps;
+  int grid_on;
+  GridView grid;
+  DiagView diag;
+  int *status;
+  int sm_count;
+  LaunchShape shape;
+};
+
+struct BatchArgs {
+  PushArgs base;
+  const long long *set_offsets;  // device [n_sets + 1]
+  int n_sets;
+  unsigned int *tile_counter;    // device scratch
+  int tile;                      // particles per tile
+};
+
+struct EvalArgs {
+  const double *xyzt;
+  long long n;
+  double *EB;
+  int *status;
+};
+
+// One launcher per pulse kind; precision selects the template instance.
+// `pulse_d` / `pulse_f` are host copies; `dpulse_*` device copies (batched).
+int launch_push(int kind, int precision, const Pulse<double> &pd, const Pulse<float> &pf,
+                const PushArgs &a, void *stream);
+int launch_eval(int kind, int precision, const Pulse<double> &pd, const Pulse<float> &pf,
+                const EvalArgs &a, void *stream);
+int launch_batch(int kind, int precision, const Pulse<double> *dpd, const Pulse<float> *dpf,
+                 const BatchArgs &a, void *stream);
+
+// per-kind entry points (ap_push_<kind>.cu)
+#define APT_DECLARE_KIND(K)                                                                       \
+  int launch_push_##K(int precision, const Pulse<double> &pd, const Pulse<float> &pf,             \
+                      const PushArgs &a, void *stream);                                           \
+  int launch_eval_##K(int precision, const Pulse<double> &pd, const Pulse<float> &pf,             \
+                      const EvalArgs &a, void *stream);                                           \
+  int launch_batch_##K(int precision, const Pulse<double> *dpd, const Pulse<float> *dpf,          \
+                       const BatchArgs &a, void *stream);
+APT_DECLARE_KIND(plane)
+APT_DECLARE_KIND(gauss)
+APT_DECLARE_KIND(lg)
+APT_DECLARE_KIND(flying)
+#undef APT_DECLARE_KIND
+
+// status bits written by kernels
+constexpr int kStatusNonfinite = 1;
+constexpr int kStatusTimeout = 2;
+
+}  // namespace apt

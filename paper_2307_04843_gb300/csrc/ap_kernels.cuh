@@ -1,0 +1,317 @@
+// ap_kernels.cuh -- kernels of the gather + push (rows a2-a12 of the hot
+// path) and their launchers, instantiated once per pulse kind by
+// ap_push_<kind>.cu (AP_KIND_ID / AP_KIND_NAME set before inclusion).
+#pragma once
+
+#include "ap_device.cuh"
+
+namespace apt {
+
+// One particle through n_steps fused steps: load (a2), per step the local
+// coordinates and phase (a3), envelope and profile (a4-a7), grid gather
+// (a8), Boris and position (a9), light-front diagnostic (a10); then store
+// (a11).  `valid` is false for the padding lanes of the last warp, which run
+// the loop on a dummy particle so that warp reductions see full warps.
+// Returns the final gamma (double) of a valid particle, 0 otherwise.
+template <int KIND, int PREC, bool GRID>
+__device__ __forceinline__ double push_one(const Pulse<Real<PREC>> &P, const PushArgs &a,
+                                           long long i, bool valid) {
+  using R = Real<PREC>;
+  double X = 0.0, Y = 0.0, Z = 0.0;
+  R u[3] = {R(0), R(0), R(0)};
+  if (valid) {
+    X = a.x[i];
+    Y = a.y[i];
+    Z = a.z[i];
+    const R *ux = static_cast<const R *>(a.ux);
+    const R *uy = static_cast<const R *>(a.uy);
+    const R *uz = static_cast<const R *>(a.uz);
+    u[0] = ux[i];
+    u[1] = uy[i];
+    u[2] = uz[i];
+  }
+  Pos<PREC> pos;
+  pos.load(X, Y, Z);
+  TimeBase<PREC> tb;
+  tb.init(P, a.t0, a.dt);
+  const R dtR = (R)a.dt;
+  const R h0 = R(1) / rsqrt_r(fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], R(1))))) - u[2];
+  GridCache<R> gc;
+  gc.cell = -1;
+  double *lf = a.diag.lf;
+  for (long long s = 0; s < a.n_steps; ++s) {
+    Local<R> L = local_coords<PREC>(P, tb, s, pos);
+    R E[3], B[3];
+    analytic_fields<KIND, PREC>(P, L, E, B);
+    if constexpr (GRID) grid_gather<R>(a.grid, gc, pos.xr(), pos.yr(), pos.zr(), E, B);
+    R ig = boris(u, E, B, dtR);
+    pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtR);
+    if (lf) {
+      R dev = valid ? fabs((R(1) / ig - u[2]) - h0) : R(0);
+      warp_max_to(lf + s, dev, 0xffffffffu);
+    }
+  }
+  if (!valid) return 0.0;
+  pos.store(a.x + i, a.y + i, a.z + i);
+  R *ux = static_cast<R *>(a.ux);
+  R *uy = static_cast<R *>(a.uy);
+  R *uz = static_cast<R *>(a.uz);
+  ux[i] = u[0];
+  uy[i] = u[1];
+  uz[i] = u[2];
+  const double dx = (double)u[0], dy = (double)u[1], dz = (double)u[2];
+  if (!all_finite(a.x[i], a.y[i], a.z[i], dx, dy, dz)) atomicOr(a.status, kStatusNonfinite);
+  // gamma in double from the stored momentum, fixed operation order
+  return __dsqrt_rn(__dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                        __dmul_rn(dz, dz)),
+                              1.0));
+}
+
+__device__ __forceinline__ void hist_add(uint32_t *s_hist, const DiagView &d, double g) {
+  if (!isfinite(g)) return;
+  double f = floor(__dmul_rn(__dsub_rn(g, d.hist_lo), d.hist_scale));
+  int b = f < 0.0 ? 0 : (f > (double)(d.bins - 1) ? d.bins - 1 : (int)f);
+  atomicAdd(&s_hist[b], 1u);
+}
+
+// block sum of a double; result valid in thread 0
+__device__ __forceinline__ double block_sum(double v, double *s_red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) s_red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < nw; ++k) r += s_red[k];
+  return r;
+}
+
+// Plain launch: a grid-stride loop over warps of particles (all lanes of a
+// warp share the trip count), one particle per thread, every step fused.
+template <int KIND, int PREC, bool GRID>
+__global__ void __launch_bounds__(256) push_kernel(const __grid_constant__ Pulse<Real<PREC>> P,
+                                                   const __grid_constant__ PushArgs a) {
+  extern __shared__ uint32_t s_hist[];
+  __shared__ double s_red[32];
+  const bool hist = a.diag.hist != nullptr;
+  if (hist) {
+    for (int b = threadIdx.x; b < a.diag.bins; b += blockDim.x) s_hist[b] = 0u;
+    __syncthreads();
+  }
+  double acc = 0.0;
+  const long long npad = (a.n + 31) & ~31LL;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += stride) {
+    const bool valid = i < a.n;
+    double g = push_one<KIND, PREC, GRID>(P, a, i, valid);
+    if (valid) {
+      acc += g;
+      if (hist) hist_add(s_hist, a.diag, g);
+    }
+  }
+  if (a.diag.set_sum) {
+    double t = block_sum(acc, s_red);
+    if (threadIdx.x == 0) atomicAdd(a.diag.set_sum, t);
+  }
+  if (hist) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < a.diag.bins; b += blockDim.x)
+      if (s_hist[b]) atomicAdd(&a.diag.hist[b], s_hist[b]);
+  }
+}
+
+// Batched persistent launch (row a12): blocks pop fixed-size tiles of
+// (set, particles) from a global counter until the tile count is reached;
+// each set's pulse is copied to shared memory; the loop is bounded by the
+// tile count and no block waits on another.
+template <int KIND, int PREC, bool GRID>
+__global__ void __launch_bounds__(256) batch_kernel(const Pulse<Real<PREC>> *__restrict__ sets,
+                                                    const __grid_constant__ BatchArgs ba) {
+  using R = Real<PREC>;
+  extern __shared__ long long s_prefix[];  // [n_sets + 1] tile prefix
+  __shared__ double s_red[32];
+  __shared__ long long s_tile;
+  __shared__ int s_set;
+  __shared__ __align__(16) unsigned char s_pulse_raw[sizeof(Pulse<R>)];
+  Pulse<R> &sp = *reinterpret_cast<Pulse<R> *>(s_pulse_raw);
+  const PushArgs &a = ba.base;
+  const int T = ba.tile;
+  // tile prefix over sets: tiles of set s = ceil(N_s / T)
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    for (int s = 0; s < ba.n_sets; ++s) {
+      s_prefix[s] = acc;
+      long long ns = ba.set_offsets[s + 1] - ba.set_offsets[s];
+      if (ns < 0) ns = 0;  // malformed offsets: no tiles (particles are bounds-checked below)
+      acc += (ns + T - 1) / T;
+    }
+    s_prefix[ba.n_sets] = acc;
+    s_set = -1;
+  }
+  __syncthreads();
+  const long long total = s_prefix[ba.n_sets];
+  // per-set pulse size copied to shared memory (flying focus: only n_comp components)
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(ba.tile_counter, 1u);
+    __syncthreads();
+    const long long tile = s_tile;
+    if (tile >= total) break;
+    // set of this tile: last s with prefix[s] <= tile (binary search)
+    int lo = 0, hi = ba.n_sets;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (s_prefix[mid] <= tile) lo = mid; else hi = mid;
+    }
+    const int set = lo;
+    if (set != s_set) {
+      const int words = (int)(sizeof(Pulse<R>) / 4);
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(sets + set);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(s_pulse_raw);
+      for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+      __syncthreads();
+      if (threadIdx.x == 0) s_set = set;
+    }
+    __syncthreads();
+    const long long first = ba.set_offsets[set] + (tile - s_prefix[set]) * T;
+    const long long end_set = ba.set_offsets[set + 1];
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < T; k += blockDim.x) {
+      const long long i = first + k;
+      const bool valid = i >= 0 && i < end_set && i < a.n;
+      double g = push_one<KIND, PREC, GRID>(sp, a, i, valid);
+      if (valid) acc += g;
+    }
+    if (a.diag.set_sum) {
+      double t = block_sum(acc, s_red);
+      if (threadIdx.x == 0) atomicAdd(a.diag.set_sum + set, t);
+    }
+    __syncthreads();
+  }
+}
+
+// Field evaluation hook: one point per thread, the push's own code path at
+// step 0 of a time base starting at the point's t.
+template <int KIND, int PREC>
+__global__ void __launch_bounds__(256) eval_kernel(const __grid_constant__ Pulse<Real<PREC>> P,
+                                                   const __grid_constant__ EvalArgs a) {
+  using R = Real<PREC>;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const double x = a.xyzt[i], y = a.xyzt[a.n + i], z = a.xyzt[2 * a.n + i],
+               t = a.xyzt[3 * a.n + i];
+  Pos<PREC> pos;
+  pos.load(x, y, z);
+  TimeBase<PREC> tb;
+  tb.init(P, t, 0.0);
+  Local<R> L = local_coords<PREC>(P, tb, 0, pos);
+  R E[3], B[3];
+  analytic_fields<KIND, PREC>(P, L, E, B);
+  for (int c = 0; c < 3; ++c) {
+    a.EB[(long long)c * a.n + i] = (double)E[c];
+    a.EB[(long long)(c + 3) * a.n + i] = (double)B[c];
+  }
+}
+
+// ------------------------------------------------------------ launchers
+
+template <typename K>
+inline int occupancy_blocks(K kernel, int block, size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem) != cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
+template <int KIND, int PREC, bool GRID>
+int launch_push_t(const Pulse<Real<PREC>> &P, const PushArgs &a, void *stream) {
+  auto kern = push_kernel<KIND, PREC, GRID>;
+  const int block = a.shape.block;
+  const size_t smem = a.diag.hist ? (size_t)a.diag.bins * sizeof(uint32_t) : 0;
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return AP_ERR_CUDA;
+  }
+  const long long npad = (a.n + 31) & ~31LL;
+  long long want = (npad + block - 1) / block;
+  int per_sm = a.shape.blocks_per_sm > 0 ? a.shape.blocks_per_sm : occupancy_blocks(kern, block, smem);
+  long long cap = (long long)a.sm_count * per_sm;
+  int grid = (int)(want < cap ? want : cap);
+  if (grid < 1) grid = 1;
+  kern<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(P, a);
+  return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+}
+
+template <int KIND, int PREC>
+int launch_eval_t(const Pulse<Real<PREC>> &P, const EvalArgs &a, void *stream) {
+  const int block = 128;
+  const long long grid = (a.n + block - 1) / block;
+  eval_kernel<KIND, PREC><<<(unsigned)grid, block, 0, static_cast<cudaStream_t>(stream)>>>(P, a);
+  return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+}
+
+template <int KIND, int PREC, bool GRID>
+int launch_batch_t(const Pulse<Real<PREC>> *sets, const BatchArgs &ba, void *stream) {
+  auto kern = batch_kernel<KIND, PREC, GRID>;
+  const int block = ba.base.shape.block;
+  const size_t smem = (size_t)(ba.n_sets + 1) * sizeof(long long);
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return AP_ERR_CUDA;
+  }
+  int per_sm = ba.base.shape.blocks_per_sm > 0 ? ba.base.shape.blocks_per_sm
+                                                : occupancy_blocks(kern, block, smem);
+  const int grid = ba.base.sm_count * per_sm;
+  kern<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(sets, ba);
+  return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+}
+
+}  // namespace apt
+
+// Per-kind launchers: dispatch on precision and grid.
+#define APT_DEFINE_KIND(K, KID)                                                                   \
+  namespace apt {                                                                                 \
+  int launch_push_##K(int precision, const Pulse<double> &pd, const Pulse<float> &pf,             \
+                      const PushArgs &a, void *stream) {                                          \
+    switch (precision) {                                                                          \
+      case AP_FP64:                                                                               \
+        return a.grid_on ? launch_push_t<KID, AP_FP64, true>(pd, a, stream)                       \
+                         : launch_push_t<KID, AP_FP64, false>(pd, a, stream);                     \
+      case AP_FP32_PHASE64:                                                                       \
+        return a.grid_on ? launch_push_t<KID, AP_FP32_PHASE64, true>(pf, a, stream)               \
+                         : launch_push_t<KID, AP_FP32_PHASE64, false>(pf, a, stream);             \
+      case AP_FP32_PHASEFF:                                                                       \
+        return a.grid_on ? launch_push_t<KID, AP_FP32_PHASEFF, true>(pf, a, stream)               \
+                         : launch_push_t<KID, AP_FP32_PHASEFF, false>(pf, a, stream);             \
+      default:                                                                                    \
+        return AP_ERR_ARG;                                                                        \
+    }                                                                                             \
+  }                                                                                               \
+  int launch_eval_##K(int precision, const Pulse<double> &pd, const Pulse<float> &pf,             \
+                      const EvalArgs &a, void *stream) {                                          \
+    switch (precision) {                                                                          \
+      case AP_FP64: return launch_eval_t<KID, AP_FP64>(pd, a, stream);                            \
+      case AP_FP32_PHASE64: return launch_eval_t<KID, AP_FP32_PHASE64>(pf, a, stream);            \
+      case AP_FP32_PHASEFF: return launch_eval_t<KID, AP_FP32_PHASEFF>(pf, a, stream);            \
+      default: return AP_ERR_ARG;                                                                 \
+    }                                                                                             \
+  }                                                                                               \
+  int launch_batch_##K(int precision, const Pulse<double> *dpd, const Pulse<float> *dpf,          \
+                       const BatchArgs &a, void *stream) {                                        \
+    switch (precision) {                                                                          \
+      case AP_FP64:                                                                               \
+        return a.base.grid_on ? launch_batch_t<KID, AP_FP64, true>(dpd, a, stream)                \
+                              : launch_batch_t<KID, AP_FP64, false>(dpd, a, stream);              \
+      case AP_FP32_PHASE64:                                                                       \
+        return a.base.grid_on ? launch_batch_t<KID, AP_FP32_PHASE64, true>(dpf, a, stream)        \
+                              : launch_batch_t<KID, AP_FP32_PHASE64, false>(dpf, a, stream);      \
+      case AP_FP32_PHASEFF:                                                                       \
+        return a.base.grid_on ? launch_batch_t<KID, AP_FP32_PHASEFF, true>(dpf, a, stream)        \
+                              : launch_batch_t<KID, AP_FP32_PHASEFF, false>(dpf, a, stream);      \
+      default:                                                                                    \
+        return AP_ERR_ARG;                                                                        \
+    }                                                                                             \
+  }                                                                                               \
+  }

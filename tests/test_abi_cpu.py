@@ -1,0 +1,92 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every entry point declared in include/ap.h, and its
+argument validation rejects bad pulse descriptions before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2307_04843_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ap.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ap_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return _lib.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    # the binding declares exactly the header's entry points
+    assert sorted(_lib.SIGNATURES) == names
+
+
+def test_version_and_status_strings(L):
+    assert _lib.ap_version() == 1
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+        s = _lib.ap_status_string(code)
+        assert s and s != "unknown status"
+    assert _lib.ap_status_string(12345) == "unknown status"
+
+
+def _init_rc(L, d, n=1):
+    arr = (_lib.ApPulseDesc * n)(*([_lib.pulse_desc(d)] * n))
+    h = ctypes.c_void_p()
+    return L.ap_init_pulse(arr, n, ctypes.byref(h)), h
+
+
+@pytest.mark.parametrize("bad", [
+    dict(kind="gauss", w0=0.0, env="cw"),                       # beam without a waist
+    dict(kind="plane", omega=0.0),                               # no frequency
+    dict(kind="plane", env="sin2", env_len=0.0),                 # empty envelope
+    dict(kind="plane", env="sgauss", env_len=1.0, sg_order=0),   # bad super-Gaussian order
+    dict(kind="lg", w0=1.0, lg_p=9),                             # p beyond the table
+    dict(kind="lg", w0=1.0, lg_l=-9),
+    dict(kind="flying", w0=1.0, n_comp=1, beta_f=0.99, ff_length=10.0),
+    dict(kind="flying", w0=1.0, n_comp=500, beta_f=0.99, ff_length=10.0),
+    dict(kind="flying", w0=1.0, n_comp=8, beta_f=0.0, ff_length=10.0),
+    dict(kind="plane", yee=True, yee_dx=0.1, yee_dt=0.2),       # Courant number > 1
+    dict(kind="plane", a0=float("nan")),
+])
+def test_invalid_descriptions_rejected_on_host(L, bad):
+    rc, h = _init_rc(L, bad)
+    assert rc == _lib.AP_ERR_ARG
+    assert not h.value
+
+
+def test_flying_focus_with_yee_dispersion_unsupported(L):
+    rc, _ = _init_rc(L, dict(kind="flying", w0=1.0, n_comp=8, beta_f=0.99, ff_length=10.0, yee=True,
+                             yee_dx=0.1, yee_dt=0.05))
+    assert rc == _lib.AP_ERR_UNSUPPORTED
+
+
+def test_null_and_count_arguments(L):
+    h = ctypes.c_void_p()
+    assert L.ap_init_pulse(None, 1, ctypes.byref(h)) == _lib.AP_ERR_ARG
+    arr = (_lib.ApPulseDesc * 1)(_lib.pulse_desc(dict(kind="plane")))
+    assert L.ap_init_pulse(arr, 0, ctypes.byref(h)) == _lib.AP_ERR_ARG
+    assert L.ap_init_pulse(arr, _lib.AP_MAX_SETS + 1, ctypes.byref(h)) == _lib.AP_ERR_ARG
+    assert L.ap_init_pulse(arr, 1, None) == _lib.AP_ERR_ARG
+    assert L.ap_set_launch(None, None) == _lib.AP_ERR_ARG
+    assert L.ap_num_sets(None) == _lib.AP_ERR_ARG
+    assert L.ap_gather_push(None, None, None, 0.0, 0.1, 1, 0, None, None) == _lib.AP_ERR_ARG
+    assert L.ap_batch_workspace_bytes(None) == 0
+    L.ap_destroy(None)
+    L.ap_graph_destroy(None)
+
+
+def test_build_is_up_to_date_after_build(L):
+    assert build.up_to_date()
+    assert os.path.exists(build.LIB)

@@ -1,0 +1,104 @@
+"""Batched persistent launch (workload 5 shape): many Gaussian pulse-parameter
+sets with uneven particle counts in one launch, and its CUDA-graph replay.
+
+Checks: every particle's final state equals (bit for bit) the plain
+single-set push of the same set, since both run the same per-particle code;
+per-set sums of final gamma match the oracle; the graph replays the call."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_04843_gb300 import workloads
+from support import THREADS, rel_u_err
+
+
+def _small_batch(n_sets=9, total=1500, n_steps=400, seed=None):
+    cfg = workloads.config(5)
+    sets, counts = workloads.batch_sets(cfg, seed=seed)
+    sets = sets[:n_sets]
+    counts = workloads.scaled_counts(counts[:n_sets], total)
+    counts[2] = 1      # a set of one particle
+    counts[4] = 37     # ragged
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    parts = workloads.particles_uniform(cfg["box"], int(off[-1]), workloads.seed_for(5))
+    return cfg, sets, off, parts, n_steps
+
+
+def _run_batched(sets, off, parts, t0, dt, n_steps, precision, graph=False, replays=1):
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    with _lib.Handle(sets) as h:
+        dev = _lib.to_device(parts, precision)
+        d_off = torch.as_tensor(off).cuda()
+        ws = torch.zeros(_lib.ap_batch_workspace_bytes(h.h) // 4, dtype=torch.int32, device="cuda")
+        diag = dict(set_sum=torch.zeros(len(sets), dtype=torch.float64, device="cuda"))
+        if graph:
+            s = torch.cuda.Stream()
+            g = _lib.ap_batch_graph_create(h.h, dev, d_off, None, t0, dt, n_steps, precision, diag, ws, s)
+            snapshot = {k: v.clone() for k, v in dev.items()}
+            for r in range(replays):
+                for k in dev:
+                    dev[k].copy_(snapshot[k])
+                torch.cuda.synchronize()
+                _lib.ap_graph_launch(g, s)
+                s.synchronize()
+            _lib.ap_graph_destroy(g)
+        else:
+            _lib.ap_gather_push_batched(h.h, dev, d_off, None, t0, dt, n_steps, precision, diag, ws)
+        st = h.status()
+        torch.cuda.synchronize()
+        return _lib.to_host(dev), diag["set_sum"].cpu().numpy(), st
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batched_equals_per_set_push_and_oracle(precision):
+    from support import gpu_push
+    cfg, sets, off, parts, n_steps = _small_batch()
+    out, sums, st = _run_batched(sets, off, parts, cfg["t0"], cfg["dt"], n_steps, precision)
+    assert st == 0
+    for s in range(len(sets)):
+        sl = slice(off[s], off[s + 1])
+        sub = {k: v[sl] for k, v in parts.items()}
+        one, _, _ = gpu_push(sets[s], sub, cfg["t0"], cfg["dt"], n_steps, precision)
+        for k in one:
+            np.testing.assert_array_equal(out[k][sl], one[k])
+    # oracle on every set (small), per-set sums of gamma
+    refs = [oracle.push(sets[s], {k: v[off[s]:off[s + 1]] for k, v in parts.items()}, cfg["t0"],
+                        cfg["dt"], n_steps, threads=THREADS) for s in range(len(sets))]
+    ref = {k: np.concatenate([r[k] for r in refs]) for k in refs[0]}
+    e = rel_u_err(out, ref)
+    assert np.median(e) <= (1e-10 if precision == "fp64" else 1e-4)
+    assert np.max(e) <= (1e-7 if precision == "fp64" else 1e-3)
+    ref_sums = oracle.set_gamma_sums(off, ref["ux"], ref["uy"], ref["uz"])
+    np.testing.assert_allclose(sums, ref_sums, rtol=1e-12 if precision == "fp64" else 1e-4)
+    own_sums = oracle.set_gamma_sums(off, out["ux"], out["uy"], out["uz"])
+    np.testing.assert_allclose(sums, own_sums, rtol=1e-13)
+
+
+@pytest.mark.gpu
+def test_graph_replay_matches_direct_call():
+    cfg, sets, off, parts, n_steps = _small_batch(n_steps=200)
+    a, sa, _ = _run_batched(sets, off, parts, cfg["t0"], cfg["dt"], n_steps, "fp32")
+    b, sb, st = _run_batched(sets, off, parts, cfg["t0"], cfg["dt"], n_steps, "fp32", graph=True, replays=3)
+    assert st == 0
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+    np.testing.assert_allclose(sa, sb, rtol=1e-14)
+
+
+@pytest.mark.gpu
+def test_batched_argument_errors():
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    cfg, sets, off, parts, _ = _small_batch()
+    with _lib.Handle(sets) as h:
+        dev = _lib.to_device(parts, "fp32")
+        d_off = torch.as_tensor(off).cuda()
+        small = torch.zeros(1, dtype=torch.int32, device="cuda")
+        with pytest.raises(_lib.APError) as e:
+            _lib.ap_gather_push_batched(h.h, dev, d_off, None, 0.0, 0.02, 5, "fp32", None, small)
+        assert e.value.status == _lib.AP_ERR_WORKSPACE
+        ws = torch.zeros(64, dtype=torch.int32, device="cuda")
+        with pytest.raises(_lib.APError):
+            _lib.ap_gather_push_batched(h.h, dev, d_off[:-1], None, 0.0, 0.02, 5, "fp32", None, ws)

@@ -1,0 +1,115 @@
+"""Field parity: ap_eval_fields (the push's own field code at one time step)
+against the oracle's textbook fields, element by element, for every pulse
+kind, polarisation, envelope and the optional terms.
+
+Tolerances (absolute, in units of a0): FP64 1e-10 (the oracle's
+finite-difference longitudinal terms are accurate to ~1e-12); FP32 with a
+double or float-float phase 4e-6 for single beams (float arithmetic of
+~20 operations on O(1) quantities, MUFU sin/cos absolute error ~4e-7 and
+exp2 relative error ~2e-7), 4e-5 for the 64-component flying focus (64
+float terms summed)."""
+import math
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_04843_gb300 import workloads
+
+L = 2 * math.pi
+
+CASES = {
+    "plane-x-sin2": dict(kind="plane", pol="x", env="sin2", env_len=10, a0=1.0, t_focus=10 * math.pi),
+    "plane-y-sgauss": dict(kind="plane", pol="y", env="sgauss", env_len=25.0, sg_order=4, a0=2.0),
+    "plane-cp-gauss": dict(kind="plane", pol="cp", env="gauss", env_len=30.0, a0=3.0, phase0=0.4),
+    "gauss-x-lon": dict(kind="gauss", pol="x", env="gauss", env_len=30.0, a0=10.0, w0=3 * L,
+                        longitudinal=True),
+    "gauss-y-nolon": dict(kind="gauss", pol="y", env="cw", a0=2.0, w0=2 * L, z_focus=5.0, t_focus=3.0),
+    "gauss-cm-lon-yee": dict(kind="gauss", pol="cm", env="gauss", env_len=20.0, a0=1.5, w0=4 * L,
+                             longitudinal=True, yee=True, yee_dx=0.2, yee_dt=0.1),
+    "lg12-cp-lon": dict(kind="lg", pol="cp", env="sin2", env_len=20, a0=20.0, w0=2 * L, lg_p=1, lg_l=2,
+                        longitudinal=True, t_focus=30.0),
+    "lg2m1-x-lon": dict(kind="lg", pol="x", env="cw", a0=1.0, w0=3 * L, lg_p=2, lg_l=-1, longitudinal=True),
+    "lg03-y": dict(kind="lg", pol="y", env="gauss", env_len=40.0, a0=1.0, w0=3 * L, lg_p=0, lg_l=3),
+    "flying-8-lon": dict(kind="flying", pol="x", a0=2.0, w0=2 * L, n_comp=8, bw_frac=0.05, beta_f=0.9,
+                         ff_length=40 * L, longitudinal=True),
+}
+
+
+def _points(pulse, n, seed):
+    rng = np.random.default_rng(seed)
+    w0 = pulse.get("w0", 3 * L)
+    zR = 0.5 * w0 * w0
+    x = rng.uniform(-1.5, 1.5, n) * w0
+    y = rng.uniform(-1.5, 1.5, n) * w0
+    if pulse["kind"] == "flying":
+        st = oracle.state(pulse)
+        z = st["z_mid"] + rng.uniform(-60, 60, n)
+        t = st["t_mid"] + rng.uniform(-60, 60, n)
+    else:
+        z = pulse.get("z_focus", 0.0) + rng.uniform(-1, 1, n) * min(zR, 100.0)
+        t = pulse.get("t_focus", 0.0) + (z - pulse.get("z_focus", 0.0)) + rng.uniform(-40, 40, n)
+    return x, y, z, t
+
+
+def _tol(pulse, precision):
+    a0 = pulse["a0"]
+    if precision == "fp64":
+        return 1e-10 * a0
+    return (4e-5 if pulse["kind"] == "flying" else 4e-6) * a0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("precision", ["fp64", "fp32_phase64", "fp32"])
+def test_fields_match_oracle(name, precision):
+    from paper_2307_04843_gb300 import _lib
+    pulse = CASES[name]
+    n = 257  # several blocks and a ragged tail
+    x, y, z, t = _points(pulse, n, seed=zlib.crc32(name.encode()) % 1000)
+    ref = oracle.fields(pulse, x, y, z, t)
+    with _lib.Handle(pulse) as h:
+        got = h.eval_fields(x, y, z, t, precision=precision).cpu().numpy()
+    err = np.abs(got - ref)
+    assert np.max(err) <= _tol(pulse, precision), (name, precision, np.max(err), np.unravel_index(np.argmax(err), err.shape))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_flying_focus_64_components(precision):
+    from paper_2307_04843_gb300 import _lib
+    pulse = dict(workloads.config(4)["pulse"])
+    x, y, z, t = _points(pulse, 129, seed=11)
+    ref = oracle.fields(pulse, x, y, z, t)
+    with _lib.Handle(pulse) as h:
+        got = h.eval_fields(x, y, z, t, precision=precision).cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= _tol(pulse, precision)
+
+
+@pytest.mark.gpu
+def test_fields_far_from_origin_phase_accuracy():
+    """Large |z| and t (phase ~ 1e4 rad): the float-float phase keeps the
+    field within the FP32 bound; a plain float phase would not (~1e-3)."""
+    from paper_2307_04843_gb300 import _lib
+    pulse = dict(kind="plane", pol="x", env="cw", a0=1.0)
+    rng = np.random.default_rng(5)
+    z = rng.uniform(5000, 6000, 200)
+    t = z + rng.uniform(-3000, 3000, 200)
+    x = y = np.zeros(200)
+    ref = oracle.fields(pulse, x, y, z, t)
+    with _lib.Handle(pulse) as h:
+        got = h.eval_fields(x, y, z, t, precision="fp32").cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 4e-6
+
+
+@pytest.mark.gpu
+def test_eval_fields_empty_and_bad_set():
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    with _lib.Handle(CASES["plane-x-sin2"]) as h:
+        xyzt = torch.zeros((4, 0), dtype=torch.float64, device="cuda")
+        EB = torch.zeros((6, 0), dtype=torch.float64, device="cuda")
+        _lib.ap_eval_fields(h.h, 0, xyzt, EB, "fp64")
+        with pytest.raises(_lib.APError):
+            _lib.ap_eval_fields(h.h, 1, xyzt, EB, "fp64")
