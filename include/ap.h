@@ -230,6 +230,32 @@ int ap_gather_push_batched(ap_handle h, const ap_particles *p, const ap_grid *g,
                            double dt, int64_t n_steps, int32_t precision, const ap_diag *diag,
                            void *workspace, size_t ws_bytes, void *stream);
 
+/* Size of the static scratch array used by ap_gather_push_batched_static. */
+#define AP_STATIC_SCRATCH_BYTES 4096
+
+/* Allocation-free variant of ap_gather_push_batched (the paper has no
+ * counterpart: this is a library-interface convenience).  For callers that
+ * cannot call cudaMalloc when they push -- for example a host application
+ * whose own allocator has already reserved the GPU's memory, or a time loop
+ * that must not risk a device synchronisation or an out-of-memory failure in
+ * the middle of a step.  Instead of a caller workspace it uses a file-scope
+ * static __device__ array of AP_STATIC_SCRATCH_BYTES bytes that every GPU
+ * loading the library holds until the process exits; the caller still passes
+ * the particle arrays, grid and diagnostics.  Arguments and results are those
+ * of ap_gather_push_batched.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the one array; the tile counter in it is
+ *     zeroed by each call on `stream`, but calls that overlap on the GPU race
+ *     on it and must be serialised by the caller.
+ *   - Returns AP_ERR_WORKSPACE if the scratch the call needs
+ *     (ap_batch_workspace_bytes) exceeds AP_STATIC_SCRATCH_BYTES; otherwise
+ *     the errors of ap_gather_push_batched.  Calls no cudaMalloc or cudaFree. */
+int ap_gather_push_batched_static(ap_handle h, const ap_particles *p, const ap_grid *g,
+                                  double t0, double dt, int64_t n_steps, int32_t precision,
+                                  const ap_diag *diag, void *stream);
+
 /* Captures ap_gather_push_batched (its memsets and the persistent launch)
  * into a CUDA graph on `stream` (which must not be the legacy default
  * stream); every pointer is baked into the graph and must stay valid.

@@ -92,6 +92,10 @@ SIGNATURES = {
                                               ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                               ctypes.c_int32, ctypes.POINTER(ApDiag), _vp,
                                               ctypes.c_size_t, _vp]),
+    "ap_gather_push_batched_static": (ctypes.c_int, [_vp, ctypes.POINTER(ApParticles),
+                                                     ctypes.POINTER(ApGrid), ctypes.c_double,
+                                                     ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
+                                                     ctypes.POINTER(ApDiag), _vp]),
     "ap_batch_graph_create": (ctypes.c_int, [_vp, ctypes.POINTER(ApParticles), ctypes.POINTER(ApGrid),
                                              ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                              ctypes.c_int32, ctypes.POINTER(ApDiag), _vp, ctypes.c_size_t,
@@ -301,6 +305,21 @@ def ap_gather_push_batched(h, particles, set_offsets, grid, t0, dt, n_steps, pre
                                        int(n_steps), precision_id(precision), _ref(diag_struct(diag)),
                                        _ptr(workspace), workspace.numel() * workspace.element_size(),
                                        _stream(stream)))
+
+
+def ap_gather_push_batched_static(h, particles, set_offsets, grid, t0, dt, n_steps, precision, diag,
+                                  stream=None):
+    """Batched push without a caller workspace: for callers that cannot
+    allocate device memory when they push (their allocator owns the GPU, or
+    the step loop must not risk a synchronising or failing allocation).  The
+    scratch is a static device array shared by every call on the device, so
+    calls must not overlap on the GPU; the first call on a device should come
+    before any stream capture."""
+    ps = particles_struct(particles, precision, set_offsets)
+    check("ap_gather_push_batched_static",
+          lib().ap_gather_push_batched_static(h, ctypes.byref(ps), _ref(grid_struct(grid)), float(t0),
+                                              float(dt), int(n_steps), precision_id(precision),
+                                              _ref(diag_struct(diag)), _stream(stream)))
 
 
 def ap_batch_graph_create(h, particles, set_offsets, grid, t0, dt, n_steps, precision, diag, workspace,
