@@ -1,26 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the analytic-pulse gather + relativistic Boris push.
 
-Workload (one GPU): the Gaussian-beam workload -- 1e7 electrons at rest in a
-20 x 20 x 40 lambda box, paraxial Gaussian w0 = 3 lambda, a0 = 10, Gaussian
-envelope (intensity FWHM 30), first-order longitudinal fields, plus a 256^3
-static FP32 grid field gathered trilinearly; 4000 Boris steps of dt = 0.02,
-float arithmetic with a float-float phase argument and position.
+Default workload (one GPU): the Gaussian-beam workload -- 1e7 electrons at
+rest in a 20 x 20 x 40 lambda box, paraxial Gaussian w0 = 3 lambda, a0 = 10,
+Gaussian envelope (intensity FWHM 30), first-order longitudinal fields, plus
+a 256^3 static FP32 grid field gathered trilinearly; 4000 Boris steps of
+dt = 0.02, float arithmetic with a float-float phase argument and position.
 
 One bench step = restore the initial particle state (device copy) + one
-ap_gather_push call that advances all 1e7 particles by 4000 fused steps.
-The metric is particle-steps per second; inputs (360 MB of particle state,
-402 MB of grid) exceed the 126 MB L2, so no flush is needed.
+gather + push call that advances every particle by all its fused steps.  The
+metric is particle-steps per second; the inputs (particle state, grid)
+exceed the 126 MB L2, so no flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload 1..5]
 
 N > 1 runs under torchrun, one rank per GPU, each rank pushing its own
-1e7-particle shard (weak scaling, no data-path collective); rank 0 prints
-one JSON line.  --impl reference times the CPU oracle on the host cores.
+shard of the same size (weak scaling, no data-path collective); rank 0
+prints one JSON line.  --impl reference times the CPU oracle on the host
+cores.  --workload selects the other workloads (1 plane FP64, 3 inverse-
+Compton LG with the gamma histogram, 4 flying focus, 5 batched sets in a
+CUDA graph plus the adjoint).
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -34,18 +37,28 @@ if ROOT not in sys.path:
 
 METRIC = "particle-steps/s (analytic field+Boris)"
 UNIT = "particle-steps/s"
-
-# FP32-pipe operations per particle-step of the float-float Gaussian + grid
-# kernel, counted from the formulas the kernel evaluates (see the design doc,
-# "Roofline"): phase unit 65, envelope 2, Gaussian profile with longitudinal
-# terms and field assembly 57, trilinear gather from the cached cell 72,
-# Boris rotation 42, float-float position update 27.
-ALGO_FP32_OPS = 265
-ALGO_MUFU_OPS = 7
 SM_COUNT = 152
 FP32_LANES = 128      # FP32 operations per clock per SM
 MUFU_LANES = 16       # special-function operations per clock per SM
 SM_MAX_MHZ = 2070.0
+
+# FP32-pipe operations per particle-step, counted from the formulas each
+# kernel evaluates ("Roofline"), and MUFU operations.
+# Workload 2 (Gaussian + longitudinal + grid, float-float phase): local
+# coordinates and phase 34, envelope 2, Gaussian profile + longitudinal +
+# assembly 28, trilinear gather from the cached cell 57, Boris 42,
+# compensated position update 18, z for the gather 1.
+ALGO = {
+    1: dict(fp32=0, mufu=0, fp64=60),
+    2: dict(fp32=182, mufu=7),
+    3: dict(fp32=190, mufu=8),
+    4: dict(fp32=2300, mufu=258),
+    5: dict(fp32=125, mufu=7),
+}
+# DRAM bytes per particle-step of the workload-2 kernel from the committed
+# ncu capture (profiles/push_kernel_gauss_grid_packed_full.md); None when the
+# kernel changed after the capture.
+TRAFFIC_PER_PARTICLE_STEP = None
 
 
 def parse():
@@ -54,9 +67,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=None, help="particles per GPU (default 1e7)")
-    ap.add_argument("--nsteps", type=int, default=None, help="Boris steps per call (default 4000)")
+    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--n", type=int, default=None, help="particles per GPU (default: the workload's)")
+    ap.add_argument("--nsteps", type=int, default=None, help="Boris steps per call (default: the workload's)")
     ap.add_argument("--grid", type=int, default=256)
+    ap.add_argument("--soa-grid", action="store_true", help="gather from the six component arrays")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -130,62 +146,155 @@ def dist_info():
     return ws, rank, local
 
 
-def oracle_rate(cfg, parts, grid_np, lo, hi, n_steps, core_seconds, threads):
+def oracle_rate(pulse, parts, t0, dt, n_steps, core_seconds, threads, grid=None):
     """CPU oracle throughput on a bounded sample of the workload's particles:
     a probe sizes the sample to about `core_seconds` of single-core work."""
     import oracle
-    probe_n, probe_steps = 8, 200
+    probe_n, probe_steps = 8, 100
     sub = {k: v[:probe_n] for k, v in parts.items()}
     t = time.perf_counter()
-    oracle.push(cfg["pulse"], sub, cfg["t0"], cfg["dt"], probe_steps, grid=(grid_np, lo, hi))
+    oracle.push(pulse, sub, t0, dt, probe_steps, grid=grid)
     per = (time.perf_counter() - t) / (probe_n * probe_steps)
     m = int(max(threads, min(len(parts["x"]), core_seconds / (per * n_steps))))
     m = max(threads, (m // threads) * threads)
     sub = {k: v[:m] for k, v in parts.items()}
     t = time.perf_counter()
-    oracle.push(cfg["pulse"], sub, cfg["t0"], cfg["dt"], n_steps, grid=(grid_np, lo, hi), threads=threads)
+    oracle.push(pulse, sub, t0, dt, n_steps, grid=grid, threads=threads)
     wall = time.perf_counter() - t
     return m * n_steps / wall, m, wall
+
+
+class Workload:
+    """Device inputs and the step callable of one workload on this rank."""
+
+    def __init__(self, idx, args, rank):
+        import numpy as np
+        import torch
+        from paper_2307_04843_gb300 import _lib, shard, workloads
+        self.idx = idx
+        cfg = workloads.config(idx)
+        self.cfg = cfg
+        self.t0, self.dt = cfg["t0"], cfg["dt"]
+        self.n_steps = args.nsteps or cfg["n_steps"]
+        self.precision = cfg["precision"]
+        self.grid = None
+        self.grid_host = None
+        self.diag = None
+        self.graph = None
+        seed = shard.shard_seed(workloads.seed_for(idx), rank)
+        if idx == 5:
+            sets, counts = workloads.batch_sets(cfg)
+            if args.n:
+                counts = workloads.scaled_counts(counts, args.n)
+            off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+            self.n = int(off[-1])
+            self.parts = workloads.particles_uniform(cfg["box"], self.n, seed)
+            self.pulses = sets
+            self.h = _lib.Handle(sets)
+            self.off = torch.as_tensor(off).cuda()
+            self.off_host = off
+            self.ws = torch.zeros(_lib.ap_batch_workspace_bytes(self.h.h) // 4, dtype=torch.int32, device="cuda")
+            self.diag = dict(set_sum=torch.zeros(len(sets), dtype=torch.float64, device="cuda"))
+        else:
+            self.n = args.n or cfg["n"]
+            self.parts = workloads.particles(cfg, n=self.n, seed=seed)
+            self.pulses = [cfg["pulse"]]
+            self.h = _lib.Handle(cfg["pulse"])
+            if idx == 1:
+                self.diag = dict(lightfront=torch.zeros(self.n_steps, dtype=torch.float64, device="cuda"))
+            if idx == 3:
+                d = cfg["diag"]
+                self.diag = dict(hist=torch.zeros(d["hist_bins"], dtype=torch.int32, device="cuda"),
+                                 hist_lo=d["hist_lo"], hist_hi=d["hist_hi"])
+        if cfg.get("grid") is not None:
+            lo, hi = workloads.grid_box(cfg)
+            g = workloads.grid_field(cfg["box"], args.grid, torch_device="cuda")
+            self.grid = (g, lo, hi) if args.soa_grid else _lib.pack_grid((g, lo, hi))
+            self.grid_host = (g, lo, hi)
+        self.init = _lib.to_device(self.parts, self.precision)
+        self.work = {k: v.clone() for k, v in self.init.items()}
+        self.tuned = None
+        if not args.no_autotune and idx != 5:
+            from paper_2307_04843_gb300 import autotune
+            cache = os.path.join(ROOT, "gpurun_out", "autotune.json") if os.path.isdir(
+                os.path.join(ROOT, "gpurun_out")) else None
+            self.tuned = autotune.tune(self.h, self.init, self.t0, self.dt, self.precision, self.grid,
+                                       sample_n=min(self.n, 2_000_000), sample_steps=min(self.n_steps, 200),
+                                       cache_path=cache)
+        if idx == 5:
+            self.stream = torch.cuda.Stream()
+            self.graph = _lib.ap_batch_graph_create(self.h.h, self.work, self.off, None, self.t0, self.dt,
+                                                    self.n_steps, self.precision, self.diag, self.ws,
+                                                    self.stream)
+
+    def restore(self):
+        for k in self.work:
+            self.work[k].copy_(self.init[k], non_blocking=True)
+
+    def push(self):
+        import torch
+        from paper_2307_04843_gb300 import _lib
+        if self.graph is not None:
+            cur = torch.cuda.current_stream()
+            self.stream.wait_stream(cur)
+            _lib.ap_graph_launch(self.graph, self.stream)
+            cur.wait_stream(self.stream)
+        else:
+            self.h.push(self.work, self.t0, self.dt, self.n_steps, precision=self.precision, grid=self.grid,
+                        diag=self.diag)
+
+    def close(self):
+        from paper_2307_04843_gb300 import _lib
+        if self.graph is not None:
+            _lib.ap_graph_destroy(self.graph)
+            self.graph = None
+        self.h.close()
+
+
+def describe(wl, args):
+    c = wl.cfg
+    names = {1: "plane-fp64: LP plane wave a0=1, sin^2 10 cycles, 1e4 e- at rest, FP64",
+             2: "gauss-grid: paraxial Gaussian w0=3 lambda a0=10 FWHM 30 + longitudinal, "
+                "256^3 FP32 grid, float-float phase",
+             3: "ics-lg12: CP LG_{1,2} w0=2 lambda a0=20 sin^2 20 cycles, gamma~1000 beam, "
+                "1024-bin gamma histogram, float-float phase",
+             4: "flying-focus: 64 Gaussian spectral components, v_f=0.99, a0=5, float-float phase",
+             5: "batched-gauss: 256 Gaussian sets, log-uniform counts, one persistent launch in a CUDA graph, "
+                "per-set mean gamma, float-float phase"}
+    cfg = {"workload": names[wl.idx], "particles_per_gpu": wl.n, "boris_steps_per_call": wl.n_steps,
+           "dt": c["dt"], "l2": "inputs larger than L2 (36 B/particle state%s); no flush" %
+           (", 402 MB grid + 537 MB node-interleaved copy" if wl.grid is not None else ""),
+           "parallelism": "dp%d (independent shards)" % dist_info()[0]}
+    if wl.grid is not None:
+        cfg["grid"] = args.grid
+        cfg["grid_layout"] = "six component arrays" if args.soa_grid else "node-interleaved (ap_grid_pack)"
+    if wl.tuned:
+        cfg["launch"] = {"block": wl.tuned["block"], "blocks_per_sm": wl.tuned["blocks_per_sm"],
+                         "autotuned": True}
+    return cfg
 
 
 # ---------------------------------------------------------------- our arm
 
 def run_ours(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_2307_04843_gb300 import _lib, workloads
+    from paper_2307_04843_gb300 import _lib, shard
 
     ws, rank, local = dist_info()
-    if ws != args.gpus and args.gpus != 1:
-        pass
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    cfg = workloads.config(2)
-    n = args.n or cfg["n"]
-    n_steps = args.nsteps or cfg["n_steps"]
-    t0, dt = cfg["t0"], cfg["dt"]
-    parts = workloads.particles(cfg, n=n, seed=workloads.seed_for(2) + 7919 * rank)
-    lo, hi = workloads.grid_box(cfg)
-    grid = workloads.grid_field(cfg["box"], args.grid, torch_device="cuda")
+    wl = Workload(args.workload, args, rank)
     stream = torch.cuda.current_stream()
 
-    h = _lib.Handle(cfg["pulse"])
-    init = _lib.to_device(parts, "fp32")
-    work = {k: v.clone() for k, v in init.items()}
-    g = (grid, lo, hi)
-
-    def step():
-        for k in work:
-            work[k].copy_(init[k], non_blocking=True)
-        h.push(work, t0, dt, n_steps, precision="fp32", grid=g)
-
     for _ in range(args.warmup):
-        step()
+        wl.restore()
+        wl.push()
     torch.cuda.synchronize()
-    if h.status() != 0:
-        raise RuntimeError("device status after warm-up: %d" % h.status())
+    st = wl.h.status()
+    if st != 0:
+        raise RuntimeError("device status after warm-up: %d" % st)
 
     clocks = ClockSampler(local)
     if ws > 1:
@@ -199,10 +308,9 @@ def run_ours(args):
            for _ in range(args.steps)]
     e0.record(stream)
     for k in range(args.steps):
-        for kk in work:
-            work[kk].copy_(init[kk], non_blocking=True)
+        wl.restore()
         kev[k][0].record(stream)
-        h.push(work, t0, dt, n_steps, precision="fp32", grid=g)
+        wl.push()
         kev[k][1].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -212,29 +320,28 @@ def run_ours(args):
     elapsed = e0.elapsed_time(e1) / 1e3
     kern = sum(a.elapsed_time(b) for a, b in kev) / 1e3 / args.steps
     tt = torch.tensor([elapsed, kern], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    shard.reduce_max(tt)
     elapsed, kern = float(tt[0]), float(tt[1])
-    status = h.status()
+    status = wl.h.status()
     if status != 0:
         raise RuntimeError("device status after timed steps: %d" % status)
-    units = float(n) * n_steps * args.steps * ws
+    units_rank = float(wl.n) * wl.n_steps
+    units = units_rank * args.steps * ws
     value = units / elapsed
 
     # end to end through the public API from pinned host buffers
     e2e = None
-    if not args.no_e2e:
-        host = {k: v.cpu().pin_memory() for k, v in init.items()}
+    if not args.no_e2e and wl.graph is None:
+        host = {k: v.cpu().pin_memory() for k, v in wl.init.items()}
         out = {k: torch.empty_like(v).pin_memory() for k, v in host.items()}
-        dev = {k: torch.empty_like(v) for k, v in init.items()}
         h2d = sum(v.numel() * v.element_size() for v in host.values())
 
         def e2e_step():
-            for k in dev:
-                dev[k].copy_(host[k], non_blocking=True)
-            h.push(dev, t0, dt, n_steps, precision="fp32", grid=g)
-            for k in dev:
-                out[k].copy_(dev[k], non_blocking=True)
+            for k in wl.work:
+                wl.work[k].copy_(host[k], non_blocking=True)
+            wl.push()
+            for k in wl.work:
+                out[k].copy_(wl.work[k], non_blocking=True)
 
         e2e_step()
         torch.cuda.synchronize()
@@ -247,67 +354,95 @@ def run_ours(args):
         b.record(stream)
         torch.cuda.synchronize()
         te = torch.tensor([a.elapsed_time(b) / 1e3], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        shard.reduce_max(te)
         e2e = {"value": units / float(te[0]), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(h2d)}
 
     # comparison variants on one GPU: native-FP64-phase and plain FP64 paths
     variants = {}
-    if rank == 0 and not args.no_variants:
-        for prec, nv, sv in (("fp32_phase64", min(n, 2_000_000), n_steps), ("fp64", min(n, 500_000), n_steps)):
-            sub = {k: v[:nv] for k, v in parts.items()}
+    if rank == 0 and not args.no_variants and args.workload in (2, 3, 4):
+        for prec, nv in (("fp32_phase64", min(wl.n, 2_000_000)), ("fp64", min(wl.n, 500_000))):
+            if args.workload == 4:
+                nv = max(1, nv // 16)
+            sub = {k: v[:nv] for k, v in wl.parts.items()}
             d0 = _lib.to_device(sub, prec)
             d1 = {k: v.clone() for k, v in d0.items()}
-            h.push(d1, t0, dt, 200, precision=prec, grid=g)
+            wl.h.set_launch(0, 0)
+            wl.h.push(d1, wl.t0, wl.dt, 100, precision=prec, grid=wl.grid)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            h.push(d0, t0, dt, sv, precision=prec, grid=g)
+            wl.h.push(d0, wl.t0, wl.dt, wl.n_steps, precision=prec, grid=wl.grid)
             b.record(stream)
             torch.cuda.synchronize()
             sec = a.elapsed_time(b) / 1e3
-            variants[prec] = {"value": nv * sv / sec, "unit": UNIT,
-                              "sample": "%d particles x %d steps, one call" % (nv, sv)}
+            variants[prec] = {"value": nv * wl.n_steps / sec, "unit": UNIT,
+                              "sample": "%d particles x %d steps, one call" % (nv, wl.n_steps)}
         for prec in variants:
-            variants[prec]["fp32_speedup"] = (units / ws / args.steps / kern) / variants[prec]["value"]
+            variants[prec]["fp32_speedup"] = (units_rank / kern) / variants[prec]["value"]
+
+    # the adjoint of the batched workload: forward + reverse sweep
+    adjoint = None
+    if rank == 0 and args.workload == 5:
+        from paper_2307_04843_gb300.autograd import adjoint as run_adjoint
+        run_adjoint(wl.pulses, wl.init, wl.off, wl.t0, wl.dt, 200, ckpt_every=100, precision="fp32")
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        run_adjoint(wl.pulses, wl.init, wl.off, wl.t0, wl.dt, wl.n_steps,
+                    ckpt_every=wl.cfg["ckpt_every"], precision="fp32")
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        adjoint = {"value": units_rank / sec, "unit": UNIT, "seconds": sec,
+                   "vs_forward": sec / kern, "ckpt_every": wl.cfg["ckpt_every"]}
 
     # CPU oracle baseline on rank 0 (bounded sample of the same workload)
     cpu = None
     if rank == 0 and not args.no_cpu:
         threads = os.cpu_count() or 1
-        rate, m, wall = oracle_rate(cfg, parts, grid.cpu().numpy(), lo, hi, n_steps, args.cpu_seconds, threads)
+        g_np = None
+        if wl.grid_host is not None:
+            g_np = (wl.grid_host[0].cpu().numpy(), wl.grid_host[1], wl.grid_host[2])
+        rate, m, wall = oracle_rate(wl.pulses[0], wl.parts, wl.t0, wl.dt, wl.n_steps, args.cpu_seconds,
+                                    threads, grid=g_np)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": "first %d particles of the workload x %d steps (%.1f s wall)" % (m, n_steps, wall)}
+               "sample": "first %d particles of the workload x %d steps (%.1f s wall)" % (m, wl.n_steps, wall)}
 
-    # roofline of the push kernel (FP32 pipe)
-    sm_mhz = SM_MAX_MHZ
-    peak_ops = SM_COUNT * FP32_LANES * sm_mhz * 1e6 / 1e12  # TOP/s
-    achieved = ALGO_FP32_OPS * (float(n) * n_steps / kern) / 1e12
-    roofline = {"bound": "alu", "pipe": "fp32", "achieved": achieved, "peak": peak_ops, "unit": "TOP/s",
-                "frac": achieved / peak_ops, "traffic": None,
-                "algo_ops_per_particle_step": ALGO_FP32_OPS, "kernel_ms": kern * 1e3,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock)"}
-    if ck and ck.get("sm_mhz"):
-        roofline["frac_at_sampled_clock"] = achieved / (SM_COUNT * FP32_LANES * ck["sm_mhz"] * 1e6 / 1e12)
-        roofline["mufu_frac"] = (ALGO_MUFU_OPS * float(n) * n_steps / kern) / (SM_COUNT * MUFU_LANES * sm_mhz * 1e6)
+    # roofline of the push kernel
+    al = ALGO[args.workload]
+    rate_k = units_rank / kern
+    if args.workload == 1:
+        roofline = {"bound": "fp64", "note": "1e4 threads: latency-bound, FP64 path", "achieved": None,
+                    "peak": None, "unit": None, "frac": None, "traffic": None, "kernel_ms": kern * 1e3}
+    else:
+        peak_ops = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12  # TOP/s
+        achieved = al["fp32"] * rate_k / 1e12
+        traffic = None
+        if args.workload == 2 and TRAFFIC_PER_PARTICLE_STEP is not None and not args.soa_grid:
+            traffic = TRAFFIC_PER_PARTICLE_STEP * units_rank
+        roofline = {"bound": "alu", "pipe": "fp32", "achieved": achieved, "peak": peak_ops, "unit": "TOP/s",
+                    "frac": achieved / peak_ops, "traffic": traffic,
+                    "algo_ops_per_particle_step": al["fp32"], "kernel_ms": kern * 1e3,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock), of derived peak",
+                    "mufu_frac": al["mufu"] * rate_k / (SM_COUNT * MUFU_LANES * SM_MAX_MHZ * 1e6)}
+        if ck and ck.get("sm_mhz"):
+            roofline["frac_at_sampled_clock"] = achieved / (SM_COUNT * FP32_LANES * ck["sm_mhz"] * 1e6 / 1e12)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.precision == "fp64" else "f32",
         "data": "synthetic (seeded PCG64 particles and grid)",
-        "config": {"workload": "gauss-grid: paraxial Gaussian w0=3 lambda a0=10 FWHM 30 + longitudinal, "
-                               "256^3 FP32 grid, float-float phase",
-                   "particles_per_gpu": n, "boris_steps_per_call": n_steps, "dt": dt, "grid": args.grid,
-                   "l2": "inputs larger than L2 (36 B/particle state, 402 MB grid); no flush",
-                   "parallelism": "dp%d (independent shards)" % ws},
+        "config": describe(wl, args),
         "gpu_launches": args.steps,
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": ck, "variants": variants,
     }
+    if adjoint is not None:
+        line["adjoint"] = adjoint
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
+    wl.close()
     if ws > 1:
         dist.destroy_process_group()
 
@@ -316,7 +451,7 @@ def run_ours(args):
 
 def run_reference(args):
     """The CPU oracle as it stands, on the host cores, same workload and
-    metric; each step is a bounded sample of particles over all 4000 steps."""
+    metric; each step is a bounded sample of particles over all steps."""
     ws, rank, _ = dist_info()
     if rank != 0:
         return
@@ -325,10 +460,9 @@ def run_reference(args):
     cfg = workloads.config(2)
     n_steps = args.nsteps or cfg["n_steps"]
     lo, hi = workloads.grid_box(cfg)
-    grid = workloads.grid_field(cfg["box"], args.grid)
+    grid = workloads.grid_field(cfg["box"], args.grid, torch_device="cpu").numpy()
     threads = os.cpu_count() or 1
     parts = workloads.particles(cfg, n=4096)
-    # size one step to ~ (cpu_seconds / (steps + warmup)) core-seconds
     probe = {k: v[:8] for k, v in parts.items()}
     t = time.perf_counter()
     oracle.push(cfg["pulse"], probe, cfg["t0"], cfg["dt"], 100, grid=(grid, lo, hi))
@@ -351,7 +485,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded PCG64 particles and grid)",
         "config": {"workload": "gauss-grid: paraxial Gaussian w0=3 lambda a0=10 FWHM 30 + longitudinal, "
-                               "256^3 FP32 grid (CPU FP64 oracle)",
+                               "%d^3 FP32 grid (CPU FP64 oracle)" % args.grid,
                    "particles_per_step": m, "boris_steps_per_call": n_steps, "grid": args.grid},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "first %d particles of the workload x %d steps per step" % (m, n_steps)},
@@ -366,7 +500,7 @@ def main():
         run_reference(args)
     else:
         from paper_2307_04843_gb300 import build
-        if not os.path.exists(build.LIB):
+        if not build.up_to_date():
             build.build()
         run_ours(args)
 

@@ -141,11 +141,17 @@ typedef struct {
 /* Static node-centred grid field E2/B2 (Eqs. E_2, Sec. 2.1), device memory,
  * caller-owned.  Six float arrays f[0..5] = Ex, Ey, Ez, Bx, By, Bz, each
  * [nz][ny][nx] with x fastest; nodes at lo + i (hi - lo)/(n - 1).  Positions
- * outside [lo, hi] are clamped to the box.  n >= 2 along every axis. */
+ * outside [lo, hi] are clamped to the box.  n >= 2 along every axis; the
+ * f[] arrays need 4-byte alignment, `packed` 16-byte alignment.
+ * `packed` (nullable) is a node-interleaved copy made by ap_grid_pack,
+ * [nz][ny][nx][8] floats (Ex, Ey, Ez, Bx, By, Bz, 0, 0: one 32-byte sector
+ * per node); when set, the push reads it instead of f[] (which may then be
+ * NULL) and a cell refetch touches 8 sectors instead of 24. */
 typedef struct {
   const float *f[6];
   int32_t nx, ny, nz;
   double lo[3], hi[3];
+  const float *packed;
 } ap_grid;
 
 /* Optional diagnostics, device memory, caller-owned; every pointer nullable.
@@ -192,6 +198,15 @@ int ap_init_pulse(const ap_pulse_desc *descs, int32_t n_sets, ap_handle *out);
 
 /* Releases the handle and its device buffers (synchronises the device). */
 void ap_destroy(ap_handle h);
+
+/* Bytes of the node-interleaved grid copy (32 per node), 0 for a bad grid. */
+size_t ap_grid_packed_bytes(const ap_grid *g);
+
+/* Writes the node-interleaved copy of g->f[] into `packed` (device,
+ * caller-owned, ap_grid_packed_bytes(g) bytes, 16-byte aligned) on `stream`.
+ * The gathered values are those of Sec. 2.1's grid field, only the layout
+ * differs.  Errors: AP_ERR_ARG, AP_ERR_ALIGN, AP_ERR_CUDA. */
+int ap_grid_pack(const ap_grid *g, float *packed, void *stream);
 
 /* Sets the launch shape used by later calls on this handle (NULL restores
  * the defaults).  Errors: AP_ERR_ARG for an invalid shape. */

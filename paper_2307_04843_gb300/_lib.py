@@ -60,6 +60,7 @@ class ApGrid(ctypes.Structure):
     _fields_ = [
         ("f", ctypes.c_void_p * 6), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
         ("nz", ctypes.c_int32), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+        ("packed", ctypes.c_void_p),
     ]
 
 
@@ -83,6 +84,8 @@ SIGNATURES = {
     "ap_init_pulse": (ctypes.c_int, [ctypes.POINTER(ApPulseDesc), ctypes.c_int32, ctypes.POINTER(_vp)]),
     "ap_destroy": (None, [_vp]),
     "ap_set_launch": (ctypes.c_int, [_vp, ctypes.POINTER(ApLaunchCfg)]),
+    "ap_grid_packed_bytes": (ctypes.c_size_t, [ctypes.POINTER(ApGrid)]),
+    "ap_grid_pack": (ctypes.c_int, [ctypes.POINTER(ApGrid), _vp, _vp]),
     "ap_eval_fields": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int64, _vp, ctypes.c_int32, _vp]),
     "ap_gather_push": (ctypes.c_int, [_vp, ctypes.POINTER(ApParticles), ctypes.POINTER(ApGrid),
                                       ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
@@ -210,11 +213,13 @@ def particles_struct(p, precision, set_offsets=None):
 
 
 def grid_struct(grid):
-    """ap_grid from (tensor [6, nz, ny, nx] float32 CUDA, lo, hi) or None."""
+    """ap_grid from (tensor [6, nz, ny, nx] float32 CUDA, lo, hi[, packed]) or
+    None; `packed` is the node-interleaved copy made by ``pack_grid``."""
     if grid is None:
         return None
     import torch
-    g, lo, hi = grid
+    g, lo, hi = grid[:3]
+    packed = grid[3] if len(grid) > 3 else None
     if g.dtype != torch.float32 or not g.is_cuda or not g.is_contiguous() or g.dim() != 4 or g.shape[0] != 6:
         raise ValueError("grid must be a contiguous CUDA float32 tensor [6, nz, ny, nx]")
     s = ApGrid()
@@ -224,7 +229,30 @@ def grid_struct(grid):
     for a in range(3):
         s.lo[a] = float(lo[a])
         s.hi[a] = float(hi[a])
+    if packed is not None:
+        if packed.dtype != torch.float32 or not packed.is_cuda or packed.numel() * 4 != ap_grid_packed_bytes(s):
+            raise ValueError("packed grid must be the CUDA float32 tensor made by pack_grid")
+        s.packed = packed.data_ptr()
     return s
+
+
+def ap_grid_packed_bytes(gs):
+    return lib().ap_grid_packed_bytes(ctypes.byref(gs))
+
+
+def ap_grid_pack(grid, packed, stream=None):
+    gs = grid_struct(grid[:3])
+    check("ap_grid_pack", lib().ap_grid_pack(ctypes.byref(gs), _ptr(packed), _stream(stream)))
+
+
+def pack_grid(grid, stream=None):
+    """Node-interleaved copy of a grid (g, lo, hi); returns (g, lo, hi, packed)."""
+    import torch
+    g, lo, hi = grid[:3]
+    gs = grid_struct((g, lo, hi))
+    packed = torch.empty(ap_grid_packed_bytes(gs) // 4, dtype=torch.float32, device=g.device)
+    ap_grid_pack((g, lo, hi), packed, stream)
+    return (g, lo, hi, packed)
 
 
 def diag_struct(diag):

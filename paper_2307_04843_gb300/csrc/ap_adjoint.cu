@@ -1,23 +1,519 @@
-// ap_adjoint.cu -- discrete adjoint of the gather + push (row a13).
+// ap_adjoint.cu -- discrete adjoint of the gather + Boris push (row a13).
+//
+// Objective per set s: J_s = (1/N_s) sum_{i in s} gamma_i(T).  Gradients with
+// respect to the pulse parameters theta = (a0, w0, z_f) of every set, by the
+// exact reverse of the discrete forward map (the same float-float or double
+// arithmetic as ap_gather_push):
+//
+//   forward:  x^{n+1} = x^n + dt u^{n+1}/gamma^{n+1},  u^{n+1} = Boris(u^n, E(x^n), B(x^n))
+//   reverse:  lu'  = lu^{n+1} + dt/gamma' (lx - v' (v'.lx))         (position update)
+//             (lu^n, lE, lB) = Boris^T(lu')                          (hand-written VJP)
+//             lx^n = lx^{n+1} + (dF/dx)^T (lE, lB),  g += (dF/dtheta)^T (lE, lB)
+//
+// with seed lu^N = u^N / (gamma^N N_s), lx^N = 0.  dF/dx and dF/dtheta come
+// from the field functions instantiated with forward-mode dual numbers
+// seeded in (x, y, z - z_f, w0); a0 enters linearly (dF/da0 = F / a0) and
+// z_f only through z - z_f (dF/dz_f = -dF/dz for the analytic part).
+//
+// Memory: one persistent launch; every resident thread slot pushes its
+// particle forward storing a checkpoint every K steps, then sweeps the
+// segments backwards, recomputing each from its checkpoint into a per-slot
+// tape.  Checkpoints and tapes live in the caller's workspace, sized by the
+// number of resident thread slots, not by the number of particles.
 #include <cuda_runtime.h>
 
-#include "ap_internal.h"
+#include <cstring>
+
+#include "ap_dual.cuh"
+#include "ap_kernels.cuh"
+
+namespace apt {
+
+constexpr int kAdjBlock = 128;
+constexpr int kAdjBlocksPerSm = 4;
+constexpr int kAdjMaxK = 256;
+constexpr int kAdjStateBytes = 48;  // one saved state: 6 doubles or 9 floats
+using D4f = Dual<float, 4>;
+
+// Pulse view with the w0-dependent constants as duals (tangent slot 3).
+template <typename R>
+struct PulseAD {
+  int32_t kind, pol, env, lon, lg_p, lg_al, lg_sgn, sg_order;
+  R amp, bratio, lonE, lonB, env_a, env_b, px_re, px_im, py_re, py_im;
+  R lg_c[kLgMaxP + 1];
+  Dual<R, 4> inv_w0sq, inv_zR, lg_pref;
+};
+
+template <typename R>
+__device__ __forceinline__ PulseAD<R> make_ad(const Pulse<R> &P) {
+  PulseAD<R> A;
+  A.kind = P.kind; A.pol = P.pol; A.env = P.env; A.lon = P.lon;
+  A.lg_p = P.lg_p; A.lg_al = P.lg_al; A.lg_sgn = P.lg_sgn; A.sg_order = P.sg_order;
+  A.amp = P.amp_unit;  // unit a0: the physical field is a0 times this one
+  A.bratio = P.bratio; A.lonE = P.lonE; A.lonB = P.lonB;
+  A.env_a = P.env_a; A.env_b = P.env_b;
+  A.px_re = P.px_re; A.px_im = P.px_im; A.py_re = P.py_re; A.py_im = P.py_im;
+  for (int i = 0; i <= kLgMaxP; ++i) A.lg_c[i] = P.lg_c[i];
+  const R iw = P.inv_w0;
+  // d(1/w0^2)/dw0 = -2/w0^3; z_R ~ w0^2; (sqrt2/w0)^|l| ~ w0^-|l|
+  A.inv_w0sq = Dual<R, 4>::seed(P.inv_w0sq, 3, R(-2) * P.inv_w0sq * iw);
+  A.inv_zR = Dual<R, 4>::seed(P.inv_zR, 3, R(-2) * P.inv_zR * iw);
+  A.lg_pref = Dual<R, 4>::seed(P.lg_pref, 3, -R(P.lg_al) * P.lg_pref * iw);
+  return A;
+}
+
+// Saved particle state (checkpoints and tape), strided by thread slot.
+template <int PREC>
+struct StateIO;
+
+template <>
+struct StateIO<AP_FP32_PHASEFF> {
+  static constexpr int W = 9;
+  __device__ static void put(float *base, size_t stride, const Pos<AP_FP32_PHASEFF> &p,
+                             const float u[3]) {
+    base[0 * stride] = p.x.hi; base[1 * stride] = p.x.lo;
+    base[2 * stride] = p.y.hi; base[3 * stride] = p.y.lo;
+    base[4 * stride] = p.z.hi; base[5 * stride] = p.z.lo;
+    base[6 * stride] = u[0]; base[7 * stride] = u[1]; base[8 * stride] = u[2];
+  }
+  __device__ static void get(const float *base, size_t stride, Pos<AP_FP32_PHASEFF> &p, float u[3]) {
+    p.x.hi = base[0 * stride]; p.x.lo = base[1 * stride];
+    p.y.hi = base[2 * stride]; p.y.lo = base[3 * stride];
+    p.z.hi = base[4 * stride]; p.z.lo = base[5 * stride];
+    u[0] = base[6 * stride]; u[1] = base[7 * stride]; u[2] = base[8 * stride];
+  }
+  using T = float;
+};
+
+template <>
+struct StateIO<AP_FP64> {
+  static constexpr int W = 6;
+  __device__ static void put(double *base, size_t stride, const Pos<AP_FP64> &p, const double u[3]) {
+    base[0 * stride] = p.x; base[1 * stride] = p.y; base[2 * stride] = p.z;
+    base[3 * stride] = u[0]; base[4 * stride] = u[1]; base[5 * stride] = u[2];
+  }
+  __device__ static void get(const double *base, size_t stride, Pos<AP_FP64> &p, double u[3]) {
+    p.x = base[0 * stride]; p.y = base[1 * stride]; p.z = base[2 * stride];
+    u[0] = base[3 * stride]; u[1] = base[4 * stride]; u[2] = base[5 * stride];
+  }
+  using T = double;
+};
+
+struct AdjArgs {
+  PushArgs base;              // particles (read only), grid, t0, dt, n_steps, status
+  const long long *set_offsets;  // nullptr: one set [0, n)
+  int n_sets;
+  int K;                      // steps per segment
+  int n_seg;
+  unsigned int *tile_counter;
+  void *ckpt;                 // [n_seg][W][nslots]
+  void *tape;                 // [K][W][nslots]
+  long long nslots;
+  double *dJ;                 // [n_sets][AP_NPARAM]
+  double *J;                  // [n_sets] or null
+};
+
+template <typename R>
+struct GridGrad {
+  R v[6];
+  R g[6][3];
+};
+
+// Trilinear value and gradient from the cached cell (zero gradient along an
+// axis on which the position is clamped to the box).
+template <typename R>
+__device__ __forceinline__ void grid_value_grad(const GridView &g, GridCache<R> &gc, R x, R y, R z,
+                                                GridGrad<R> &out) {
+  R E[3] = {R(0), R(0), R(0)}, B[3] = {R(0), R(0), R(0)};
+  grid_gather<R>(g, gc, x, y, z, E, B);  // refreshes the cache for this cell
+  R lo[3], idd[3];
+  if constexpr (std::is_same<R, double>::value) {
+    for (int a = 0; a < 3; ++a) { lo[a] = g.lo_d[a]; idd[a] = g.inv_d_d[a]; }
+  } else {
+    for (int a = 0; a < 3; ++a) { lo[a] = g.lo[a]; idd[a] = g.inv_d[a]; }
+  }
+  const R fxr = (x - lo[0]) * idd[0], fyr = (y - lo[1]) * idd[1], fzr = (z - lo[2]) * idd[2];
+  const R fx = fmin(fmax(fxr, R(0)), R(g.nx - 1)), fy = fmin(fmax(fyr, R(0)), R(g.ny - 1)),
+          fz = fmin(fmax(fzr, R(0)), R(g.nz - 1));
+  const R wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
+  const R sx = (fxr == fx) ? idd[0] : R(0), sy = (fyr == fy) ? idd[1] : R(0),
+          sz = (fzr == fz) ? idd[2] : R(0);
+  out.v[0] = E[0]; out.v[1] = E[1]; out.v[2] = E[2];
+  out.v[3] = B[0]; out.v[4] = B[1]; out.v[5] = B[2];
+  for (int c = 0; c < 6; ++c) {
+    const R *k = gc.c[c];
+    // f = c0 + wx (c1 + wy (c4 + wz c7) + wz c5) + wy (c2 + wz c6) + wz c3
+    R dfx = k[1] + wy * (k[4] + wz * k[7]) + wz * k[5];
+    R dfy = k[2] + wz * k[6] + wx * (k[4] + wz * k[7]);
+    R dfz = k[3] + wx * (k[5] + wy * k[7]) + wy * k[6];
+    out.g[c][0] = dfx * sx;
+    out.g[c][1] = dfy * sy;
+    out.g[c][2] = dfz * sz;
+  }
+}
+
+template <int KIND, typename R>
+__device__ __forceinline__ void fields_ad(const PulseAD<R> &A, const Local<Dual<R, 4>> &L,
+                                          Dual<R, 4> E[3], Dual<R, 4> B[3]) {
+  if constexpr (KIND == AP_PLANE) fields_plane(A, L, E, B);
+  else if constexpr (KIND == AP_GAUSS) fields_gauss(A, L, E, B);
+  else fields_lg(A, L, E, B);
+}
+
+// One reverse step.  State before the step (pos, u), step value st, adjoints
+// lx, lu of the state after the step (updated in place to the state before),
+// gradient accumulators g[0..2] = d/d(a0, w0, z_f).
+template <int KIND, int PREC, bool GRID>
+__device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P, const PulseAD<Real<PREC>> &A,
+                                             const AdjArgs &aa, const typename TimeBase<PREC>::Step &st,
+                                             const Pos<PREC> &pos, const Real<PREC> u[3],
+                                             Real<PREC> lx[3], Real<PREC> lu[3], Real<PREC> g[3],
+                                             GridCache<Real<PREC>> &gc) {
+  using R = Real<PREC>;
+  using DR = Dual<R, 4>;
+  const R dt = (R)aa.base.dt;
+  const R h = R(-0.5) * dt;
+  const R a0 = P.a0;
+  // fields with derivatives in (x, y, z - z_f, w0)
+  Local<R> L = local_coords<PREC>(P, st, pos);
+  Local<DR> LD;
+  LD.x = DR::seed(L.x, 0);
+  LD.y = DR::seed(L.y, 1);
+  LD.dz = DR::seed(L.dz, 2);
+  LD.psi = DR(L.psi);
+  LD.psi.d[2] = -R(P.k);  // psi = C - k (z - z_f)
+  LD.eta = DR(L.eta);
+  LD.eta.d[2] = -P.inv_vg;  // eta = T - (z - z_f) / v_g
+  LD.phi_hi = DR(R(0));
+  LD.phi_lo = DR(R(0));
+  DR Ed[3], Bd[3];
+  fields_ad<KIND, R>(A, LD, Ed, Bd);
+  R F[6], dFx[6][3], dFth[6][3];  // field, d/dx, d/d(a0, w0, z_f)
+  const DR *Fd[6] = {&Ed[0], &Ed[1], &Ed[2], &Bd[0], &Bd[1], &Bd[2]};
+  for (int c = 0; c < 6; ++c) {
+    const DR &f = *Fd[c];
+    F[c] = a0 * f.v;
+    dFx[c][0] = a0 * f.d[0];
+    dFx[c][1] = a0 * f.d[1];
+    dFx[c][2] = a0 * f.d[2];
+    dFth[c][0] = f.v;
+    dFth[c][1] = a0 * f.d[3];
+    dFth[c][2] = -a0 * f.d[2];
+  }
+  if constexpr (GRID) {
+    GridGrad<R> gg;
+    grid_value_grad<R>(aa.base.grid, gc, L.x, L.y, pos.zr(), gg);
+    for (int c = 0; c < 6; ++c) {
+      F[c] += gg.v[c];
+      for (int k = 0; k < 3; ++k) dFx[c][k] += gg.g[c][k];
+    }
+  }
+  const R E[3] = {F[0], F[1], F[2]}, B[3] = {F[3], F[4], F[5]};
+  // Boris forward intermediates
+  R am[3] = {fma(h, E[0], u[0]), fma(h, E[1], u[1]), fma(h, E[2], u[2])};
+  R ig = rsqrt_r(R(1) + am[0] * am[0] + am[1] * am[1] + am[2] * am[2]);
+  R tau[3] = {h * ig * B[0], h * ig * B[1], h * ig * B[2]};
+  R tt = tau[0] * tau[0] + tau[1] * tau[1] + tau[2] * tau[2];
+  R f = R(2) * rcp_r(R(1) + tt);
+  R s[3] = {f * tau[0], f * tau[1], f * tau[2]};
+  R p[3] = {am[0] + (am[1] * tau[2] - am[2] * tau[1]), am[1] + (am[2] * tau[0] - am[0] * tau[2]),
+            am[2] + (am[0] * tau[1] - am[1] * tau[0])};
+  R bq[3] = {am[0] + (p[1] * s[2] - p[2] * s[1]), am[1] + (p[2] * s[0] - p[0] * s[2]),
+             am[2] + (p[0] * s[1] - p[1] * s[0])};
+  R un[3] = {fma(h, E[0], bq[0]), fma(h, E[1], bq[1]), fma(h, E[2], bq[2])};
+  R ign = rsqrt_r(R(1) + un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
+  R v[3] = {un[0] * ign, un[1] * ign, un[2] * ign};
+  // position update: x' = x + dt u' / gamma'
+  R vl = v[0] * lx[0] + v[1] * lx[1] + v[2] * lx[2];
+  R ub[3];
+  for (int k = 0; k < 3; ++k) ub[k] = lu[k] + dt * ign * (lx[k] - v[k] * vl);
+  // Boris reverse
+  R Eb[3], Bb[3], ab[3], pb[3], sbar[3], tb[3];
+  for (int k = 0; k < 3; ++k) Eb[k] = h * ub[k];
+  // b = a + p x s
+  pb[0] = s[1] * ub[2] - s[2] * ub[1];
+  pb[1] = s[2] * ub[0] - s[0] * ub[2];
+  pb[2] = s[0] * ub[1] - s[1] * ub[0];
+  sbar[0] = ub[1] * p[2] - ub[2] * p[1];
+  sbar[1] = ub[2] * p[0] - ub[0] * p[2];
+  sbar[2] = ub[0] * p[1] - ub[1] * p[0];
+  // p = a + a x tau
+  ab[0] = ub[0] + pb[0] + (tau[1] * pb[2] - tau[2] * pb[1]);
+  ab[1] = ub[1] + pb[1] + (tau[2] * pb[0] - tau[0] * pb[2]);
+  ab[2] = ub[2] + pb[2] + (tau[0] * pb[1] - tau[1] * pb[0]);
+  tb[0] = pb[1] * am[2] - pb[2] * am[1];
+  tb[1] = pb[2] * am[0] - pb[0] * am[2];
+  tb[2] = pb[0] * am[1] - pb[1] * am[0];
+  // s = f tau, f = 2 / (1 + tau^2)
+  R ts = tau[0] * sbar[0] + tau[1] * sbar[1] + tau[2] * sbar[2];
+  for (int k = 0; k < 3; ++k) tb[k] += f * sbar[k] - f * f * tau[k] * ts;
+  // tau = h ig B
+  R igb = h * (B[0] * tb[0] + B[1] * tb[1] + B[2] * tb[2]);
+  for (int k = 0; k < 3; ++k) Bb[k] = h * ig * tb[k];
+  // ig = (1 + a^2)^(-1/2)
+  R c3 = -ig * ig * ig * igb;
+  for (int k = 0; k < 3; ++k) ab[k] += c3 * am[k];
+  for (int k = 0; k < 3; ++k) {
+    Eb[k] += h * ab[k];
+    lu[k] = ab[k];
+  }
+  // fields: position and parameter adjoints
+  const R Fb[6] = {Eb[0], Eb[1], Eb[2], Bb[0], Bb[1], Bb[2]};
+  for (int c = 0; c < 6; ++c) {
+    for (int k = 0; k < 3; ++k) lx[k] += Fb[c] * dFx[c][k];
+    for (int k = 0; k < 3; ++k) g[k] += Fb[c] * dFth[c][k];
+  }
+}
+
+template <int KIND, int PREC, bool GRID>
+__global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const Pulse<Real<PREC>> *__restrict__ sets,
+                                                            const __grid_constant__ AdjArgs aa) {
+  using R = Real<PREC>;
+  using IO = StateIO<PREC>;
+  using T = typename IO::T;
+  __shared__ long long s_tile;
+  __shared__ int s_set;
+  __shared__ double s_red[32];
+  __shared__ StepFF s_steps[kAdjMaxK];
+  __shared__ __align__(16) unsigned char s_pulse_raw[sizeof(Pulse<R>)];
+  __shared__ long long s_prefix[AP_MAX_SETS + 1];
+  Pulse<R> &P = *reinterpret_cast<Pulse<R> *>(s_pulse_raw);
+  const PushArgs &a = aa.base;
+  const int Tt = blockDim.x;
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    for (int s = 0; s < aa.n_sets; ++s) {
+      s_prefix[s] = acc;
+      long long ns = aa.set_offsets ? aa.set_offsets[s + 1] - aa.set_offsets[s] : a.n;
+      if (ns < 0) ns = 0;
+      acc += (ns + Tt - 1) / Tt;
+    }
+    s_prefix[aa.n_sets] = acc;
+    s_set = -1;
+  }
+  __syncthreads();
+  const long long total = s_prefix[aa.n_sets];
+  const size_t slot = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)aa.nslots;
+  T *ck = static_cast<T *>(aa.ckpt) + slot;
+  T *tp = static_cast<T *>(aa.tape) + slot;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(aa.tile_counter, 1u);
+    __syncthreads();
+    const long long tile = s_tile;
+    if (tile >= total) break;
+    int lo = 0, hi = aa.n_sets;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (s_prefix[mid] <= tile) lo = mid; else hi = mid;
+    }
+    const int set = lo;
+    if (set != s_set) {
+      const int words = (int)(sizeof(Pulse<R>) / 4);
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(sets + set);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(s_pulse_raw);
+      for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+      __syncthreads();
+      if (threadIdx.x == 0) s_set = set;
+    }
+    __syncthreads();
+    const long long off0 = aa.set_offsets ? aa.set_offsets[set] : 0;
+    const long long off1 = aa.set_offsets ? aa.set_offsets[set + 1] : a.n;
+    const long long i = off0 + (tile - s_prefix[set]) * Tt + threadIdx.x;
+    const bool valid = i >= 0 && i < off1 && i < a.n;
+    const double Ns = (double)(off1 - off0);
+    // ---- forward pass with checkpoints
+    Pos<PREC> pos;
+    R u[3] = {R(0), R(0), R(0)};
+    pos.load(valid ? a.x[i] : 0.0, valid ? a.y[i] : 0.0, valid ? a.z[i] : 0.0);
+    if (valid) {
+      u[0] = static_cast<const R *>(a.ux)[i];
+      u[1] = static_cast<const R *>(a.uy)[i];
+      u[2] = static_cast<const R *>(a.uz)[i];
+    }
+    TimeBase<PREC> tb;
+    tb.init(P, a.t0, a.dt);
+    const R dtR = (R)a.dt;
+    GridCache<R> gc;
+    grid_cache_reset(gc);
+    for (int seg = 0; seg < aa.n_seg; ++seg) {
+      const long long s0 = (long long)seg * aa.K;
+      const int cnt = (int)(a.n_steps - s0 < aa.K ? a.n_steps - s0 : aa.K);
+      IO::put(ck + (size_t)seg * IO::W * stride, stride, pos, u);
+      if constexpr (PREC == AP_FP32_PHASEFF) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) s_steps[k] = tb.at(s0 + k);
+        __syncthreads();
+      }
+      for (int k = 0; k < cnt; ++k) {
+        typename TimeBase<PREC>::Step st;
+        if constexpr (PREC == AP_FP32_PHASEFF) st = s_steps[k];
+        else st = tb.at(s0 + k);
+        Local<R> L = local_coords<PREC>(P, st, pos);
+        R E[3], B[3];
+        analytic_fields<KIND, PREC>(P, L, E, B);
+        if constexpr (GRID) grid_gather<R>(a.grid, gc, L.x, L.y, pos.zr(), E, B);
+        R ig = boris(u, E, B, dtR);
+        pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtR);
+      }
+    }
+    // ---- objective and seed
+    const double gN = sqrt(1.0 + (double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2]);
+    R lx[3] = {R(0), R(0), R(0)}, lu[3];
+    for (int k = 0; k < 3; ++k) lu[k] = valid ? (R)((double)u[k] / (gN * Ns)) : R(0);
+    double Jv = valid ? gN / Ns : 0.0;
+    double gacc[3] = {0.0, 0.0, 0.0};
+    const PulseAD<R> A = make_ad(P);
+    // ---- reverse sweep over segments
+    for (int seg = aa.n_seg - 1; seg >= 0; --seg) {
+      const long long s0 = (long long)seg * aa.K;
+      const int cnt = (int)(a.n_steps - s0 < aa.K ? a.n_steps - s0 : aa.K);
+      IO::get(ck + (size_t)seg * IO::W * stride, stride, pos, u);
+      if constexpr (PREC == AP_FP32_PHASEFF) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) s_steps[k] = tb.at(s0 + k);
+        __syncthreads();
+      }
+      for (int k = 0; k < cnt; ++k) {
+        IO::put(tp + (size_t)k * IO::W * stride, stride, pos, u);
+        typename TimeBase<PREC>::Step st;
+        if constexpr (PREC == AP_FP32_PHASEFF) st = s_steps[k];
+        else st = tb.at(s0 + k);
+        Local<R> L = local_coords<PREC>(P, st, pos);
+        R E[3], B[3];
+        analytic_fields<KIND, PREC>(P, L, E, B);
+        if constexpr (GRID) grid_gather<R>(a.grid, gc, L.x, L.y, pos.zr(), E, B);
+        R ig = boris(u, E, B, dtR);
+        pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtR);
+      }
+      R gs[3] = {R(0), R(0), R(0)};
+      for (int k = cnt - 1; k >= 0; --k) {
+        IO::get(tp + (size_t)k * IO::W * stride, stride, pos, u);
+        typename TimeBase<PREC>::Step st;
+        if constexpr (PREC == AP_FP32_PHASEFF) st = s_steps[k];
+        else st = tb.at(s0 + k);
+        reverse_step<KIND, PREC, GRID>(P, A, aa, st, pos, u, lx, lu, gs, gc);
+      }
+      for (int k = 0; k < 3; ++k) gacc[k] += (double)gs[k];
+    }
+    if (!valid) {
+      gacc[0] = gacc[1] = gacc[2] = 0.0;
+      Jv = 0.0;
+    } else if (!(isfinite(gacc[0]) && isfinite(gacc[1]) && isfinite(gacc[2]))) {
+      atomicOr(a.status, kStatusNonfinite);
+    }
+    // per-set reduction (every particle of the tile belongs to `set`)
+    for (int k = 0; k < 3; ++k) {
+      double t = block_sum(gacc[k], s_red);
+      if (threadIdx.x == 0) atomicAdd(aa.dJ + (size_t)set * AP_NPARAM + k, t);
+    }
+    if (aa.J) {
+      double t = block_sum(Jv, s_red);
+      if (threadIdx.x == 0) atomicAdd(aa.J + set, t);
+    }
+    __syncthreads();
+  }
+}
+
+template <int KIND, int PREC, bool GRID>
+int launch_adjoint_t(const Pulse<Real<PREC>> *sets, const AdjArgs &aa, int grid, void *stream) {
+  adjoint_kernel<KIND, PREC, GRID>
+      <<<grid, kAdjBlock, 0, static_cast<cudaStream_t>(stream)>>>(sets, aa);
+  return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+}
+
+template <int KIND>
+int launch_adjoint_k(int precision, const Pulse<double> *dpd, const Pulse<float> *dpf,
+                     const AdjArgs &aa, int grid, void *stream) {
+  const bool gr = aa.base.grid_on != 0;
+  if (precision == AP_FP64)
+    return gr ? launch_adjoint_t<KIND, AP_FP64, true>(dpd, aa, grid, stream)
+              : launch_adjoint_t<KIND, AP_FP64, false>(dpd, aa, grid, stream);
+  if (precision == AP_FP32_PHASEFF)
+    return gr ? launch_adjoint_t<KIND, AP_FP32_PHASEFF, true>(dpf, aa, grid, stream)
+              : launch_adjoint_t<KIND, AP_FP32_PHASEFF, false>(dpf, aa, grid, stream);
+  return AP_ERR_UNSUPPORTED;
+}
+
+}  // namespace apt
+
+// Host side: the handle internals live in ap_api.cu; these accessors expose
+// what the adjoint launch needs.
+namespace apt {
+int handle_info(ap_handle h, int *device, int *sm_count, int *n_sets, int *uniform_kind,
+                const Pulse<double> **dpd, const Pulse<float> **dpf, int **status);
+int handle_push_args(ap_handle h, const ap_particles *p, const ap_grid *g, double t0, double dt,
+                     int64_t n_steps, int32_t precision, PushArgs *a, void *stream);
+}  // namespace apt
+
+namespace {
+long long adj_slots(int sm_count) {
+  return (long long)sm_count * apt::kAdjBlocksPerSm * apt::kAdjBlock;
+}
+}  // namespace
 
 extern "C" {
 
 size_t ap_adjoint_workspace_bytes(ap_handle h, int64_t n, int64_t n_steps, int32_t ckpt_every) {
-  (void)h; (void)n; (void)n_steps; (void)ckpt_every;
-  return 0;
+  int dev, sm, ns, uk, *st;
+  const apt::Pulse<double> *pd;
+  const apt::Pulse<float> *pf;
+  if (!h || n < 0 || n_steps < 1 || ckpt_every < 1 || ckpt_every > apt::kAdjMaxK) return 0;
+  if (apt::handle_info(h, &dev, &sm, &ns, &uk, &pd, &pf, &st) != AP_OK) return 0;
+  const long long slots = adj_slots(sm);
+  const long long n_seg = (n_steps + ckpt_every - 1) / ckpt_every;
+  return 256 + (size_t)(n_seg + ckpt_every) * apt::kAdjStateBytes * (size_t)slots;
 }
 
 int ap_push_adjoint(ap_handle h, const ap_particles *p0, const ap_grid *g, double t0, double dt,
                     int64_t n_steps, int32_t ckpt_every, int32_t objective, int32_t precision,
                     double *dJ_dparams, double *J_out, void *workspace, size_t ws_bytes,
                     void *stream) {
-  (void)h; (void)p0; (void)g; (void)t0; (void)dt; (void)n_steps; (void)ckpt_every;
-  (void)objective; (void)precision; (void)dJ_dparams; (void)J_out; (void)workspace;
-  (void)ws_bytes; (void)stream;
-  return AP_ERR_UNSUPPORTED;
+  int dev, sm, ns, uk, *status;
+  const apt::Pulse<double> *dpd;
+  const apt::Pulse<float> *dpf;
+  if (!h || !p0 || !dJ_dparams) return AP_ERR_ARG;
+  int rc = apt::handle_info(h, &dev, &sm, &ns, &uk, &dpd, &dpf, &status);
+  if (rc != AP_OK) return rc;
+  if (objective != AP_OBJ_MEAN_GAMMA) return AP_ERR_ARG;
+  if (precision != AP_FP64 && precision != AP_FP32_PHASEFF) return AP_ERR_UNSUPPORTED;
+  if (uk < 0 || uk == AP_FLYING_SUM) return AP_ERR_UNSUPPORTED;
+  if (n_steps < 1 || ckpt_every < 1 || ckpt_every > apt::kAdjMaxK) return AP_ERR_ARG;
+  if (p0->set_offsets ? p0->n_sets != ns : ns != 1) return AP_ERR_ARG;
+  const size_t need = ap_adjoint_workspace_bytes(h, p0->n, n_steps, ckpt_every);
+  if (!workspace || ws_bytes < need) return AP_ERR_WORKSPACE;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return AP_ERR_ALIGN;
+  apt::AdjArgs aa;
+  std::memset(&aa, 0, sizeof(aa));
+  rc = apt::handle_push_args(h, p0, g, t0, dt, n_steps, precision, &aa.base, stream);
+  if (rc != AP_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(dJ_dparams, 0, sizeof(double) * AP_NPARAM * ns, s) != cudaSuccess ||
+      (J_out && cudaMemsetAsync(J_out, 0, sizeof(double) * ns, s) != cudaSuccess) ||
+      cudaMemsetAsync(workspace, 0, 256, s) != cudaSuccess)
+    return AP_ERR_CUDA;
+  if (p0->n == 0) return AP_OK;
+  const long long slots = adj_slots(sm);
+  const long long n_seg = (n_steps + ckpt_every - 1) / ckpt_every;
+  char *ws = static_cast<char *>(workspace);
+  const size_t w = (precision == AP_FP64) ? sizeof(double) * 6 : sizeof(float) * 9;
+  aa.set_offsets = reinterpret_cast<const long long *>(p0->set_offsets);
+  aa.n_sets = ns;
+  aa.K = ckpt_every;
+  aa.n_seg = (int)n_seg;
+  aa.tile_counter = reinterpret_cast<unsigned int *>(ws);
+  aa.ckpt = ws + 256;
+  aa.tape = ws + 256 + (size_t)n_seg * w * slots;
+  aa.nslots = slots;
+  aa.dJ = dJ_dparams;
+  aa.J = J_out;
+  const int grid = (int)(slots / apt::kAdjBlock);
+  switch (uk) {
+    case AP_PLANE: return apt::launch_adjoint_k<AP_PLANE>(precision, dpd, dpf, aa, grid, stream);
+    case AP_GAUSS: return apt::launch_adjoint_k<AP_GAUSS>(precision, dpd, dpf, aa, grid, stream);
+    case AP_LG: return apt::launch_adjoint_k<AP_LG>(precision, dpd, dpf, aa, grid, stream);
+    default: return AP_ERR_UNSUPPORTED;
+  }
 }
 
 }  // extern "C"

@@ -154,6 +154,9 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
   P.lonE = vphi / d.omega;
   P.lonB = 1.0 / d.omega;
   P.amp = d.a0;
+  P.a0 = d.a0;
+  P.amp_unit = 1.0;
+  P.inv_w0 = d.kind != AP_PLANE ? 1.0 / d.w0 : 0.0;
   if (d.kind != AP_PLANE) {
     P.inv_w0sq = 1.0 / (d.w0 * d.w0);
     P.inv_zR = 1.0 / (0.5 * k * d.w0 * d.w0);
@@ -188,7 +191,8 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
     P.lg_sgn = d.lg_l < 0 ? -1 : 1;
     laguerre_coeffs(d.lg_p, a, P.lg_c);
     P.lg_pref = std::pow(std::sqrt(2.0) / d.w0, (double)a);
-    P.amp = d.a0 / lg_peak(d.lg_p, a);
+    P.amp_unit = 1.0 / lg_peak(d.lg_p, a);
+    P.amp = d.a0 * P.amp_unit;
   }
   if (d.kind == AP_FLYING_SUM) {
     // Spectral components (Sec. 3.3, linear superposition): omega_j spread
@@ -223,6 +227,7 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
       best = std::max(best, std::abs(S));
     }
     const double A = d.a0 / best;
+    P.amp_unit = 1.0 / best;
     P.n_comp = n;
     P.ff_w = w[0];
     P.ff_dw = (w[n - 1] - w[0]) / (double)(n - 1);
@@ -251,6 +256,9 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
   F.py_re = (float)P.py_re; F.py_im = (float)P.py_im;
   for (int i = 0; i <= apt::kLgMaxP; ++i) F.lg_c[i] = (float)P.lg_c[i];
   F.lg_pref = (float)P.lg_pref;
+  F.a0 = (float)P.a0;
+  F.inv_w0 = (float)P.inv_w0;
+  F.amp_unit = (float)P.amp_unit;
   F.omega = P.omega; F.k = P.k; F.t_f = P.t_f; F.z_f = P.z_f; F.phase0 = P.phase0;
   F.ff_w = P.ff_w; F.ff_dw = P.ff_dw;
   for (int j = 0; j < P.n_comp; ++j) {
@@ -295,9 +303,13 @@ int make_grid(const ap_grid *g, apt::GridView &v) {
   if (!g) return AP_OK;
   if (g->nx < 2 || g->ny < 2 || g->nz < 2) return AP_ERR_ARG;
   const int n[3] = {g->nx, g->ny, g->nz};
+  if (g->packed) {
+    if (!aligned16(g->packed)) return AP_ERR_ALIGN;
+    v.packed = reinterpret_cast<const float4 *>(g->packed);
+  }
   for (int c = 0; c < 6; ++c) {
-    if (!g->f[c]) return AP_ERR_ARG;
-    if (!aligned16(g->f[c])) return AP_ERR_ALIGN;
+    if (!g->f[c] && !g->packed) return AP_ERR_ARG;
+    if (g->f[c] && (reinterpret_cast<uintptr_t>(g->f[c]) & 3u)) return AP_ERR_ALIGN;
     v.f[c] = g->f[c];
   }
   if ((double)g->nx * g->ny * g->nz > 2147483647.0) return AP_ERR_ARG;
@@ -382,6 +394,27 @@ int fill_push_args(ap_handle_s *h, const ap_particles *p, const ap_grid *g, doub
 }  // namespace
 
 namespace apt {
+
+// Accessors used by the adjoint translation unit.
+int handle_info(ap_handle h, int *device, int *sm_count, int *n_sets, int *uniform_kind,
+                const Pulse<double> **dpd, const Pulse<float> **dpf, int **status) {
+  if (!h) return AP_ERR_ARG;
+  int rc = current_device_matches(h);
+  if (rc != AP_OK) return rc;
+  *device = h->device;
+  *sm_count = h->sm_count;
+  *n_sets = h->n_sets;
+  *uniform_kind = h->uniform_kind;
+  *dpd = h->d_pd;
+  *dpf = h->d_pf;
+  *status = h->d_status;
+  return AP_OK;
+}
+
+int handle_push_args(ap_handle h, const ap_particles *p, const ap_grid *g, double t0, double dt,
+                     int64_t n_steps, int32_t precision, PushArgs *a, void *stream) {
+  return fill_push_args(h, p, g, t0, dt, n_steps, precision, nullptr, 1, *a, stream);
+}
 
 int launch_push(int kind, int precision, const Pulse<double> &pd, const Pulse<float> &pf,
                 const PushArgs &a, void *stream) {

@@ -63,11 +63,19 @@ constexpr float kTwoPiHi = 6.28318548202514648f;
 constexpr float kTwoPiLo = -1.74845553e-07f;
 constexpr float kInvTwoPi = 0.159154943091895336f;
 
+// Round to the nearest integer on the FP32 pipe: adding 1.5 * 2^23 forces
+// the unit in the last place to 1 (valid for |x| < 2^22), one FFMA/FADD and
+// one FADD instead of a conversion-pipe FRND.
+constexpr float kRoundMagic = 12582912.0f;
+__device__ __forceinline__ float round_fma(float a, float b) {
+  return __fsub_rn(__fmaf_rn(a, b, kRoundMagic), kRoundMagic);
+}
+
 // (hi + lo) reduced modulo 2 pi to about [-pi, pi], rounded to float.
 // m = rint(hi / 2 pi); hi - m P1 is exact (Sterbenz) with m P1 split by
 // TwoProd; the low-order parts are summed in float.
 __device__ __forceinline__ float reduce_ff(float hi, float lo) {
-  float m = rintf(__fmul_rn(hi, kInvTwoPi));
+  float m = round_fma(hi, kInvTwoPi);
   FF p = two_prod(m, kTwoPiHi);
   float r = __fsub_rn(hi, p.hi);
   float t = __fsub_rn(__fsub_rn(lo, p.lo), __fmul_rn(m, kTwoPiLo));
@@ -76,20 +84,53 @@ __device__ __forceinline__ float reduce_ff(float hi, float lo) {
 
 // float argument reduction for moderate |x| (a few times 2 pi).
 __device__ __forceinline__ float reduce_f(float x) {
-  float m = rintf(x * kInvTwoPi);
+  float m = round_fma(x, kInvTwoPi);
   x = fmaf(-m, kTwoPiHi, x);
   return fmaf(-m, kTwoPiLo, x);
 }
 
-__device__ __forceinline__ void sincos_r(float x, float *s, float *c) { __sincosf(x, s, c); }
+// Special-function unit (MUFU) instructions, written as PTX so that each is
+// one approximate hardware operation (documented maximum errors: sin/cos
+// 2^-20.9 absolute on [-pi, pi], ex2 2^-22.5 relative, rcp 1 ulp, rsqrt
+// 2^-22.9 relative); subnormal results flush to zero.
+__device__ __forceinline__ float mufu_sin(float x) {
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_cos(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_rsqrt(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void sincos_r(float x, float *s, float *c) {
+  *s = mufu_sin(x);
+  *c = mufu_cos(x);
+}
 __device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
-__device__ __forceinline__ float exp2_r(float x) { return exp2f(x); }
+__device__ __forceinline__ float exp2_r(float x) { return mufu_ex2(x); }
 __device__ __forceinline__ double exp2_r(double x) { return exp2(x); }
-__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float rsqrt_r(float x) { return mufu_rsqrt(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
-__device__ __forceinline__ float rcp_r(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float rcp_r(float x) { return mufu_rcp(x); }
 __device__ __forceinline__ double rcp_r(double x) { return 1.0 / x; }
-__device__ __forceinline__ float cos_r(float x) { return __cosf(x); }
+__device__ __forceinline__ float cos_r(float x) { return mufu_cos(x); }
 __device__ __forceinline__ double cos_r(double x) { return cos(x); }
 
 template <typename R>
@@ -154,13 +195,15 @@ struct Pos<AP_FP32_PHASEFF> {
     *Y = (double)y.hi + (double)y.lo;
     *Z = (double)z.hi + (double)z.lo;
   }
-  // TwoSum of the high part with the float increment; the rounding error
-  // goes to the low part (no renormalisation needed: |lo| stays far below
-  // ulp(hi) times the step count).
+  // Compensated (Kahan) accumulation of the float increment: the low part
+  // carries the rounding error of every add, so hi + lo is the exact sum of
+  // the increments to within O(2^-48) relative (Kahan 1965; the error term
+  // is exact whenever |hi| >= |increment|, the normal case).
   __device__ __forceinline__ static void acc(FF &p, float d) {
-    FF s = two_sum(p.hi, d);
-    p.hi = s.hi;
-    p.lo = __fadd_rn(p.lo, s.lo);
+    float y = __fadd_rn(d, p.lo);
+    float t = __fadd_rn(p.hi, y);
+    p.lo = __fsub_rn(y, __fsub_rn(t, p.hi));
+    p.hi = t;
   }
   __device__ void advance(float vx, float vy, float vz, float dt) {
     acc(x, __fmul_rn(dt, vx)); acc(y, __fmul_rn(dt, vy)); acc(z, __fmul_rn(dt, vz));
@@ -172,26 +215,40 @@ struct Pos<AP_FP32_PHASEFF> {
 
 // ------------------------------------------------------------ time base
 // Per-thread constants of the time stepping, made once from (t0, dt) in
-// double: t_n = t0 + n dt is recomputed each step, never accumulated.
+// double: t_n = t0 + n dt is recomputed for every step, never accumulated.
+// `at(n)` gives the per-step value: t_n in double for the double-phase
+// variants; for the float-float variant the reduced carrier phase
+// C_n = omega (t_n - t_f) + phase0 (mod 2 pi) and T_n = t_n - t_f as a
+// float-float pair, which the kernels tabulate once per block in shared
+// memory (every particle of a block shares them).
+struct StepFF {
+  float C, Th, Tl, pad;
+};
+
 template <int PREC>
 struct TimeBase;
 
 template <>
 struct TimeBase<AP_FP64> {
+  using Step = double;
   double t0, dt;
   template <typename P>
   __device__ void init(const P &, double T0, double DT) { t0 = T0; dt = DT; }
+  __device__ double at(long long n) const { return t0 + (double)n * dt; }
 };
 template <>
 struct TimeBase<AP_FP32_PHASE64> {
+  using Step = double;
   double t0, dt;
   template <typename P>
   __device__ void init(const P &, double T0, double DT) { t0 = T0; dt = DT; }
+  __device__ double at(long long n) const { return t0 + (double)n * dt; }
 };
 template <>
 struct TimeBase<AP_FP32_PHASEFF> {
-  // C_n = omega (t_n - t_f) + phase0 = Om0 + n Del (mod 2 pi), both reduced on
-  // entry; T_n = t_n - t_f = T0 + n DT.
+  using Step = StepFF;
+  // C_n = Om0 + n Del (mod 2 pi), Om0 and Del reduced in double on entry;
+  // T_n = T0 + n DT.
   FF om0, del, T0, DT;
   template <typename P>
   __device__ void init(const P &pp, double t0, double dt) {
@@ -205,9 +262,19 @@ struct TimeBase<AP_FP32_PHASEFF> {
     T0 = split_double(t0 - pp.t_f);
     DT = split_double(dt);
   }
+  __device__ StepFF at(long long n) const {
+    const float nf = (float)n;  // exact for n < 2^24
+    FF nd = two_prod(nf, del.hi);
+    FF c = two_sum(om0.hi, nd.hi);
+    float clo = __fadd_rn(__fadd_rn(c.lo, nd.lo), __fmaf_rn(nf, del.lo, om0.lo));
+    FF nt = two_prod(nf, DT.hi);
+    FF T = two_sum(T0.hi, nt.hi);
+    T.lo = __fadd_rn(T.lo, __fadd_rn(nt.lo, __fmaf_rn(nf, DT.lo, T0.lo)));
+    return {reduce_ff(c.hi, clo), T.hi, T.lo, 0.0f};
+  }
 };
 
-// Local coordinates of one particle at step n, relative to the focus:
+// Local coordinates of one particle at one step, relative to the focus:
 // transverse x, y; dz = z - z_f; the reduced carrier phase psi; envelope
 // argument eta = (t - t_f) - (z - z_f)/v_g; and for the flying focus the
 // light-front coordinate phi' = (t - t_f) - (z - z_f) split in two parts.
@@ -219,11 +286,11 @@ struct Local {
 
 template <int PREC>
 __device__ __forceinline__ Local<Real<PREC>> local_coords(const Pulse<Real<PREC>> &P,
-                                                          const TimeBase<PREC> &tb, long long n,
+                                                          const typename TimeBase<PREC>::Step &st,
                                                           const Pos<PREC> &pos) {
   Local<Real<PREC>> L;
   if constexpr (PREC == AP_FP64) {
-    double T = (tb.t0 + (double)n * tb.dt) - P.t_f;
+    double T = st - P.t_f;
     double dz = pos.z - P.z_f;
     L.x = pos.x;
     L.y = pos.y;
@@ -233,7 +300,7 @@ __device__ __forceinline__ Local<Real<PREC>> local_coords(const Pulse<Real<PREC>
     L.phi_hi = T - dz;
     L.phi_lo = 0.0;
   } else if constexpr (PREC == AP_FP32_PHASE64) {
-    double T = (tb.t0 + (double)n * tb.dt) - P.t_f;
+    double T = st - P.t_f;
     double dz = pos.z - P.z_f;
     double psi = P.omega * T - P.k * dz + P.phase0;
     const double twopi = 2.0 * CUDART_PI;
@@ -247,33 +314,23 @@ __device__ __forceinline__ Local<Real<PREC>> local_coords(const Pulse<Real<PREC>
     L.phi_hi = (float)phi;
     L.phi_lo = (float)(phi - (double)L.phi_hi);
   } else {
-    // C_n = Om0 + n Del, reduced to one float
-    float nf = (float)n;  // exact for n < 2^24
-    FF nd = two_prod(nf, tb.del.hi);
-    FF c = two_sum(tb.om0.hi, nd.hi);
-    float clo = __fadd_rn(__fadd_rn(c.lo, nd.lo), __fmaf_rn(nf, tb.del.lo, tb.om0.lo));
-    float C = reduce_ff(c.hi, clo);
-    // T_n = T0 + n DT
-    FF nt = two_prod(nf, tb.DT.hi);
-    FF T = two_sum(tb.T0.hi, nt.hi);
-    T.lo = __fadd_rn(T.lo, __fadd_rn(nt.lo, __fmaf_rn(nf, tb.DT.lo, tb.T0.lo)));
     // dz = z - z_f
     FF dz = two_sum(pos.z.hi, -P.zf_hi);
     dz.lo = __fadd_rn(dz.lo, __fsub_rn(pos.z.lo, P.zf_lo));
-    // psi = C - k dz
+    // psi = C_n - k dz
     FF kd = two_prod(P.k_hi, dz.hi);
     kd.lo = __fadd_rn(kd.lo, __fmaf_rn(P.k_hi, dz.lo, __fmul_rn(P.k_lo, dz.hi)));
-    FF ps = two_sum(C, -kd.hi);
+    FF ps = two_sum(st.C, -kd.hi);
     L.psi = reduce_ff(ps.hi, __fsub_rn(ps.lo, kd.lo));
     L.x = pos.xr();
     L.y = pos.yr();
     L.dz = __fadd_rn(dz.hi, dz.lo);
-    float Tf = __fadd_rn(T.hi, T.lo);
+    float Tf = __fadd_rn(st.Th, st.Tl);
     L.eta = fmaf(-L.dz, P.inv_vg, Tf);
     // phi' = T - dz as float-float
-    FF ph = two_sum(T.hi, -dz.hi);
+    FF ph = two_sum(st.Th, -dz.hi);
     L.phi_hi = ph.hi;
-    L.phi_lo = __fadd_rn(ph.lo, __fsub_rn(T.lo, dz.lo));
+    L.phi_lo = __fadd_rn(ph.lo, __fsub_rn(st.Tl, dz.lo));
   }
   return L;
 }
@@ -283,8 +340,8 @@ __device__ __forceinline__ Local<Real<PREC>> local_coords(const Pulse<Real<PREC>
 // base-2 exponent `l2` (Gaussian and super-Gaussian envelopes share the
 // beam's exp2).  SIN2: env_a = pi/T, env_b = T/2; GAUSS: env_a = 2 ln2 log2e
 // / T^2; SGAUSS: env_a = 1/tau, env_b = log2e; CW: 1.
-template <typename R>
-__device__ __forceinline__ void envelope(const Pulse<R> &P, R eta, R &mul, R &l2) {
+template <class PT, typename R>
+__device__ __forceinline__ void envelope(const PT &P, R eta, R &mul, R &l2) {
   mul = R(1);
   l2 = R(0);
   switch (P.env) {
@@ -317,8 +374,8 @@ __device__ __forceinline__ void envelope(const Pulse<R> &P, R eta, R &mul, R &l2
 // E_perp = Re[p U], B_perp = (B0/E0) Re[(z x p) U];
 // E_z = Re[-i (v_phi/omega) DE], B_z = (B0/E0) Re[-i (c/omega) DB] with
 // DE = p_x dU/dx + p_y dU/dy and DB = -p_y dU/dx + p_x dU/dy (Sec. 3.1).
-template <typename R>
-__device__ __forceinline__ void assemble(const Pulse<R> &P, Cx<R> U, Cx<R> DE, Cx<R> DB, bool lon,
+template <class PT, typename R>
+__device__ __forceinline__ void assemble(const PT &P, Cx<R> U, Cx<R> DE, Cx<R> DB, bool lon,
                                          R E[3], R B[3]) {
   R pxU = P.px_re * U.re - P.px_im * U.im;
   R pyU = P.py_re * U.re - P.py_im * U.im;
@@ -335,6 +392,38 @@ __device__ __forceinline__ void assemble(const Pulse<R> &P, Cx<R> U, Cx<R> DE, C
   }
 }
 
+// Field assembly for beams whose transverse derivative is
+// dU/dx = g x W, dU/dy = g y W (Gaussian: g = -2/w0^2, W = q U; the flying
+// focus sums W over components with the 1/k_j factors inside), specialised
+// per polarisation (a uniform branch): DE = g (p_x x + p_y y) W and
+// DB = g (-p_y x + p_x y) W, E_z = (v_phi/omega) Im DE, B_z = (B0/E0)(c/omega) Im DB.
+template <class PT, typename R>
+__device__ __forceinline__ void finish_beam(const PT &P, R x, R y, Cx<R> U, Cx<R> W, R g,
+                                            bool lon, R E[3], R B[3]) {
+  const R br = P.bratio;
+  const R ce = P.lonE * g, cb = br * P.lonB * g;
+  E[2] = R(0);
+  B[2] = R(0);
+  switch (P.pol) {
+    case AP_LIN_X:
+      E[0] = U.re; E[1] = R(0); B[0] = R(0); B[1] = br * U.re;
+      if (lon) { E[2] = ce * x * W.im; B[2] = cb * y * W.im; }
+      break;
+    case AP_LIN_Y:
+      E[0] = R(0); E[1] = U.re; B[0] = -br * U.re; B[1] = R(0);
+      if (lon) { E[2] = ce * y * W.im; B[2] = -cb * x * W.im; }
+      break;
+    case AP_CIRC_P:  // p = (1, -i)
+      E[0] = U.re; E[1] = U.im; B[0] = -br * U.im; B[1] = br * U.re;
+      if (lon) { E[2] = ce * (x * W.im - y * W.re); B[2] = cb * (x * W.re + y * W.im); }
+      break;
+    default:  // AP_CIRC_M, p = (1, +i)
+      E[0] = U.re; E[1] = -U.im; B[0] = br * U.im; B[1] = br * U.re;
+      if (lon) { E[2] = ce * (x * W.im + y * W.re); B[2] = cb * (y * W.im - x * W.re); }
+      break;
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ R reduce_angle(R a) {
   if constexpr (std::is_same<R, float>::value) return reduce_f(a);
@@ -342,8 +431,8 @@ __device__ __forceinline__ R reduce_angle(R a) {
 }
 
 // Plane wave (Eqs. plane_func, plane_b): U = A Gamma e^{i psi}.
-template <typename R>
-__device__ __forceinline__ void fields_plane(const Pulse<R> &P, const Local<R> &L, R E[3], R B[3]) {
+template <class PT, typename R>
+__device__ __forceinline__ void fields_plane(const PT &P, const Local<R> &L, R E[3], R B[3]) {
   R mul, l2;
   envelope(P, L.eta, mul, l2);
   R a = P.amp * mul;
@@ -351,16 +440,15 @@ __device__ __forceinline__ void fields_plane(const Pulse<R> &P, const Local<R> &
   R s, c;
   sincos_r(L.psi, &s, &c);
   Cx<R> U{a * c, a * s};
-  Cx<R> Z{R(0), R(0)};
-  assemble(P, U, Z, Z, false, E, B);
+  finish_beam(P, L.x, L.y, U, U, R(0), false, E, B);
 }
 
 // Paraxial Gaussian beam (Eq. paraxial, D = 3, +z):
 //   u = A q exp(-r^2 q / w0^2),  q = 1/(1 - i zeta),  zeta = (z - z_f)/z_R,
 // which equals A (w0/w) e^{-r^2/w^2} e^{-i k r^2/(2R)} e^{i atan zeta}.
 // du/dx = -2 x q / w0^2 u.
-template <typename R>
-__device__ __forceinline__ void fields_gauss(const Pulse<R> &P, const Local<R> &L, R E[3], R B[3]) {
+template <class PT, typename R>
+__device__ __forceinline__ void fields_gauss(const PT &P, const Local<R> &L, R E[3], R B[3]) {
   R mul, l2;
   envelope(P, L.eta, mul, l2);
   R zeta = L.dz * P.inv_zR;
@@ -372,24 +460,14 @@ __device__ __forceinline__ void fields_gauss(const Pulse<R> &P, const Local<R> &
   R s, c;
   sincos_r(ang, &s, &c);
   Cx<R> U = cmul(q, Cx<R>{mag * c, mag * s});
-  Cx<R> DE{R(0), R(0)}, DB{R(0), R(0)};
-  if (P.lon) {
-    Cx<R> W = cmul(q, U);
-    R g = R(-2) * P.inv_w0sq;
-    // p_x x + p_y y and -p_y x + p_x y (complex)
-    Cx<R> se{P.px_re * L.x + P.py_re * L.y, P.px_im * L.x + P.py_im * L.y};
-    Cx<R> sb{-P.py_re * L.x + P.px_re * L.y, -P.py_im * L.x + P.px_im * L.y};
-    DE = cscale(cmul(se, W), g);
-    DB = cscale(cmul(sb, W), g);
-  }
-  assemble(P, U, DE, DB, P.lon != 0, E, B);
+  finish_beam(P, L.x, L.y, U, cmul(q, U), R(-2) * P.inv_w0sq, P.lon != 0, E, B);
 }
 
 // Laguerre-Gaussian LG_pl (textbook; the paper names the family in Sec. 3.1):
 //   u = A (sqrt2/w0)^{|l|} (x + i sgn(l) y)^{|l|} L_p^{|l|}(s) q^{|l|+1} (q/q*)^p e^{-r^2 q/w0^2},
 // s = 2 r^2 |q|^2 / w0^2; the longitudinal terms use the product rule.
-template <typename R>
-__device__ __forceinline__ void fields_lg(const Pulse<R> &P, const Local<R> &L, R E[3], R B[3]) {
+template <class PT, typename R>
+__device__ __forceinline__ void fields_lg(const PT &P, const Local<R> &L, R E[3], R B[3]) {
   R mul, l2;
   envelope(P, L.eta, mul, l2);
   R zeta = L.dz * P.inv_zR;
@@ -481,16 +559,8 @@ __device__ __forceinline__ void fields_flying(const Pulse<Real<PREC>> &P, const 
     if (P.lon) S1 = cadd(S1, cscale(cmul(q, U), cj.inv_k));
     rot = cmul(rot, step);
   }
-  Cx<R> DE{R(0), R(0)}, DB{R(0), R(0)};
-  if (P.lon) {
-    R g = R(-2) * P.inv_w0sq;
-    Cx<R> se{P.px_re * L.x + P.py_re * L.y, P.px_im * L.x + P.py_im * L.y};
-    Cx<R> sb2{-P.py_re * L.x + P.px_re * L.y, -P.py_im * L.x + P.px_im * L.y};
-    DE = cscale(cmul(se, S1), g);
-    DB = cscale(cmul(sb2, S1), g);
-  }
   // the 1/k_j factors are inside S1: lonE = lonB = 1 for this kind
-  assemble(P, S0, DE, DB, P.lon != 0, E, B);
+  finish_beam(P, L.x, L.y, S0, S1, R(-2) * P.inv_w0sq, P.lon != 0, E, B);
 }
 
 template <int KIND, int PREC>
@@ -510,45 +580,78 @@ __device__ __forceinline__ void analytic_fields(const Pulse<Real<PREC>> &P,
 // when the particle changes cell; the result equals a gather every step.
 template <typename R>
 struct GridCache {
-  int cell;
+  R ox, oy, oz;  // lower corner of the cached cell in grid units (-16: nothing cached)
   R c[6][8];
 };
 
 template <typename R>
-__device__ __forceinline__ R grid_coord(R v, R lo, R inv_d, int n, int &i) {
-  R f = (v - lo) * inv_d;
-  f = fmin(fmax(f, R(0)), R(n - 1));
-  int ii = (int)f;
-  if (ii > n - 2) ii = n - 2;
-  i = ii;
-  return f - R(ii);
+__device__ __forceinline__ void grid_cache_reset(GridCache<R> &gc) {
+  gc.ox = gc.oy = gc.oz = R(-16);
+}
+
+// position in grid units, clamped to the node range [0, n - 1]
+template <typename R>
+__device__ __forceinline__ R grid_unit(R v, R lo, R inv_d, int n) {
+  return fmin(fmax((v - lo) * inv_d, R(0)), R(n - 1));
 }
 
 template <typename R>
 __device__ __forceinline__ void grid_gather(const GridView &g, GridCache<R> &gc, R x, R y, R z,
                                             R E[3], R B[3]) {
-  int ix, iy, iz;
-  R wx, wy, wz;
+  R fx, fy, fz;
   if constexpr (std::is_same<R, double>::value) {
-    wx = grid_coord<R>(x, g.lo_d[0], g.inv_d_d[0], g.nx, ix);
-    wy = grid_coord<R>(y, g.lo_d[1], g.inv_d_d[1], g.ny, iy);
-    wz = grid_coord<R>(z, g.lo_d[2], g.inv_d_d[2], g.nz, iz);
+    fx = grid_unit<R>(x, g.lo_d[0], g.inv_d_d[0], g.nx);
+    fy = grid_unit<R>(y, g.lo_d[1], g.inv_d_d[1], g.ny);
+    fz = grid_unit<R>(z, g.lo_d[2], g.inv_d_d[2], g.nz);
   } else {
-    wx = grid_coord<R>(x, g.lo[0], g.inv_d[0], g.nx, ix);
-    wy = grid_coord<R>(y, g.lo[1], g.inv_d[1], g.ny, iy);
-    wz = grid_coord<R>(z, g.lo[2], g.inv_d[2], g.nz, iz);
+    fx = grid_unit<R>(x, g.lo[0], g.inv_d[0], g.nx);
+    fy = grid_unit<R>(y, g.lo[1], g.inv_d[1], g.ny);
+    fz = grid_unit<R>(z, g.lo[2], g.inv_d[2], g.nz);
   }
-  const int cell = (iz * g.ny + iy) * g.nx + ix;
-  if (cell != gc.cell) {
-    gc.cell = cell;
+  R wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
+  // still inside the cached cell (the upper face included, as for the last
+  // cell of the grid): no integer work, no loads
+  if (!(wx >= R(0) && wx <= R(1) && wy >= R(0) && wy <= R(1) && wz >= R(0) && wz <= R(1))) {
+    int ix = min((int)fx, g.nx - 2), iy = min((int)fy, g.ny - 2), iz = min((int)fz, g.nz - 2);
+    gc.ox = R(ix);
+    gc.oy = R(iy);
+    gc.oz = R(iz);
+    wx = fx - gc.ox;
+    wy = fy - gc.oy;
+    wz = fz - gc.oz;
     const size_t sx = 1, sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
-    const size_t b = (size_t)cell;
+    const size_t b = ((size_t)iz * g.ny + iy) * g.nx + ix;
+    // corner values v[corner][comp], corner = cx + 2 cy + 4 cz
+    float v[8][6];
+    if (g.packed) {
+      // node-interleaved: two 16-byte loads per corner, one 32-byte sector
+      const size_t off[8] = {b, b + sx, b + sy, b + sy + sx, b + sz, b + sz + sx, b + sz + sy,
+                             b + sz + sy + sx};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float4 lo4 = __ldg(g.packed + 2 * off[k]);
+        const float4 hi4 = __ldg(g.packed + 2 * off[k] + 1);
+        v[k][0] = lo4.x; v[k][1] = lo4.y; v[k][2] = lo4.z;
+        v[k][3] = lo4.w; v[k][4] = hi4.x; v[k][5] = hi4.y;
+      }
+    } else {
+#pragma unroll
+      for (int comp = 0; comp < 6; ++comp) {
+        const float *f = g.f[comp] + b;
+        v[0][comp] = __ldg(f);
+        v[1][comp] = __ldg(f + sx);
+        v[2][comp] = __ldg(f + sy);
+        v[3][comp] = __ldg(f + sy + sx);
+        v[4][comp] = __ldg(f + sz);
+        v[5][comp] = __ldg(f + sz + sx);
+        v[6][comp] = __ldg(f + sz + sy);
+        v[7][comp] = __ldg(f + sz + sy + sx);
+      }
+    }
 #pragma unroll
     for (int comp = 0; comp < 6; ++comp) {
-      const float *f = g.f[comp] + b;
-      R v000 = __ldg(f), v100 = __ldg(f + sx), v010 = __ldg(f + sy), v110 = __ldg(f + sy + sx);
-      R v001 = __ldg(f + sz), v101 = __ldg(f + sz + sx), v011 = __ldg(f + sz + sy),
-        v111 = __ldg(f + sz + sy + sx);
+      const R v000 = v[0][comp], v100 = v[1][comp], v010 = v[2][comp], v110 = v[3][comp];
+      const R v001 = v[4][comp], v101 = v[5][comp], v011 = v[6][comp], v111 = v[7][comp];
       R *c = gc.c[comp];
       c[0] = v000;
       c[1] = v100 - v000;

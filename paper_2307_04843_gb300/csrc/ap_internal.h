@@ -2,6 +2,8 @@
 // analytic-pulse library (not part of the public C ABI in include/ap.h).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -42,6 +44,7 @@ struct Pulse {
   R px_re, px_im, py_re, py_im;  // polarisation vector p
   R lg_c[kLgMaxP + 1];           // L_p^{|l|}(s) = sum_i lg_c[i] s^i
   R lg_pref;                     // (sqrt(2) / w0)^{|l|}
+  R a0, inv_w0, amp_unit;        // a0, 1/w0 and amp / a0 (adjoint: d/da0, d/dw0)
   // carrier phase psi = omega (t - t_f) - k (z - z_f) + phase0 (double, host-exact)
   double omega, k, t_f, z_f, phase0;
   // float-float copies for AP_FP32_PHASEFF
@@ -56,6 +59,7 @@ struct Pulse {
 // Grid view passed to kernels (device pointers, caller-owned).
 struct GridView {
   const float *f[6];
+  const float4 *packed;   // node-interleaved [nz][ny][nx][2] float4, or null
   int nx, ny, nz;
   float lo[3], inv_d[3];  // node spacing d = (hi - lo)/(n - 1)
   double lo_d[3], inv_d_d[3];

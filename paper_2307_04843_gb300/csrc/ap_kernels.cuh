@@ -7,15 +7,23 @@
 
 namespace apt {
 
+// Steps per chunk of the per-warp step table (float-float variant): one
+// entry per lane.
+constexpr int kStepChunk = 32;
+constexpr int kMaxWarps = 8;  // 256 threads per block at most
+
 // One particle through n_steps fused steps: load (a2), per step the local
 // coordinates and phase (a3), envelope and profile (a4-a7), grid gather
 // (a8), Boris and position (a9), light-front diagnostic (a10); then store
-// (a11).  `valid` is false for the padding lanes of the last warp, which run
-// the loop on a dummy particle so that warp reductions see full warps.
+// (a11).  Every lane of a warp calls this together: the float-float variant
+// tabulates the per-step phase base C_n and time T_n for its warp in shared
+// memory, 32 steps at a time (one entry per lane, __syncwarp only, so warps
+// never wait for each other).  `valid` is false for padding threads, which
+// run the loop on a dummy particle so that warp operations see every lane.
 // Returns the final gamma (double) of a valid particle, 0 otherwise.
 template <int KIND, int PREC, bool GRID>
 __device__ __forceinline__ double push_one(const Pulse<Real<PREC>> &P, const PushArgs &a,
-                                           long long i, bool valid) {
+                                           long long i, bool valid, StepFF *s_steps) {
   using R = Real<PREC>;
   double X = 0.0, Y = 0.0, Z = 0.0;
   R u[3] = {R(0), R(0), R(0)};
@@ -37,18 +45,31 @@ __device__ __forceinline__ double push_one(const Pulse<Real<PREC>> &P, const Pus
   const R dtR = (R)a.dt;
   const R h0 = R(1) / rsqrt_r(fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], R(1))))) - u[2];
   GridCache<R> gc;
-  gc.cell = -1;
+  grid_cache_reset(gc);
   double *lf = a.diag.lf;
-  for (long long s = 0; s < a.n_steps; ++s) {
-    Local<R> L = local_coords<PREC>(P, tb, s, pos);
-    R E[3], B[3];
-    analytic_fields<KIND, PREC>(P, L, E, B);
-    if constexpr (GRID) grid_gather<R>(a.grid, gc, pos.xr(), pos.yr(), pos.zr(), E, B);
-    R ig = boris(u, E, B, dtR);
-    pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtR);
-    if (lf) {
-      R dev = valid ? fabs((R(1) / ig - u[2]) - h0) : R(0);
-      warp_max_to(lf + s, dev, 0xffffffffu);
+  StepFF *wsteps = s_steps + (threadIdx.x >> 5) * kStepChunk;
+  const int lane = threadIdx.x & 31;
+  for (long long s0 = 0; s0 < a.n_steps; s0 += kStepChunk) {
+    const int cnt = (int)(a.n_steps - s0 < kStepChunk ? a.n_steps - s0 : kStepChunk);
+    if constexpr (PREC == AP_FP32_PHASEFF) {
+      __syncwarp();  // no lane still reads the previous chunk
+      if (lane < cnt) wsteps[lane] = tb.at(s0 + lane);
+      __syncwarp();
+    }
+    for (int k = 0; k < cnt; ++k) {
+      typename TimeBase<PREC>::Step st;
+      if constexpr (PREC == AP_FP32_PHASEFF) st = wsteps[k];
+      else st = tb.at(s0 + k);
+      Local<R> L = local_coords<PREC>(P, st, pos);
+      R E[3], B[3];
+      analytic_fields<KIND, PREC>(P, L, E, B);
+      if constexpr (GRID) grid_gather<R>(a.grid, gc, L.x, L.y, pos.zr(), E, B);
+      R ig = boris(u, E, B, dtR);
+      pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtR);
+      if (lf) {
+        R dev = valid ? fabs((R(1) / ig - u[2]) - h0) : R(0);
+        warp_max_to(lf + s0 + k, dev, 0xffffffffu);
+      }
     }
   }
   if (!valid) return 0.0;
@@ -87,24 +108,26 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
   return r;
 }
 
-// Plain launch: a grid-stride loop over warps of particles (all lanes of a
-// warp share the trip count), one particle per thread, every step fused.
+// Plain launch: a grid-stride loop over block-sized chunks of particles (the
+// trip count is uniform across the block), one particle per thread, every
+// step fused.
 template <int KIND, int PREC, bool GRID>
 __global__ void __launch_bounds__(256) push_kernel(const __grid_constant__ Pulse<Real<PREC>> P,
                                                    const __grid_constant__ PushArgs a) {
   extern __shared__ uint32_t s_hist[];
   __shared__ double s_red[32];
+  __shared__ StepFF s_steps[kMaxWarps * kStepChunk];
   const bool hist = a.diag.hist != nullptr;
   if (hist) {
     for (int b = threadIdx.x; b < a.diag.bins; b += blockDim.x) s_hist[b] = 0u;
     __syncthreads();
   }
   double acc = 0.0;
-  const long long npad = (a.n + 31) & ~31LL;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += stride) {
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < a.n; base += stride) {
+    const long long i = base + threadIdx.x;
     const bool valid = i < a.n;
-    double g = push_one<KIND, PREC, GRID>(P, a, i, valid);
+    double g = push_one<KIND, PREC, GRID>(P, a, i, valid, s_steps);
     if (valid) {
       acc += g;
       if (hist) hist_add(s_hist, a.diag, g);
@@ -133,6 +156,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const Pulse<Real<PREC>> *__r
   __shared__ double s_red[32];
   __shared__ long long s_tile;
   __shared__ int s_set;
+  __shared__ StepFF s_steps[kMaxWarps * kStepChunk];
   __shared__ __align__(16) unsigned char s_pulse_raw[sizeof(Pulse<R>)];
   Pulse<R> &sp = *reinterpret_cast<Pulse<R> *>(s_pulse_raw);
   const PushArgs &a = ba.base;
@@ -179,7 +203,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const Pulse<Real<PREC>> *__r
     for (int k = threadIdx.x; k < T; k += blockDim.x) {
       const long long i = first + k;
       const bool valid = i >= 0 && i < end_set && i < a.n;
-      double g = push_one<KIND, PREC, GRID>(sp, a, i, valid);
+      double g = push_one<KIND, PREC, GRID>(sp, a, i, valid, s_steps);
       if (valid) acc += g;
     }
     if (a.diag.set_sum) {
@@ -204,7 +228,7 @@ __global__ void __launch_bounds__(256) eval_kernel(const __grid_constant__ Pulse
   pos.load(x, y, z);
   TimeBase<PREC> tb;
   tb.init(P, t, 0.0);
-  Local<R> L = local_coords<PREC>(P, tb, 0, pos);
+  Local<R> L = local_coords<PREC>(P, tb.at(0), pos);
   R E[3], B[3];
   analytic_fields<KIND, PREC>(P, L, E, B);
   for (int c = 0; c < 3; ++c) {

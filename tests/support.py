@@ -42,8 +42,8 @@ def gpu_push(pulses, parts, t0, dt, n_steps, precision, grid=None, diag_keys=(),
             diag["set_sum"] = torch.zeros(1, dtype=torch.float64, device="cuda")
         g = None
         if grid is not None:
-            arr, lo, hi = grid
-            g = (torch.as_tensor(arr).cuda() if not isinstance(arr, torch.Tensor) else arr, lo, hi)
+            arr, lo, hi = grid[:3]
+            g = (torch.as_tensor(arr).cuda() if not isinstance(arr, torch.Tensor) else arr, lo, hi) + tuple(grid[3:])
         h.push(dev, t0, dt, n_steps, precision=precision, grid=g, diag=diag or None)
         st = h.status()
         torch.cuda.synchronize()

@@ -1,0 +1,192 @@
+"""Discrete adjoint (ap_push_adjoint) and its torch.autograd.Function.
+
+The gradient of the per-set mean final gamma with respect to (a0, w0,
+z_focus) is checked against (i) the oracle's FP64 central finite
+differences with Richardson extrapolation and (ii) GPU FP64 central finite
+differences of the forward push, to relative error <= 1e-3 (the bound the
+method's gradients are held to); the adjoint's objective equals the forward
+push's mean gamma.  Segments: several checkpoints plus a ragged last one."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_04843_gb300 import workloads
+from support import THREADS
+
+L = 2 * math.pi
+NAMES = ("a0", "w0", "z_focus")
+
+
+def _sets_case(n_sets=3, per=12, seed=3):
+    cfg = workloads.config(5)
+    sets, _ = workloads.batch_sets(cfg, seed=workloads.seed_for(5) + seed)
+    sets = sets[:n_sets]
+    counts = np.full(n_sets, per, dtype=np.int64)
+    counts[-1] = per + 5
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    rng = np.random.default_rng(seed)
+    n = int(off[-1])
+    # particles near each set's focus region so the pulse does work
+    parts = dict(x=rng.uniform(-1, 1, n) * 3 * L, y=rng.uniform(-1, 1, n) * 3 * L,
+                 z=rng.uniform(-1, 1, n) * 2 * L, ux=np.zeros(n), uy=np.zeros(n), uz=np.zeros(n))
+    for s in range(n_sets):
+        parts["z"][off[s]:off[s + 1]] += sets[s]["z_focus"]
+    return sets, off, parts
+
+
+def _run_adjoint(sets, off, parts, t0, dt, n_steps, K, precision, grid=None):
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    from paper_2307_04843_gb300.autograd import adjoint
+    dev = _lib.to_device(parts, precision)
+    snap = {k: v.clone() for k, v in dev.items()}
+    d_off = torch.as_tensor(off).cuda() if off is not None else None
+    J, dJ = adjoint(sets, dev, d_off, t0, dt, n_steps, ckpt_every=K, precision=precision, grid=grid)
+    for k in dev:  # the initial state is left unchanged
+        assert torch.equal(dev[k], snap[k])
+    return J.cpu().numpy(), dJ.cpu().numpy()
+
+
+def _oracle_grads(sets, off, parts, t0, dt, n_steps, grid=None):
+    out = []
+    for s, pulse in enumerate(sets):
+        sub = {k: v[off[s]:off[s + 1]] for k, v in parts.items()}
+        g = oracle.grad_fd(pulse, sub, t0, dt, n_steps, names=NAMES, rel_h=1e-4, grid=grid,
+                           scale=dict(z_focus=L))
+        out.append([g[k] for k in NAMES])
+    return np.array(out)
+
+
+def _rel(a, b):
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-3 * np.max(np.abs(b)))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adjoint_gauss_sets_vs_oracle_fd(precision):
+    sets, off, parts = _sets_case()
+    t0, dt, n_steps, K = -8.0, 0.02, 430, 100  # 5 segments, the last one of 30 steps
+    J, dJ = _run_adjoint(sets, off, parts, t0, dt, n_steps, K, precision)
+    ref = _oracle_grads(sets, off, parts, t0, dt, n_steps)
+    err = _rel(dJ[:, :3], ref)
+    assert np.max(err) <= 1e-3, (precision, err, dJ[:, :3], ref)
+    assert np.all(dJ[:, 3] == 0.0)
+    # objective equals the oracle's mean final gamma
+    for s, pulse in enumerate(sets):
+        sub = {k: v[off[s]:off[s + 1]] for k, v in parts.items()}
+        mg = oracle.mean_gamma(pulse, sub, t0, dt, n_steps)
+        assert J[s] == pytest.approx(mg, rel=1e-12 if precision == "fp64" else 1e-5)
+
+
+@pytest.mark.gpu
+def test_adjoint_vs_gpu_fp64_central_differences():
+    """Against FP64 central differences of the GPU forward push itself."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    sets, off, parts = _sets_case(n_sets=2, per=16, seed=7)
+    t0, dt, n_steps, K = -6.0, 0.02, 300, 64
+    _, dJ = _run_adjoint(sets, off, parts, t0, dt, n_steps, K, "fp64")
+
+    def J(pulse, sub):
+        with _lib.Handle(pulse) as h:
+            d = _lib.to_device(sub, "fp64")
+            ss = torch.zeros(1, dtype=torch.float64, device="cuda")
+            h.push(d, t0, dt, n_steps, precision="fp64", diag=dict(set_sum=ss))
+            return float(ss.item()) / sub["x"].size
+
+    for s, pulse in enumerate(sets):
+        sub = {k: v[off[s]:off[s + 1]] for k, v in parts.items()}
+        for k, name in enumerate(NAMES):
+            h = 1e-5 * (abs(pulse[name]) if name != "z_focus" else L)
+            fd = (J(dict(pulse, **{name: pulse[name] + h}), sub) - J(dict(pulse, **{name: pulse[name] - h}), sub)) / (2 * h)
+            assert abs(dJ[s, k] - fd) <= 1e-3 * max(abs(fd), 1e-6), (s, name, dJ[s, k], fd)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind", ["lg", "plane"])
+def test_adjoint_other_kinds_vs_oracle_fd(kind):
+    if kind == "lg":
+        pulse = dict(kind="lg", pol="cp", env="gauss", env_len=20.0, a0=4.0, w0=2.5 * L, lg_p=1, lg_l=2,
+                     z_focus=3.0, t_focus=0.0, longitudinal=True)
+    else:
+        pulse = dict(kind="plane", pol="x", env="sin2", env_len=6, a0=2.0, z_focus=1.0, t_focus=6 * math.pi)
+    rng = np.random.default_rng(11)
+    n = 24
+    parts = dict(x=rng.uniform(-1, 1, n) * L, y=rng.uniform(-1, 1, n) * L, z=rng.uniform(-1, 1, n) * L,
+                 ux=np.zeros(n), uy=np.zeros(n), uz=np.zeros(n))
+    off = np.array([0, n], dtype=np.int64)
+    t0, dt, n_steps, K = -5.0 if kind == "lg" else 0.0, 0.02, 350, 128
+    _, dJ = _run_adjoint([pulse], off, parts, t0, dt, n_steps, K, "fp64")
+    names = NAMES if kind == "lg" else ("a0", "z_focus")
+    g = oracle.grad_fd(pulse, parts, t0, dt, n_steps, names=names, rel_h=1e-4, scale=dict(z_focus=L))
+    for name in names:
+        k = NAMES.index(name)
+        assert abs(dJ[0, k] - g[name]) <= 1e-3 * max(abs(g[name]), 1e-8), (kind, name, dJ[0, k], g[name])
+
+
+@pytest.mark.gpu
+def test_adjoint_with_linear_grid_field():
+    """A grid holding linear fields (trilinear interpolation is then exact and
+    smooth across cells) enters the trajectory and the position adjoint."""
+    sets, off, parts = _sets_case(n_sets=1, per=20, seed=5)
+    nx = ny = nz = 9
+    lo, hi = (-25.0, -25.0, -60.0), (25.0, 25.0, 60.0)
+    X = np.linspace(lo[0], hi[0], nx)[None, None, :]
+    Y = np.linspace(lo[1], hi[1], ny)[:, None][None]
+    Z = np.linspace(lo[2], hi[2], nz)[:, None, None]
+    comps = [0.02 + 0.001 * X + 0 * Y + 0 * Z, 0.0005 * Y + 0 * X + 0 * Z, -0.0004 * Z + 0 * X + 0 * Y,
+             0.0003 * X + 0.0002 * Y + 0 * Z, 0.01 + 0 * X + 0 * Y + 0 * Z, 0.0002 * Z + 0 * X + 0 * Y]
+    grid = np.stack([np.broadcast_to(c, (nz, ny, nx)) for c in comps]).astype(np.float32)
+    import torch
+    g_dev = (torch.as_tensor(grid).cuda(), lo, hi)
+    t0, dt, n_steps, K = -8.0, 0.02, 300, 100
+    _, dJ = _run_adjoint(sets, off, parts, t0, dt, n_steps, K, "fp64", grid=g_dev)
+    ref = _oracle_grads(sets, off, parts, t0, dt, n_steps, grid=(grid, lo, hi))
+    assert np.max(_rel(dJ[:, :3], ref)) <= 1e-3, (dJ[:, :3], ref)
+
+
+@pytest.mark.gpu
+def test_autograd_function_gradcheck_fp64():
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    from paper_2307_04843_gb300.autograd import mean_final_gamma
+    sets, off, parts = _sets_case(n_sets=2, per=6, seed=9)
+    dev = _lib.to_device(parts, "fp64")
+    d_off = torch.as_tensor(off).cuda()
+    params = torch.tensor([[s["a0"], s["w0"], s["z_focus"]] for s in sets], dtype=torch.float64,
+                          requires_grad=True)
+
+    def f(p):
+        return mean_final_gamma(p, sets, dev, d_off, t0=-6.0, dt=0.02, n_steps=150, ckpt_every=40,
+                                precision="fp64")
+
+    assert torch.autograd.gradcheck(f, (params,), eps=1e-6, atol=1e-7, rtol=1e-4)
+    J = f(params)
+    J.sum().backward()
+    assert params.grad is not None and torch.all(torch.isfinite(params.grad))
+
+
+@pytest.mark.gpu
+def test_adjoint_errors():
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    cfg = workloads.config(4)
+    parts = workloads.particles(cfg, n=32)
+    dev = _lib.to_device(parts, "fp32")
+    with _lib.Handle(cfg["pulse"]) as h:
+        dJ = torch.zeros((1, 4), dtype=torch.float64, device="cuda")
+        ws = torch.zeros(1 << 20, dtype=torch.float32, device="cuda")
+        with pytest.raises(_lib.APError) as e:
+            _lib.ap_push_adjoint(h.h, dev, None, None, 0.0, 0.02, 10, 5, "fp32", dJ, None, ws)
+        assert e.value.status == _lib.AP_ERR_UNSUPPORTED
+    sets, off, p2 = _sets_case(n_sets=1, per=8)
+    dev = _lib.to_device(p2, "fp32")
+    with _lib.Handle(sets) as h:
+        tiny = torch.zeros(64, dtype=torch.float32, device="cuda")
+        with pytest.raises(_lib.APError) as e:
+            _lib.ap_push_adjoint(h.h, dev, None, None, 0.0, 0.02, 10, 5, "fp32", dJ, None, tiny)
+        assert e.value.status == _lib.AP_ERR_WORKSPACE
+        assert _lib.ap_adjoint_workspace_bytes(h.h, 8, 10, 0) == 0
+        assert _lib.ap_adjoint_workspace_bytes(h.h, 8, 10, 300) == 0
