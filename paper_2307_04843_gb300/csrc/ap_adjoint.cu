@@ -125,27 +125,31 @@ template <typename R>
 __device__ __forceinline__ void grid_value_grad(const GridView &g, GridCache<R> &gc, R x, R y, R z,
                                                 GridGrad<R> &out) {
   R E[3] = {R(0), R(0), R(0)}, B[3] = {R(0), R(0), R(0)};
-  grid_gather<R>(g, gc, x, y, z, E, B);  // refreshes the cache for this cell
-  R lo[3], idd[3];
+  grid_gather<R>(g, gc, x, y, z, E, B);  // refreshes the cache and the weights
+  R idd[3], off[3];
   if constexpr (std::is_same<R, double>::value) {
-    for (int a = 0; a < 3; ++a) { lo[a] = g.lo_d[a]; idd[a] = g.inv_d_d[a]; }
+    for (int a = 0; a < 3; ++a) { idd[a] = g.inv_d_d[a]; off[a] = g.off_d[a]; }
   } else {
-    for (int a = 0; a < 3; ++a) { lo[a] = g.lo[a]; idd[a] = g.inv_d[a]; }
+    for (int a = 0; a < 3; ++a) { idd[a] = g.inv_d[a]; off[a] = g.off[a]; }
   }
-  const R fxr = (x - lo[0]) * idd[0], fyr = (y - lo[1]) * idd[1], fzr = (z - lo[2]) * idd[2];
-  const R fx = fmin(fmax(fxr, R(0)), R(g.nx - 1)), fy = fmin(fmax(fyr, R(0)), R(g.ny - 1)),
-          fz = fmin(fmax(fzr, R(0)), R(g.nz - 1));
-  const R wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
-  const R sx = (fxr == fx) ? idd[0] : R(0), sy = (fyr == fy) ? idd[1] : R(0),
-          sz = (fzr == fz) ? idd[2] : R(0);
+  // unclamped grid coordinates: the gradient vanishes along clamped axes
+  const R fxr = fma(x, idd[0], off[0]), fyr = fma(y, idd[1], off[1]), fzr = fma(z, idd[2], off[2]);
+  const R wx = gc.wx, wy = gc.wy, wz = gc.wz;
+  const R ux = R(1) - wx, uy = R(1) - wy, uz = R(1) - wz;
+  const R sx = (fxr >= R(0) && fxr <= R(g.nx - 1)) ? idd[0] : R(0);
+  const R sy = (fyr >= R(0) && fyr <= R(g.ny - 1)) ? idd[1] : R(0);
+  const R sz = (fzr >= R(0) && fzr <= R(g.nz - 1)) ? idd[2] : R(0);
   out.v[0] = E[0]; out.v[1] = E[1]; out.v[2] = E[2];
   out.v[3] = B[0]; out.v[4] = B[1]; out.v[5] = B[2];
   for (int c = 0; c < 6; ++c) {
+    // raw corners k[cx + 2 cy + 4 cz]; derivative of the trilinear weights
     const R *k = gc.c[c];
-    // f = c0 + wx (c1 + wy (c4 + wz c7) + wz c5) + wy (c2 + wz c6) + wz c3
-    R dfx = k[1] + wy * (k[4] + wz * k[7]) + wz * k[5];
-    R dfy = k[2] + wz * k[6] + wx * (k[4] + wz * k[7]);
-    R dfz = k[3] + wx * (k[5] + wy * k[7]) + wy * k[6];
+    R dfx = (k[1] - k[0]) * uy * uz + (k[3] - k[2]) * wy * uz + (k[5] - k[4]) * uy * wz +
+            (k[7] - k[6]) * wy * wz;
+    R dfy = (k[2] - k[0]) * ux * uz + (k[3] - k[1]) * wx * uz + (k[6] - k[4]) * ux * wz +
+            (k[7] - k[5]) * wx * wz;
+    R dfz = (k[4] - k[0]) * ux * uy + (k[5] - k[1]) * wx * uy + (k[6] - k[2]) * ux * wy +
+            (k[7] - k[3]) * wx * wy;
     out.g[c][0] = dfx * sx;
     out.g[c][1] = dfy * sy;
     out.g[c][2] = dfz * sz;

@@ -321,6 +321,8 @@ int make_grid(const ap_grid *g, apt::GridView &v) {
     v.inv_d_d[a] = inv;
     v.lo[a] = (float)g->lo[a];
     v.inv_d[a] = (float)inv;
+    v.off_d[a] = -g->lo[a] * inv;
+    v.off[a] = (float)v.off_d[a];
   }
   v.nx = g->nx;
   v.ny = g->ny;

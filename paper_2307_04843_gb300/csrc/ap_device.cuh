@@ -581,7 +581,8 @@ __device__ __forceinline__ void analytic_fields(const Pulse<Real<PREC>> &P,
 template <typename R>
 struct GridCache {
   R ox, oy, oz;  // lower corner of the cached cell in grid units (-16: nothing cached)
-  R c[6][8];
+  R wx, wy, wz;  // trilinear weights of the current step
+  R c[6][8];     // raw corner values c[comp][cx + 2 cy + 4 cz] of the cached cell
 };
 
 template <typename R>
@@ -591,38 +592,63 @@ __device__ __forceinline__ void grid_cache_reset(GridCache<R> &gc) {
 
 // position in grid units, clamped to the node range [0, n - 1]
 template <typename R>
-__device__ __forceinline__ R grid_unit(R v, R lo, R inv_d, int n) {
-  return fmin(fmax((v - lo) * inv_d, R(0)), R(n - 1));
+__device__ __forceinline__ R grid_unit(R v, R inv_d, R off, int n) {
+  return fmin(fmax(fma(v, inv_d, off), R(0)), R(n - 1));
 }
 
+// Phase 1 of the gather, called at the start of a step: the particle's
+// weights in its cell; on a cell change the corner values of the new cell
+// are requested into the cache (raw), so that their memory latency overlaps
+// the analytic field evaluation that runs before grid_eval.
 template <typename R>
-__device__ __forceinline__ void grid_gather(const GridView &g, GridCache<R> &gc, R x, R y, R z,
-                                            R E[3], R B[3]) {
+__device__ __forceinline__ void grid_fetch(const GridView &g, GridCache<R> &gc, R x, R y, R z) {
   R fx, fy, fz;
   if constexpr (std::is_same<R, double>::value) {
-    fx = grid_unit<R>(x, g.lo_d[0], g.inv_d_d[0], g.nx);
-    fy = grid_unit<R>(y, g.lo_d[1], g.inv_d_d[1], g.ny);
-    fz = grid_unit<R>(z, g.lo_d[2], g.inv_d_d[2], g.nz);
+    fx = grid_unit<R>(x, g.inv_d_d[0], g.off_d[0], g.nx);
+    fy = grid_unit<R>(y, g.inv_d_d[1], g.off_d[1], g.ny);
+    fz = grid_unit<R>(z, g.inv_d_d[2], g.off_d[2], g.nz);
   } else {
-    fx = grid_unit<R>(x, g.lo[0], g.inv_d[0], g.nx);
-    fy = grid_unit<R>(y, g.lo[1], g.inv_d[1], g.ny);
-    fz = grid_unit<R>(z, g.lo[2], g.inv_d[2], g.nz);
+    fx = grid_unit<R>(x, g.inv_d[0], g.off[0], g.nx);
+    fy = grid_unit<R>(y, g.inv_d[1], g.off[1], g.ny);
+    fz = grid_unit<R>(z, g.inv_d[2], g.off[2], g.nz);
   }
   R wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
   // still inside the cached cell (the upper face included, as for the last
-  // cell of the grid): no integer work, no loads
-  if (!(wx >= R(0) && wx <= R(1) && wy >= R(0) && wy <= R(1) && wz >= R(0) && wz <= R(1))) {
-    int ix = min((int)fx, g.nx - 2), iy = min((int)fy, g.ny - 2), iz = min((int)fz, g.nz - 2);
-    gc.ox = R(ix);
-    gc.oy = R(iy);
-    gc.oz = R(iz);
+  // cell of the grid): no integer work, no loads.  The warp-uniform test in
+  // front keeps the refetch a real branch (taken only when some lane of the
+  // warp changed cell) instead of predicated code issued every step; every
+  // lane of the warp calls this together.
+  const bool need = !(wx >= R(0) && wx <= R(1) && wy >= R(0) && wy <= R(1) && wz >= R(0) && wz <= R(1));
+  if (__any_sync(0xffffffffu, need) && need) {
+    int ix, iy, iz;
+    if constexpr (std::is_same<R, float>::value) {
+      // lower cell corner without the conversion pipe: rint(f - 1/2) through
+      // the 1.5 * 2^23 magic number (a face point may land in the cell below,
+      // where its weight is 1: same value), clamped to [0, n - 2]; the
+      // integer is read from the bits of (corner + magic)
+      auto corner = [](float f, int n, int &i) {
+        float c = __fsub_rn(__fadd_rn(__fsub_rn(f, 0.5f), kRoundMagic), kRoundMagic);
+        c = fminf(fmaxf(c, 0.0f), (float)(n - 2));
+        i = __float_as_int(__fadd_rn(c, kRoundMagic)) - __float_as_int(kRoundMagic);
+        return c;
+      };
+      gc.ox = corner(fx, g.nx, ix);
+      gc.oy = corner(fy, g.ny, iy);
+      gc.oz = corner(fz, g.nz, iz);
+    } else {
+      ix = min((int)fx, g.nx - 2);
+      iy = min((int)fy, g.ny - 2);
+      iz = min((int)fz, g.nz - 2);
+      gc.ox = R(ix);
+      gc.oy = R(iy);
+      gc.oz = R(iz);
+    }
     wx = fx - gc.ox;
     wy = fy - gc.oy;
     wz = fz - gc.oz;
     const size_t sx = 1, sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
     const size_t b = ((size_t)iz * g.ny + iy) * g.nx + ix;
-    // corner values v[corner][comp], corner = cx + 2 cy + 4 cz
-    float v[8][6];
+    // raw corner values c[comp][corner], corner = cx + 2 cy + 4 cz
     if (g.packed) {
       // node-interleaved: two 16-byte loads per corner, one 32-byte sector
       const size_t off[8] = {b, b + sx, b + sy, b + sy + sx, b + sz, b + sz + sx, b + sz + sy,
@@ -631,52 +657,171 @@ __device__ __forceinline__ void grid_gather(const GridView &g, GridCache<R> &gc,
       for (int k = 0; k < 8; ++k) {
         const float4 lo4 = __ldg(g.packed + 2 * off[k]);
         const float4 hi4 = __ldg(g.packed + 2 * off[k] + 1);
-        v[k][0] = lo4.x; v[k][1] = lo4.y; v[k][2] = lo4.z;
-        v[k][3] = lo4.w; v[k][4] = hi4.x; v[k][5] = hi4.y;
+        gc.c[0][k] = lo4.x; gc.c[1][k] = lo4.y; gc.c[2][k] = lo4.z;
+        gc.c[3][k] = lo4.w; gc.c[4][k] = hi4.x; gc.c[5][k] = hi4.y;
       }
     } else {
 #pragma unroll
       for (int comp = 0; comp < 6; ++comp) {
         const float *f = g.f[comp] + b;
-        v[0][comp] = __ldg(f);
-        v[1][comp] = __ldg(f + sx);
-        v[2][comp] = __ldg(f + sy);
-        v[3][comp] = __ldg(f + sy + sx);
-        v[4][comp] = __ldg(f + sz);
-        v[5][comp] = __ldg(f + sz + sx);
-        v[6][comp] = __ldg(f + sz + sy);
-        v[7][comp] = __ldg(f + sz + sy + sx);
+        R *c = gc.c[comp];
+        c[0] = __ldg(f);
+        c[1] = __ldg(f + sx);
+        c[2] = __ldg(f + sy);
+        c[3] = __ldg(f + sy + sx);
+        c[4] = __ldg(f + sz);
+        c[5] = __ldg(f + sz + sx);
+        c[6] = __ldg(f + sz + sy);
+        c[7] = __ldg(f + sz + sy + sx);
       }
     }
-#pragma unroll
-    for (int comp = 0; comp < 6; ++comp) {
-      const R v000 = v[0][comp], v100 = v[1][comp], v010 = v[2][comp], v110 = v[3][comp];
-      const R v001 = v[4][comp], v101 = v[5][comp], v011 = v[6][comp], v111 = v[7][comp];
-      R *c = gc.c[comp];
-      c[0] = v000;
-      c[1] = v100 - v000;
-      c[2] = v010 - v000;
-      c[3] = v001 - v000;
-      c[4] = (v110 - v100) - (v010 - v000);
-      c[5] = (v101 - v100) - (v001 - v000);
-      c[6] = (v011 - v010) - (v001 - v000);
-      c[7] = ((v111 - v110) - (v101 - v100)) - ((v011 - v010) - (v001 - v000));
-    }
   }
+  gc.wx = wx;
+  gc.wy = wy;
+  gc.wz = wz;
+}
+
+// The 8 trilinear weights of the cached cell, corner = cx + 2 cy + 4 cz.
+template <typename R>
+__device__ __forceinline__ void trilinear_weights(const GridCache<R> &gc, R w[8]) {
+  const R wx = gc.wx, wy = gc.wy, wz = gc.wz;
+  const R ux = R(1) - wx, uy = R(1) - wy, uz = R(1) - wz;
+  const R a00 = ux * uy, a10 = wx * uy, a01 = ux * wy, a11 = wx * wy;
+  w[0] = a00 * uz; w[1] = a10 * uz; w[2] = a01 * uz; w[3] = a11 * uz;
+  w[4] = a00 * wz; w[5] = a10 * wz; w[6] = a01 * wz; w[7] = a11 * wz;
+}
+
+// Phase 2: add the interpolated grid field to E, B, straight from the raw
+// corner values (no per-refetch conversion: a refetch by any lane would
+// otherwise cost the whole warp the conversion).
+template <typename R>
+__device__ __forceinline__ void grid_eval(GridCache<R> &gc, R E[3], R B[3]) {
+  R w[8];
+  trilinear_weights(gc, w);
   R out[6];
 #pragma unroll
   for (int comp = 0; comp < 6; ++comp) {
     const R *c = gc.c[comp];
-    R t = fma(wz, c[7], c[4]);
-    t = fma(wy, t, c[1]);
-    t = fma(wz, c[5], t);
-    R u = fma(wz, c[6], c[2]);
-    R r = fma(wx, t, c[0]);
-    r = fma(wy, u, r);
-    out[comp] = fma(wz, c[3], r);
+    R r = w[0] * c[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) r = fma(w[k], c[k], r);
+    out[comp] = r;
   }
   E[0] += out[0]; E[1] += out[1]; E[2] += out[2];
   B[0] += out[3]; B[1] += out[4]; B[2] += out[5];
+}
+
+// Both phases back to back.
+template <typename R>
+__device__ __forceinline__ void grid_gather(const GridView &g, GridCache<R> &gc, R x, R y, R z,
+                                            R E[3], R B[3]) {
+  grid_fetch(g, gc, x, y, z);
+  grid_eval(gc, E, B);
+}
+
+// ---------------------------------------------- shared-memory cell cache
+// The float kernels keep the current cell in shared memory instead of 48
+// registers (which capped occupancy at ~18 warps per SM): 16 slots of 16
+// bytes per thread, slot 2k = (Ex, Ey, Ez, Bx) and slot 2k+1 = (By, Bz, -, -)
+// of corner k = cx + 2 cy + 4 cz, slots interleaved across the block so that
+// a warp's 16-byte accesses are conflict-free.  A refetch is issued as
+// asynchronous global->shared copies (cp.async, no register staging) at the
+// start of the step and waited for just before the interpolation, after the
+// analytic field, so the copy latency overlaps that work.
+struct GridSlots {
+  float ox, oy, oz;  // lower corner of the cached cell in grid units
+  float wx, wy, wz;  // weights of the current step
+  unsigned s0;       // shared-window address of this thread's slot 0
+  unsigned step;     // bytes between consecutive slots of one thread
+};
+
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(unsigned dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ float4 lds128(unsigned addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr));
+  return v;
+}
+
+__device__ __forceinline__ void grid_slots_init(GridSlots &gc, void *slots_base) {
+  gc.ox = gc.oy = gc.oz = -16.0f;
+  gc.s0 = (unsigned)__cvta_generic_to_shared(slots_base) + 16u * threadIdx.x;
+  gc.step = 16u * blockDim.x;
+}
+
+// Every lane of the warp calls this together (warp-uniform refetch branch).
+__device__ __forceinline__ void grid_fetch(const GridView &g, GridSlots &gc, float x, float y,
+                                           float z) {
+  const float fx = grid_unit<float>(x, g.inv_d[0], g.off[0], g.nx);
+  const float fy = grid_unit<float>(y, g.inv_d[1], g.off[1], g.ny);
+  const float fz = grid_unit<float>(z, g.inv_d[2], g.off[2], g.nz);
+  float wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
+  const bool need = !(wx >= 0.0f && wx <= 1.0f && wy >= 0.0f && wy <= 1.0f && wz >= 0.0f && wz <= 1.0f);
+  if (__any_sync(0xffffffffu, need) && need) {
+    // lower cell corner without the conversion pipe (see the register cache)
+    auto corner = [](float f, int n, int &i) {
+      float c = __fsub_rn(__fadd_rn(__fsub_rn(f, 0.5f), kRoundMagic), kRoundMagic);
+      c = fminf(fmaxf(c, 0.0f), (float)(n - 2));
+      i = __float_as_int(__fadd_rn(c, kRoundMagic)) - __float_as_int(kRoundMagic);
+      return c;
+    };
+    int ix, iy, iz;
+    gc.ox = corner(fx, g.nx, ix);
+    gc.oy = corner(fy, g.ny, iy);
+    gc.oz = corner(fz, g.nz, iz);
+    wx = fx - gc.ox;
+    wy = fy - gc.oy;
+    wz = fz - gc.oz;
+    const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
+    const size_t b = ((size_t)iz * g.ny + iy) * g.nx + ix;
+    const size_t off[8] = {b, b + 1, b + sy, b + sy + 1, b + sz, b + sz + 1, b + sz + sy,
+                           b + sz + sy + 1};
+    if (g.packed) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        cp_async16(gc.s0 + (2 * k) * gc.step, g.packed + 2 * off[k]);
+        cp_async16(gc.s0 + (2 * k + 1) * gc.step, g.packed + 2 * off[k] + 1);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int comp = 0; comp < 6; ++comp)
+          cp_async4(gc.s0 + (2 * k + comp / 4) * gc.step + 4u * (comp % 4), g.f[comp] + off[k]);
+    }
+  }
+  gc.wx = wx;
+  gc.wy = wy;
+  gc.wz = wz;
+}
+
+__device__ __forceinline__ void grid_eval(const GridSlots &gc, float E[3], float B[3]) {
+  cp_async_wait_all();  // this thread's copies (if any) have landed
+  const float ux = 1.0f - gc.wx, uy = 1.0f - gc.wy, uz = 1.0f - gc.wz;
+  const float a00 = ux * uy, a10 = gc.wx * uy, a01 = ux * gc.wy, a11 = gc.wx * gc.wy;
+  const float w[8] = {a00 * uz, a10 * uz, a01 * uz, a11 * uz, a00 * gc.wz, a10 * gc.wz,
+                      a01 * gc.wz, a11 * gc.wz};
+  float o[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float4 lo = lds128(gc.s0 + (2 * k) * gc.step);
+    const float4 hi = lds128(gc.s0 + (2 * k + 1) * gc.step);
+    o[0] = fmaf(w[k], lo.x, o[0]);
+    o[1] = fmaf(w[k], lo.y, o[1]);
+    o[2] = fmaf(w[k], lo.z, o[2]);
+    o[3] = fmaf(w[k], lo.w, o[3]);
+    o[4] = fmaf(w[k], hi.x, o[4]);
+    o[5] = fmaf(w[k], hi.y, o[5]);
+  }
+  E[0] += o[0]; E[1] += o[1]; E[2] += o[2];
+  B[0] += o[3]; B[1] += o[4]; B[2] += o[5];
 }
 
 // ------------------------------------------------------------ Boris push

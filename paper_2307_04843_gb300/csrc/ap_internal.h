@@ -63,6 +63,8 @@ struct GridView {
   int nx, ny, nz;
   float lo[3], inv_d[3];  // node spacing d = (hi - lo)/(n - 1)
   double lo_d[3], inv_d_d[3];
+  float off[3];           // -lo / d: grid units u = x inv_d + off
+  double off_d[3];
 };
 
 // Diagnostics view.

@@ -10,7 +10,26 @@ namespace apt {
 // Steps per chunk of the per-warp step table (float-float variant): one
 // entry per lane.
 constexpr int kStepChunk = 32;
-constexpr int kMaxWarps = 8;  // 256 threads per block at most
+
+// Dynamic shared memory of the push kernels, per block of T threads: the
+// per-warp step tables (16 B per thread), then for the float grid kernels the
+// cell-cache slots (16 slots x 16 B per thread).
+__host__ __device__ constexpr size_t step_table_bytes(int threads) { return 16u * (size_t)threads; }
+__host__ __device__ constexpr size_t grid_slot_bytes(int threads) { return 256u * (size_t)threads; }
+
+// Grid cell cache of a variant: registers for double, shared memory for float.
+template <int PREC, bool GRID>
+struct CacheOf {
+  using type = GridCache<Real<PREC>>;
+};
+template <>
+struct CacheOf<AP_FP32_PHASE64, true> {
+  using type = GridSlots;
+};
+template <>
+struct CacheOf<AP_FP32_PHASEFF, true> {
+  using type = GridSlots;
+};
 
 // One particle through n_steps fused steps: load (a2), per step the local
 // coordinates and phase (a3), envelope and profile (a4-a7), grid gather
@@ -23,7 +42,8 @@ constexpr int kMaxWarps = 8;  // 256 threads per block at most
 // Returns the final gamma (double) of a valid particle, 0 otherwise.
 template <int KIND, int PREC, bool GRID>
 __device__ __forceinline__ double push_one(const Pulse<Real<PREC>> &P, const PushArgs &a,
-                                           long long i, bool valid, StepFF *s_steps) {
+                                           long long i, bool valid, StepFF *s_steps,
+                                           void *slots) {
   using R = Real<PREC>;
   double X = 0.0, Y = 0.0, Z = 0.0;
   R u[3] = {R(0), R(0), R(0)};
@@ -44,8 +64,9 @@ __device__ __forceinline__ double push_one(const Pulse<Real<PREC>> &P, const Pus
   tb.init(P, a.t0, a.dt);
   const R dtR = (R)a.dt;
   const R h0 = R(1) / rsqrt_r(fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], R(1))))) - u[2];
-  GridCache<R> gc;
-  grid_cache_reset(gc);
+  typename CacheOf<PREC, GRID>::type gc;
+  if constexpr (GRID && !std::is_same<R, double>::value) grid_slots_init(gc, slots);
+  else grid_cache_reset(gc);
   double *lf = a.diag.lf;
   StepFF *wsteps = s_steps + (threadIdx.x >> 5) * kStepChunk;
   const int lane = threadIdx.x & 31;
@@ -61,9 +82,10 @@ __device__ __forceinline__ double push_one(const Pulse<Real<PREC>> &P, const Pus
       if constexpr (PREC == AP_FP32_PHASEFF) st = wsteps[k];
       else st = tb.at(s0 + k);
       Local<R> L = local_coords<PREC>(P, st, pos);
+      if constexpr (GRID) grid_fetch(a.grid, gc, L.x, L.y, pos.zr());
       R E[3], B[3];
       analytic_fields<KIND, PREC>(P, L, E, B);
-      if constexpr (GRID) grid_gather<R>(a.grid, gc, L.x, L.y, pos.zr(), E, B);
+      if constexpr (GRID) grid_eval(gc, E, B);
       R ig = boris(u, E, B, dtR);
       pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtR);
       if (lf) {
@@ -110,13 +132,17 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
 
 // Plain launch: a grid-stride loop over block-sized chunks of particles (the
 // trip count is uniform across the block), one particle per thread, every
-// step fused.
+// step fused.  Dynamic shared memory: step tables, grid slots (float grid
+// kernels), then the histogram (hist_off bytes in).
 template <int KIND, int PREC, bool GRID>
-__global__ void __launch_bounds__(256) push_kernel(const __grid_constant__ Pulse<Real<PREC>> P,
-                                                   const __grid_constant__ PushArgs a) {
-  extern __shared__ uint32_t s_hist[];
+__global__ void __launch_bounds__(256)
+    push_kernel(const __grid_constant__ Pulse<Real<PREC>> P, const __grid_constant__ PushArgs a,
+                unsigned hist_off) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ double s_red[32];
-  __shared__ StepFF s_steps[kMaxWarps * kStepChunk];
+  StepFF *s_steps = reinterpret_cast<StepFF *>(s_dyn);
+  void *slots = s_dyn + step_table_bytes(blockDim.x);
+  uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_dyn + hist_off);
   const bool hist = a.diag.hist != nullptr;
   if (hist) {
     for (int b = threadIdx.x; b < a.diag.bins; b += blockDim.x) s_hist[b] = 0u;
@@ -127,7 +153,7 @@ __global__ void __launch_bounds__(256) push_kernel(const __grid_constant__ Pulse
   for (long long base = (long long)blockIdx.x * blockDim.x; base < a.n; base += stride) {
     const long long i = base + threadIdx.x;
     const bool valid = i < a.n;
-    double g = push_one<KIND, PREC, GRID>(P, a, i, valid, s_steps);
+    double g = push_one<KIND, PREC, GRID>(P, a, i, valid, s_steps, slots);
     if (valid) {
       acc += g;
       if (hist) hist_add(s_hist, a.diag, g);
@@ -148,15 +174,20 @@ __global__ void __launch_bounds__(256) push_kernel(const __grid_constant__ Pulse
 // (set, particles) from a global counter until the tile count is reached;
 // each set's pulse is copied to shared memory; the loop is bounded by the
 // tile count and no block waits on another.
+// Dynamic shared memory: step tables, grid slots (float grid kernels), then
+// the [n_sets + 1] tile prefix (prefix_off bytes in).
 template <int KIND, int PREC, bool GRID>
 __global__ void __launch_bounds__(256) batch_kernel(const Pulse<Real<PREC>> *__restrict__ sets,
-                                                    const __grid_constant__ BatchArgs ba) {
+                                                    const __grid_constant__ BatchArgs ba,
+                                                    unsigned prefix_off) {
   using R = Real<PREC>;
-  extern __shared__ long long s_prefix[];  // [n_sets + 1] tile prefix
+  extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ double s_red[32];
   __shared__ long long s_tile;
   __shared__ int s_set;
-  __shared__ StepFF s_steps[kMaxWarps * kStepChunk];
+  StepFF *s_steps = reinterpret_cast<StepFF *>(s_dyn);
+  void *slots = s_dyn + step_table_bytes(blockDim.x);
+  long long *s_prefix = reinterpret_cast<long long *>(s_dyn + prefix_off);
   __shared__ __align__(16) unsigned char s_pulse_raw[sizeof(Pulse<R>)];
   Pulse<R> &sp = *reinterpret_cast<Pulse<R> *>(s_pulse_raw);
   const PushArgs &a = ba.base;
@@ -203,7 +234,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const Pulse<Real<PREC>> *__r
     for (int k = threadIdx.x; k < T; k += blockDim.x) {
       const long long i = first + k;
       const bool valid = i >= 0 && i < end_set && i < a.n;
-      double g = push_one<KIND, PREC, GRID>(sp, a, i, valid, s_steps);
+      double g = push_one<KIND, PREC, GRID>(sp, a, i, valid, s_steps, slots);
       if (valid) acc += g;
     }
     if (a.diag.set_sum) {
@@ -247,23 +278,37 @@ inline int occupancy_blocks(K kernel, int block, size_t smem) {
   return nb > 0 ? nb : 1;
 }
 
+// dynamic shared memory before the kernel-specific tail (histogram / prefix)
+template <int PREC, bool GRID>
+inline size_t push_smem_head(int block) {
+  size_t s = step_table_bytes(block);
+  if (GRID && PREC != AP_FP64) s += grid_slot_bytes(block);
+  return s;
+}
+
+template <typename K>
+inline int set_smem(K kern, size_t smem) {
+  if (smem <= 48 * 1024) return AP_OK;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                 cudaSuccess
+             ? AP_OK
+             : AP_ERR_CUDA;
+}
+
 template <int KIND, int PREC, bool GRID>
 int launch_push_t(const Pulse<Real<PREC>> &P, const PushArgs &a, void *stream) {
   auto kern = push_kernel<KIND, PREC, GRID>;
   const int block = a.shape.block;
-  const size_t smem = a.diag.hist ? (size_t)a.diag.bins * sizeof(uint32_t) : 0;
-  if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return AP_ERR_CUDA;
-  }
+  const size_t head = push_smem_head<PREC, GRID>(block);
+  const size_t smem = head + (a.diag.hist ? (size_t)a.diag.bins * sizeof(uint32_t) : 0);
+  if (set_smem(kern, smem) != AP_OK) return AP_ERR_CUDA;
   const long long npad = (a.n + 31) & ~31LL;
   long long want = (npad + block - 1) / block;
   int per_sm = a.shape.blocks_per_sm > 0 ? a.shape.blocks_per_sm : occupancy_blocks(kern, block, smem);
   long long cap = (long long)a.sm_count * per_sm;
   int grid = (int)(want < cap ? want : cap);
   if (grid < 1) grid = 1;
-  kern<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(P, a);
+  kern<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(P, a, (unsigned)head);
   return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }
 
@@ -279,16 +324,13 @@ template <int KIND, int PREC, bool GRID>
 int launch_batch_t(const Pulse<Real<PREC>> *sets, const BatchArgs &ba, void *stream) {
   auto kern = batch_kernel<KIND, PREC, GRID>;
   const int block = ba.base.shape.block;
-  const size_t smem = (size_t)(ba.n_sets + 1) * sizeof(long long);
-  if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return AP_ERR_CUDA;
-  }
+  const size_t head = push_smem_head<PREC, GRID>(block);
+  const size_t smem = head + (size_t)(ba.n_sets + 1) * sizeof(long long);
+  if (set_smem(kern, smem) != AP_OK) return AP_ERR_CUDA;
   int per_sm = ba.base.shape.blocks_per_sm > 0 ? ba.base.shape.blocks_per_sm
                                                 : occupancy_blocks(kern, block, smem);
   const int grid = ba.base.sm_count * per_sm;
-  kern<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(sets, ba);
+  kern<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(sets, ba, (unsigned)head);
   return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }
 
