@@ -65,6 +65,10 @@ extern "C" {
 #define AP_LG 2           /* Laguerre-Gaussian LG_pl, named in Sec. 3.1 (textbook form) */
 #define AP_FLYING_SUM 3   /* flying focus as a linear superposition of Gaussian spectral
                              components (Sec. 3.3) */
+#define AP_FLYING_CF 4    /* closed-form Gaussian flying focus (Sec. 3.3, modified paraxial
+                             limit): Eq. paraxial with x_f - x -> xi0 - xi, xi = z - v_f t,
+                             x_R -> (1 - beta_f) x_R; focus at z_focus at t_focus, which is
+                             also when the envelope peak is there; beta_f < 1 */
 /* polarisation vector p */
 #define AP_LIN_X 0        /* p = (1, 0) */
 #define AP_LIN_Y 1        /* p = (0, 1) */
@@ -114,7 +118,8 @@ typedef struct {
                          time t_a at which the focus is at z_a */
   double env_len;     /* see AP_ENV_* */
   double phase0;      /* carrier phase at (t_focus, z_focus) */
-  double beta_f;      /* flying focus: focal velocity v_f / c (nonzero) */
+  double beta_f;      /* flying focus: focal velocity v_f / c (AP_FLYING_SUM: nonzero;
+                         AP_FLYING_CF: below 1, may be negative) */
   double bw_frac;     /* flying focus: frequencies span omega (1 +- bw_frac) */
   double ff_length;   /* flying focus: length L of the focal range */
   double yee_dx, yee_dt; /* AP_F_YEE_DISP: cell size and time step of the Yee solver */
@@ -296,8 +301,10 @@ size_t ap_adjoint_workspace_bytes(ap_handle h, int64_t n, int64_t n_steps, int32
  * reduced warp -> block -> FP64 atomics into dJ_dparams (device double
  * [n_sets][AP_NPARAM]) and J into J_out (device double [n_sets], nullable).
  * The call zeroes both.  The grid, if given, enters the forward trajectory
- * and the position adjoint.  precision: AP_FP32_PHASEFF or AP_FP64.
- * Errors: AP_ERR_ARG, AP_ERR_ALIGN, AP_ERR_WORKSPACE, AP_ERR_CUDA. */
+ * and the position adjoint.  precision: AP_FP32_PHASEFF or AP_FP64.  The
+ * beta_f row is nonzero only for AP_FLYING_CF.
+ * Errors: AP_ERR_ARG, AP_ERR_ALIGN, AP_ERR_WORKSPACE, AP_ERR_CUDA;
+ * AP_ERR_UNSUPPORTED for AP_FLYING_SUM or another precision. */
 int ap_push_adjoint(ap_handle h, const ap_particles *p0, const ap_grid *g, double t0, double dt,
                     int64_t n_steps, int32_t ckpt_every, int32_t objective, int32_t precision,
                     double *dJ_dparams, double *J_out, void *workspace, size_t ws_bytes,

@@ -13,7 +13,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KINDS = {"plane": 0, "gauss": 1, "lg": 2, "flying": 3}
+KINDS = {"plane": 0, "gauss": 1, "lg": 2, "flying": 3, "flying_cf": 4}
 POLS = {"x": 0, "y": 1, "cp": 2, "cm": 3}
 ENVS = {"sin2": 0, "gauss": 1, "sgauss": 2, "cw": 3}
 MAX_COMP = 256
@@ -73,7 +73,7 @@ def lib():
         L.or_prepare.restype = ctypes.c_int
         L.or_envelope.argtypes = [ctypes.POINTER(_State), ctypes.c_double]
         L.or_envelope.restype = ctypes.c_double
-        L.or_profile.argtypes = [ctypes.POINTER(_State), ctypes.c_int] + [ctypes.c_double] * 3 + [dp, dp]
+        L.or_profile.argtypes = [ctypes.POINTER(_State), ctypes.c_int] + [ctypes.c_double] * 4 + [dp, dp]
         L.or_profile.restype = None
         L.or_fields.argtypes = [ctypes.POINTER(_State)] + [ctypes.c_double] * 4 + [dp]
         L.or_fields.restype = None
@@ -152,11 +152,11 @@ def fields(pulse, x, y, z, t):
     return out.reshape((6,) + shape)
 
 
-def profile(pulse, x, y, z, j=0):
-    """Complex transverse profile u at one point."""
+def profile(pulse, x, y, z, j=0, t=0.0):
+    """Complex transverse profile u at one point (t: closed-form flying focus)."""
     st = prepare(pulse)
     re, im = ctypes.c_double(), ctypes.c_double()
-    lib().or_profile(ctypes.byref(st), j, x, y, z, ctypes.byref(re), ctypes.byref(im))
+    lib().or_profile(ctypes.byref(st), j, x, y, z, t, ctypes.byref(re), ctypes.byref(im))
     return complex(re.value, im.value)
 
 

@@ -82,7 +82,7 @@ static void polarisation(int pol, double complex *px, double complex *py) {
 int or_prepare(const or_pulse *p, or_state *s) {
   s->p = *p;
   if (!(p->omega > 0.0)) return -1;
-  if (p->kind < OR_PLANE || p->kind > OR_FLYING) return -1;
+  if (p->kind < OR_PLANE || p->kind > OR_FLYING_CF) return -1;
   /* Phase velocity, group velocity and B0/E0: vacuum unless the second-order
    * Yee expressions are requested (Eqs. vphi, vg, e_amp, Sec. 2.1). */
   s->vphi = 1.0;
@@ -100,9 +100,10 @@ int or_prepare(const or_pulse *p, or_state *s) {
   s->zR = 0.5 * s->k * p->w0 * p->w0;
   s->amp = p->a0;
   s->n = 0;
-  if (p->kind == OR_GAUSS || p->kind == OR_LG || p->kind == OR_FLYING) {
+  if (p->kind != OR_PLANE) {
     if (!(p->w0 > 0.0)) return -1;
   }
+  if (p->kind == OR_FLYING_CF && !(p->beta_f < 1.0)) return -1;
   if (p->kind == OR_LG) {
     if (p->lg_p < 0) return -1;
     int al = p->lg_l < 0 ? -p->lg_l : p->lg_l;
@@ -145,7 +146,7 @@ int or_prepare(const or_pulse *p, or_state *s) {
       double complex S = 0.0;
       for (int j = 0; j < n; ++j) {
         double ur, ui;
-        or_profile(s, j, 0.0, 0.0, zi, &ur, &ui);
+        or_profile(s, j, 0.0, 0.0, zi, 0.0, &ur, &ui);
         double psi = s->fw[j] * s->t_mid - s->fk[j] * zi - s->fphi[j];
         S += (ur + I * ui) * cexp(I * psi);
       }
@@ -188,12 +189,22 @@ double or_envelope(const or_state *s, double eta) {
  *   u = A (w0/w) e^{-r^2/w^2} e^{-i k r^2 / (2R)} e^{+i atan zeta}
  * and for LG_pl (textbook) the extra factor
  *   (sqrt(2) r / w)^{|l|} L_p^{|l|}(2 r^2 / w^2) e^{i (2p + |l|) atan zeta} e^{i l theta}. */
-void or_profile(const or_state *s, int j, double x, double y, double z, double *re, double *im) {
+void or_profile(const or_state *s, int j, double x, double y, double z, double t, double *re,
+                double *im) {
   const or_pulse *p = &s->p;
   double zf = s->p.z_focus, zR = s->zR, k = s->k, A = s->amp;
   if (p->kind == OR_PLANE) { *re = A; *im = 0.0; return; }
   if (p->kind == OR_FLYING) { zf = s->fz[j]; zR = s->fzR[j]; k = s->fk[j]; }
   double dz = z - zf;
+  if (p->kind == OR_FLYING_CF) {
+    /* Sec. 3.3: Eq. paraxial with x_f - x -> xi0 - xi, xi = z - v_f t,
+     * xi0 = z_f - v_f t_f, and the wavenumber of the transverse profile
+     * k (1 - beta_f), so that x_R -> (1 - beta_f) x_R and the profile solves
+     * the reduced flying-focus paraxial equation. */
+    dz = (z - p->beta_f * t) - (p->z_focus - p->beta_f * p->t_focus);
+    zR = (1.0 - p->beta_f) * s->zR;
+    k = (1.0 - p->beta_f) * s->k;
+  }
   double zeta = dz / zR;
   double w = p->w0 * sqrt(1.0 + zeta * zeta);
   double invR = dz / (dz * dz + zR * zR);
@@ -211,20 +222,20 @@ void or_profile(const or_state *s, int j, double x, double y, double z, double *
   *im = mag * sin(phase);
 }
 
-static double complex profile_c(const or_state *s, int j, double x, double y, double z) {
+static double complex profile_c(const or_state *s, int j, double x, double y, double z, double t) {
   double re, im;
-  or_profile(s, j, x, y, z, &re, &im);
+  or_profile(s, j, x, y, z, t, &re, &im);
   return re + I * im;
 }
 
 /* 4th-order central differences of the profile in x and y, h = 1e-3 w0. */
-static void profile_grad(const or_state *s, int j, double x, double y, double z,
+static void profile_grad(const or_state *s, int j, double x, double y, double z, double t,
                          double complex *dx, double complex *dy) {
   double h = 1e-3 * s->p.w0;
-  *dx = (profile_c(s, j, x - 2 * h, y, z) - 8.0 * profile_c(s, j, x - h, y, z) +
-         8.0 * profile_c(s, j, x + h, y, z) - profile_c(s, j, x + 2 * h, y, z)) / (12.0 * h);
-  *dy = (profile_c(s, j, x, y - 2 * h, z) - 8.0 * profile_c(s, j, x, y - h, z) +
-         8.0 * profile_c(s, j, x, y + h, z) - profile_c(s, j, x, y + 2 * h, z)) / (12.0 * h);
+  *dx = (profile_c(s, j, x - 2 * h, y, z, t) - 8.0 * profile_c(s, j, x - h, y, z, t) +
+         8.0 * profile_c(s, j, x + h, y, z, t) - profile_c(s, j, x + 2 * h, y, z, t)) / (12.0 * h);
+  *dy = (profile_c(s, j, x, y - 2 * h, z, t) - 8.0 * profile_c(s, j, x, y - h, z, t) +
+         8.0 * profile_c(s, j, x, y + h, z, t) - profile_c(s, j, x, y + 2 * h, z, t)) / (12.0 * h);
 }
 
 /* ---------------------------------------------------------------- fields */
@@ -241,10 +252,10 @@ void or_fields(const or_state *s, double x, double y, double z, double t, double
     for (int j = 0; j < s->n; ++j) {
       double psi = s->fw[j] * t - s->fk[j] * z - s->fphi[j] + p->phase0;
       double complex ph = cexp(I * psi);
-      U += profile_c(s, j, x, y, z) * ph;
+      U += profile_c(s, j, x, y, z, t) * ph;
       if (lon) {
         double complex gx, gy;
-        profile_grad(s, j, x, y, z, &gx, &gy);
+        profile_grad(s, j, x, y, z, t, &gx, &gy);
         /* divergence conditions: d/dz -> -i k_j */
         DX += (-I / s->fk[j]) * gx * ph;
         DY += (-I / s->fk[j]) * gy * ph;
@@ -255,10 +266,10 @@ void or_fields(const or_state *s, double x, double y, double z, double t, double
     double G = or_envelope(s, eta);
     double psi = p->omega * (t - p->t_focus) - s->k * (z - p->z_focus) + p->phase0;
     double complex ph = G * cexp(I * psi);
-    U = profile_c(s, 0, x, y, z) * ph;
+    U = profile_c(s, 0, x, y, z, t) * ph;
     if (lon) {
       double complex gx, gy;
-      profile_grad(s, 0, x, y, z, &gx, &gy);
+      profile_grad(s, 0, x, y, z, t, &gx, &gy);
       DX = gx * ph;
       DY = gy * ph;
     }

@@ -42,6 +42,7 @@ extern "C" {
 #define OR_GAUSS 1   /* paraxial Gaussian (LG_00), Eq. paraxial, D = 3 */
 #define OR_LG 2      /* Laguerre-Gaussian LG_pl (named in Sec. 3.1, textbook form) */
 #define OR_FLYING 3  /* flying focus as a sum of Gaussian spectral components (Sec. 3.3) */
+#define OR_FLYING_CF 4 /* closed-form Gaussian flying focus (Sec. 3.3, modified paraxial limit) */
 
 /* polarisations: p = (1,0), (0,1), (1,-i), (1,+i) */
 #define OR_LIN_X 0
@@ -68,7 +69,7 @@ typedef struct {
                                flying focus: start z_a of the focal range and its time t_a */
   double env_len;           /* SIN2: cycles N; GAUSS: intensity FWHM; SGAUSS: tau */
   double phase0;
-  double beta_f;            /* flying focus: focal velocity v_f / c */
+  double beta_f;            /* flying focus: focal velocity v_f / c (closed form: < 1) */
   double bw_frac;           /* flying focus: half-width of the frequency spread / omega */
   double ff_length;         /* flying focus: length L of the focal range */
   double yee_dx, yee_dt;    /* cell size and time step entering Eqs. vphi, vg, e_amp */
@@ -93,8 +94,10 @@ int or_prepare(const or_pulse *p, or_state *s);
 double or_envelope(const or_state *s, double eta);
 
 /* Complex transverse profile u of one beam (component j for the flying focus,
- * ignored otherwise) at (x, y, z), returned as re/im. */
-void or_profile(const or_state *s, int j, double x, double y, double z, double *re, double *im);
+ * ignored otherwise) at (x, y, z) and time t (used by the closed-form flying
+ * focus only), returned as re/im. */
+void or_profile(const or_state *s, int j, double x, double y, double z, double t, double *re,
+                double *im);
 
 /* Analytic E1, B1 at (x, y, z, t): EB = {Ex, Ey, Ez, Bx, By, Bz}. */
 void or_fields(const or_state *s, double x, double y, double z, double t, double EB[6]);

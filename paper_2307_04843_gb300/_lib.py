@@ -24,7 +24,7 @@ AP_ERR_TIMEOUT = -5
 AP_ERR_WORKSPACE = -6
 AP_ERR_UNSUPPORTED = -7
 
-KINDS = {"plane": 0, "gauss": 1, "lg": 2, "flying": 3}
+KINDS = {"plane": 0, "gauss": 1, "lg": 2, "flying": 3, "flying_cf": 4}
 POLS = {"x": 0, "y": 1, "cp": 2, "cm": 3}
 ENVS = {"sin2": 0, "gauss": 1, "sgauss": 2, "cw": 3}
 PRECISIONS = {"fp64": 0, "fp32_phase64": 1, "fp32": 2, "fp32_phaseff": 2}

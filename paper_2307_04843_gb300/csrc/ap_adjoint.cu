@@ -1,7 +1,8 @@
 // ap_adjoint.cu -- discrete adjoint of the gather + Boris push (row a13).
 //
 // Objective per set s: J_s = (1/N_s) sum_{i in s} gamma_i(T).  Gradients with
-// respect to the pulse parameters theta = (a0, w0, z_f) of every set, by the
+// respect to the pulse parameters theta = (a0, w0, z_f, beta_f) of every set
+// (beta_f only for the closed-form flying focus; zero otherwise), by the
 // exact reverse of the discrete forward map (the same float-float or double
 // arithmetic as ap_gather_push):
 //
@@ -12,8 +13,8 @@
 //
 // with seed lu^N = u^N / (gamma^N N_s), lx^N = 0.  dF/dx and dF/dtheta come
 // from the field functions instantiated with forward-mode dual numbers
-// seeded in (x, y, z - z_f, w0); a0 enters linearly (dF/da0 = F / a0) and
-// z_f only through z - z_f (dF/dz_f = -dF/dz for the analytic part).
+// seeded in (x, y, z - z_f, w0, beta_f); a0 enters linearly (dF/da0 = F / a0)
+// and z_f only through z - z_f (dF/dz_f = -dF/dz for the analytic part).
 //
 // Memory: one persistent launch; every resident thread slot pushes its
 // particle forward storing a checkpoint every K steps, then sweeps the
@@ -33,15 +34,17 @@ constexpr int kAdjBlock = 128;
 constexpr int kAdjBlocksPerSm = 4;
 constexpr int kAdjMaxK = 256;
 constexpr int kAdjStateBytes = 48;  // one saved state: 6 doubles or 9 floats
-using D4f = Dual<float, 4>;
+constexpr int kTan = 5;  // tangents: x, y, z - z_f, w0, beta_f
+constexpr int kNp = 4;   // parameters: a0, w0, z_f, beta_f
 
-// Pulse view with the w0-dependent constants as duals (tangent slot 3).
+// Pulse view with the w0-dependent constants as duals (tangent slot 3) and,
+// for the closed-form flying focus, the beta_f-dependent ones (slot 4).
 template <typename R>
 struct PulseAD {
   int32_t kind, pol, env, lon, lg_p, lg_al, lg_sgn, sg_order;
   R amp, bratio, lonE, lonB, env_a, env_b, px_re, px_im, py_re, py_im;
   R lg_c[kLgMaxP + 1];
-  Dual<R, 4> inv_w0sq, inv_zR, lg_pref;
+  Dual<R, kTan> inv_w0sq, inv_zR, lg_pref, beta_f;
 };
 
 template <typename R>
@@ -56,9 +59,13 @@ __device__ __forceinline__ PulseAD<R> make_ad(const Pulse<R> &P) {
   for (int i = 0; i <= kLgMaxP; ++i) A.lg_c[i] = P.lg_c[i];
   const R iw = P.inv_w0;
   // d(1/w0^2)/dw0 = -2/w0^3; z_R ~ w0^2; (sqrt2/w0)^|l| ~ w0^-|l|
-  A.inv_w0sq = Dual<R, 4>::seed(P.inv_w0sq, 3, R(-2) * P.inv_w0sq * iw);
-  A.inv_zR = Dual<R, 4>::seed(P.inv_zR, 3, R(-2) * P.inv_zR * iw);
-  A.lg_pref = Dual<R, 4>::seed(P.lg_pref, 3, -R(P.lg_al) * P.lg_pref * iw);
+  A.inv_w0sq = Dual<R, kTan>::seed(P.inv_w0sq, 3, R(-2) * P.inv_w0sq * iw);
+  A.inv_zR = Dual<R, kTan>::seed(P.inv_zR, 3, R(-2) * P.inv_zR * iw);
+  A.lg_pref = Dual<R, kTan>::seed(P.lg_pref, 3, -R(P.lg_al) * P.lg_pref * iw);
+  // closed-form flying focus: zeta = ((z - z_f) - beta_f (t - t_f)) / z_R',
+  // 1/z_R' = 1 / ((1 - beta_f) z_R) -> d/dbeta_f = (1/z_R') / (1 - beta_f)
+  A.beta_f = Dual<R, kTan>::seed(P.beta_f, 4, P.kind == AP_FLYING_CF ? R(1) : R(0));
+  if (P.kind == AP_FLYING_CF) A.inv_zR.d[4] = P.inv_zR * P.inv_1mb;
   return A;
 }
 
@@ -157,28 +164,29 @@ __device__ __forceinline__ void grid_value_grad(const GridView &g, GridCache<R> 
 }
 
 template <int KIND, typename R>
-__device__ __forceinline__ void fields_ad(const PulseAD<R> &A, const Local<Dual<R, 4>> &L,
-                                          Dual<R, 4> E[3], Dual<R, 4> B[3]) {
+__device__ __forceinline__ void fields_ad(const PulseAD<R> &A, const Local<Dual<R, kTan>> &L,
+                                          Dual<R, kTan> E[3], Dual<R, kTan> B[3]) {
   if constexpr (KIND == AP_PLANE) fields_plane(A, L, E, B);
   else if constexpr (KIND == AP_GAUSS) fields_gauss(A, L, E, B);
+  else if constexpr (KIND == AP_FLYING_CF) fields_gauss<true>(A, L, E, B);
   else fields_lg(A, L, E, B);
 }
 
 // One reverse step.  State before the step (pos, u), step value st, adjoints
 // lx, lu of the state after the step (updated in place to the state before),
-// gradient accumulators g[0..2] = d/d(a0, w0, z_f).
+// gradient accumulators g[0..3] = d/d(a0, w0, z_f, beta_f).
 template <int KIND, int PREC, bool GRID>
 __device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P, const PulseAD<Real<PREC>> &A,
                                              const AdjArgs &aa, const typename TimeBase<PREC>::Step &st,
                                              const Pos<PREC> &pos, const Real<PREC> u[3],
-                                             Real<PREC> lx[3], Real<PREC> lu[3], Real<PREC> g[3],
+                                             Real<PREC> lx[3], Real<PREC> lu[3], Real<PREC> g[kNp],
                                              GridCache<Real<PREC>> &gc) {
   using R = Real<PREC>;
-  using DR = Dual<R, 4>;
+  using DR = Dual<R, kTan>;
   const R dt = (R)aa.base.dt;
   const R h = R(-0.5) * dt;
   const R a0 = P.a0;
-  // fields with derivatives in (x, y, z - z_f, w0)
+  // fields with derivatives in (x, y, z - z_f, w0, beta_f)
   Local<R> L = local_coords<PREC>(P, st, pos);
   Local<DR> LD;
   LD.x = DR::seed(L.x, 0);
@@ -188,11 +196,12 @@ __device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P, const P
   LD.psi.d[2] = -R(P.k);  // psi = C - k (z - z_f)
   LD.eta = DR(L.eta);
   LD.eta.d[2] = -P.inv_vg;  // eta = T - (z - z_f) / v_g
+  LD.T = DR(L.T);
   LD.phi_hi = DR(R(0));
   LD.phi_lo = DR(R(0));
   DR Ed[3], Bd[3];
   fields_ad<KIND, R>(A, LD, Ed, Bd);
-  R F[6], dFx[6][3], dFth[6][3];  // field, d/dx, d/d(a0, w0, z_f)
+  R F[6], dFx[6][3], dFth[6][kNp];  // field, d/dx, d/d(a0, w0, z_f, beta_f)
   const DR *Fd[6] = {&Ed[0], &Ed[1], &Ed[2], &Bd[0], &Bd[1], &Bd[2]};
   for (int c = 0; c < 6; ++c) {
     const DR &f = *Fd[c];
@@ -203,6 +212,7 @@ __device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P, const P
     dFth[c][0] = f.v;
     dFth[c][1] = a0 * f.d[3];
     dFth[c][2] = -a0 * f.d[2];
+    dFth[c][3] = a0 * f.d[4];
   }
   if constexpr (GRID) {
     GridGrad<R> gg;
@@ -265,7 +275,7 @@ __device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P, const P
   const R Fb[6] = {Eb[0], Eb[1], Eb[2], Bb[0], Bb[1], Bb[2]};
   for (int c = 0; c < 6; ++c) {
     for (int k = 0; k < 3; ++k) lx[k] += Fb[c] * dFx[c][k];
-    for (int k = 0; k < 3; ++k) g[k] += Fb[c] * dFth[c][k];
+    for (int k = 0; k < kNp; ++k) g[k] += Fb[c] * dFth[c][k];
   }
 }
 
@@ -366,7 +376,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const Pulse<Real<PRE
     R lx[3] = {R(0), R(0), R(0)}, lu[3];
     for (int k = 0; k < 3; ++k) lu[k] = valid ? (R)((double)u[k] / (gN * Ns)) : R(0);
     double Jv = valid ? gN / Ns : 0.0;
-    double gacc[3] = {0.0, 0.0, 0.0};
+    double gacc[kNp] = {0.0, 0.0, 0.0, 0.0};
     const PulseAD<R> A = make_ad(P);
     // ---- reverse sweep over segments
     for (int seg = aa.n_seg - 1; seg >= 0; --seg) {
@@ -390,7 +400,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const Pulse<Real<PRE
         R ig = boris(u, E, B, dtR);
         pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtR);
       }
-      R gs[3] = {R(0), R(0), R(0)};
+      R gs[kNp] = {R(0), R(0), R(0), R(0)};
       for (int k = cnt - 1; k >= 0; --k) {
         IO::get(tp + (size_t)k * IO::W * stride, stride, pos, u);
         typename TimeBase<PREC>::Step st;
@@ -398,16 +408,16 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const Pulse<Real<PRE
         else st = tb.at(s0 + k);
         reverse_step<KIND, PREC, GRID>(P, A, aa, st, pos, u, lx, lu, gs, gc);
       }
-      for (int k = 0; k < 3; ++k) gacc[k] += (double)gs[k];
+      for (int k = 0; k < kNp; ++k) gacc[k] += (double)gs[k];
     }
     if (!valid) {
-      gacc[0] = gacc[1] = gacc[2] = 0.0;
+      gacc[0] = gacc[1] = gacc[2] = gacc[3] = 0.0;
       Jv = 0.0;
-    } else if (!(isfinite(gacc[0]) && isfinite(gacc[1]) && isfinite(gacc[2]))) {
+    } else if (!(isfinite(gacc[0]) && isfinite(gacc[1]) && isfinite(gacc[2]) && isfinite(gacc[3]))) {
       atomicOr(a.status, kStatusNonfinite);
     }
     // per-set reduction (every particle of the tile belongs to `set`)
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kNp; ++k) {
       double t = block_sum(gacc[k], s_red);
       if (threadIdx.x == 0) atomicAdd(aa.dJ + (size_t)set * AP_NPARAM + k, t);
     }
@@ -516,6 +526,8 @@ int ap_push_adjoint(ap_handle h, const ap_particles *p0, const ap_grid *g, doubl
     case AP_PLANE: return apt::launch_adjoint_k<AP_PLANE>(precision, dpd, dpf, aa, grid, stream);
     case AP_GAUSS: return apt::launch_adjoint_k<AP_GAUSS>(precision, dpd, dpf, aa, grid, stream);
     case AP_LG: return apt::launch_adjoint_k<AP_LG>(precision, dpd, dpf, aa, grid, stream);
+    case AP_FLYING_CF:
+      return apt::launch_adjoint_k<AP_FLYING_CF>(precision, dpd, dpf, aa, grid, stream);
     default: return AP_ERR_UNSUPPORTED;
   }
 }

@@ -98,7 +98,8 @@ double lg_peak(int p, int a) {
 }
 
 int check_desc(const ap_pulse_desc &d) {
-  if (d.kind < AP_PLANE || d.kind > AP_FLYING_SUM) return AP_ERR_ARG;
+  if (d.kind < AP_PLANE || d.kind > AP_FLYING_CF) return AP_ERR_ARG;
+  if (d.kind == AP_FLYING_CF && !(d.beta_f < 1.0 && std::isfinite(d.beta_f))) return AP_ERR_ARG;
   if (d.pol < AP_LIN_X || d.pol > AP_CIRC_M) return AP_ERR_ARG;
   if (!(d.omega > 0.0) || !std::isfinite(d.a0) || !std::isfinite(d.phase0)) return AP_ERR_ARG;
   if (!std::isfinite(d.z_focus) || !std::isfinite(d.t_focus)) return AP_ERR_ARG;
@@ -160,6 +161,12 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
   if (d.kind != AP_PLANE) {
     P.inv_w0sq = 1.0 / (d.w0 * d.w0);
     P.inv_zR = 1.0 / (0.5 * k * d.w0 * d.w0);
+  }
+  if (d.kind == AP_FLYING_CF) {
+    // Sec. 3.3: x_R -> (1 - beta_f) x_R for the moving focus
+    P.beta_f = d.beta_f;
+    P.inv_1mb = 1.0 / (1.0 - d.beta_f);
+    P.inv_zR *= P.inv_1mb;
   }
   switch (P.env) {
     case AP_ENV_SIN2: {
@@ -256,6 +263,8 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
   F.py_re = (float)P.py_re; F.py_im = (float)P.py_im;
   for (int i = 0; i <= apt::kLgMaxP; ++i) F.lg_c[i] = (float)P.lg_c[i];
   F.lg_pref = (float)P.lg_pref;
+  F.beta_f = (float)P.beta_f;
+  F.inv_1mb = (float)P.inv_1mb;
   F.a0 = (float)P.a0;
   F.inv_w0 = (float)P.inv_w0;
   F.amp_unit = (float)P.amp_unit;
@@ -425,6 +434,7 @@ int launch_push(int kind, int precision, const Pulse<double> &pd, const Pulse<fl
     case AP_GAUSS: return launch_push_gauss(precision, pd, pf, a, stream);
     case AP_LG: return launch_push_lg(precision, pd, pf, a, stream);
     case AP_FLYING_SUM: return launch_push_flying(precision, pd, pf, a, stream);
+    case AP_FLYING_CF: return launch_push_flyingcf(precision, pd, pf, a, stream);
     default: return AP_ERR_ARG;
   }
 }
@@ -436,6 +446,7 @@ int launch_eval(int kind, int precision, const Pulse<double> &pd, const Pulse<fl
     case AP_GAUSS: return launch_eval_gauss(precision, pd, pf, a, stream);
     case AP_LG: return launch_eval_lg(precision, pd, pf, a, stream);
     case AP_FLYING_SUM: return launch_eval_flying(precision, pd, pf, a, stream);
+    case AP_FLYING_CF: return launch_eval_flyingcf(precision, pd, pf, a, stream);
     default: return AP_ERR_ARG;
   }
 }
@@ -447,6 +458,7 @@ int launch_batch(int kind, int precision, const Pulse<double> *dpd, const Pulse<
     case AP_GAUSS: return launch_batch_gauss(precision, dpd, dpf, a, stream);
     case AP_LG: return launch_batch_lg(precision, dpd, dpf, a, stream);
     case AP_FLYING_SUM: return launch_batch_flying(precision, dpd, dpf, a, stream);
+    case AP_FLYING_CF: return launch_batch_flyingcf(precision, dpd, dpf, a, stream);
     default: return AP_ERR_ARG;
   }
 }

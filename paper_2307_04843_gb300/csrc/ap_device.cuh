@@ -281,6 +281,7 @@ struct TimeBase<AP_FP32_PHASEFF> {
 template <typename R>
 struct Local {
   R x, y, dz, psi, eta;
+  R T;              // t - t_f (closed-form flying focus)
   R phi_hi, phi_lo;  // flying focus only (float-float, or double in phi_hi)
 };
 
@@ -297,6 +298,7 @@ __device__ __forceinline__ Local<Real<PREC>> local_coords(const Pulse<Real<PREC>
     L.dz = dz;
     L.psi = P.omega * T - P.k * dz + P.phase0;
     L.eta = T - dz * P.inv_vg;
+    L.T = T;
     L.phi_hi = T - dz;
     L.phi_lo = 0.0;
   } else if constexpr (PREC == AP_FP32_PHASE64) {
@@ -310,6 +312,7 @@ __device__ __forceinline__ Local<Real<PREC>> local_coords(const Pulse<Real<PREC>
     L.dz = (float)dz;
     L.psi = (float)psi;
     L.eta = (float)(T - dz * (double)P.inv_vg);
+    L.T = (float)T;
     double phi = T - dz;
     L.phi_hi = (float)phi;
     L.phi_lo = (float)(phi - (double)L.phi_hi);
@@ -327,6 +330,7 @@ __device__ __forceinline__ Local<Real<PREC>> local_coords(const Pulse<Real<PREC>
     L.dz = __fadd_rn(dz.hi, dz.lo);
     float Tf = __fadd_rn(st.Th, st.Tl);
     L.eta = fmaf(-L.dz, P.inv_vg, Tf);
+    L.T = Tf;
     // phi' = T - dz as float-float
     FF ph = two_sum(st.Th, -dz.hi);
     L.phi_hi = ph.hi;
@@ -447,11 +451,16 @@ __device__ __forceinline__ void fields_plane(const PT &P, const Local<R> &L, R E
 //   u = A q exp(-r^2 q / w0^2),  q = 1/(1 - i zeta),  zeta = (z - z_f)/z_R,
 // which equals A (w0/w) e^{-r^2/w^2} e^{-i k r^2/(2R)} e^{i atan zeta}.
 // du/dx = -2 x q / w0^2 u.
-template <class PT, typename R>
+// MOVING: closed-form flying focus (Sec. 3.3): the same profile with
+// x_f - x -> xi0 - xi, i.e. zeta = ((z - z_f) - beta_f (t - t_f)) / z_R',
+// z_R' = (1 - beta_f) z_R (inv_zR holds 1/z_R').
+template <bool MOVING = false, class PT, typename R>
 __device__ __forceinline__ void fields_gauss(const PT &P, const Local<R> &L, R E[3], R B[3]) {
   R mul, l2;
   envelope(P, L.eta, mul, l2);
-  R zeta = L.dz * P.inv_zR;
+  R zeta;
+  if constexpr (MOVING) zeta = fma(-P.beta_f, L.T, L.dz) * P.inv_zR;
+  else zeta = L.dz * P.inv_zR;
   R inv = rcp_r(fma(zeta, zeta, R(1)));
   Cx<R> q{inv, zeta * inv};
   R a = (L.x * L.x + L.y * L.y) * P.inv_w0sq;
@@ -570,6 +579,7 @@ __device__ __forceinline__ void analytic_fields(const Pulse<Real<PREC>> &P,
   if constexpr (KIND == AP_PLANE) fields_plane(P, L, E, B);
   else if constexpr (KIND == AP_GAUSS) fields_gauss(P, L, E, B);
   else if constexpr (KIND == AP_LG) fields_lg(P, L, E, B);
+  else if constexpr (KIND == AP_FLYING_CF) fields_gauss<true>(P, L, E, B);
   else fields_flying<PREC>(P, L, E, B);
 }
 

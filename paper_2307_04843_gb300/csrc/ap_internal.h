@@ -45,6 +45,7 @@ struct Pulse {
   R lg_c[kLgMaxP + 1];           // L_p^{|l|}(s) = sum_i lg_c[i] s^i
   R lg_pref;                     // (sqrt(2) / w0)^{|l|}
   R a0, inv_w0, amp_unit;        // a0, 1/w0 and amp / a0 (adjoint: d/da0, d/dw0)
+  R beta_f, inv_1mb;             // closed-form flying focus: v_f / c and 1 / (1 - beta_f)
   // carrier phase psi = omega (t - t_f) - k (z - z_f) + phase0 (double, host-exact)
   double omega, k, t_f, z_f, phase0;
   // float-float copies for AP_FP32_PHASEFF
@@ -133,6 +134,7 @@ APT_DECLARE_KIND(plane)
 APT_DECLARE_KIND(gauss)
 APT_DECLARE_KIND(lg)
 APT_DECLARE_KIND(flying)
+APT_DECLARE_KIND(flyingcf)
 #undef APT_DECLARE_KIND
 
 // status bits written by kernels

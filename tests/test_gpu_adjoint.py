@@ -127,6 +127,28 @@ def test_adjoint_other_kinds_vs_oracle_fd(kind):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adjoint_flying_focus_closed_form_vs_oracle_fd(precision):
+    """All four rows, including d/dbeta_f, for the closed-form flying focus."""
+    pulse = dict(kind="flying_cf", pol="x", env="gauss", env_len=20.0, a0=3.0, w0=2.5 * L, beta_f=-0.5,
+                 z_focus=1.0, t_focus=0.0, longitudinal=True)
+    rng = np.random.default_rng(19)
+    n = 40
+    parts = dict(x=rng.uniform(-1, 1, n) * 2 * L, y=rng.uniform(-1, 1, n) * 2 * L,
+                 z=rng.uniform(-1, 1, n) * 2 * L, ux=np.zeros(n), uy=np.zeros(n), uz=np.zeros(n))
+    off = np.array([0, n], dtype=np.int64)
+    t0, dt, n_steps, K = -6.0, 0.02, 500, 96
+    _, dJ = _run_adjoint([pulse], off, parts, t0, dt, n_steps, K, precision)
+    names = NAMES + ("beta_f",)
+    g = oracle.grad_fd(pulse, parts, t0, dt, n_steps, names=names, rel_h=1e-4,
+                       scale=dict(z_focus=L, beta_f=0.1))
+    gmax = max(abs(g[k]) for k in names)
+    for k, name in enumerate(names):
+        assert abs(dJ[0, k] - g[name]) <= 1e-3 * max(abs(g[name]), 1e-2 * gmax), (precision, name, dJ[0, k], g[name])
+    assert abs(g["beta_f"]) > 1e-3 * gmax  # the focal velocity matters here
+
+
+@pytest.mark.gpu
 def test_adjoint_with_linear_grid_field():
     """A grid holding linear fields (trilinear interpolation is then exact and
     smooth across cells) enters the trajectory and the position adjoint."""

@@ -34,6 +34,11 @@ CASES = {
     "lg03-y": dict(kind="lg", pol="y", env="gauss", env_len=40.0, a0=1.0, w0=3 * L, lg_p=0, lg_l=3),
     "flying-8-lon": dict(kind="flying", pol="x", a0=2.0, w0=2 * L, n_comp=8, bw_frac=0.05, beta_f=0.9,
                          ff_length=40 * L, longitudinal=True),
+    # closed-form flying focus: counter-propagating (beta_f = -1) and subluminal focus
+    "flyingcf-x-lon": dict(kind="flying_cf", pol="x", env="gauss", env_len=40.0, a0=2.0, w0=3 * L,
+                           beta_f=-1.0, z_focus=2.0, t_focus=1.0, longitudinal=True),
+    "flyingcf-cp-sub": dict(kind="flying_cf", pol="cp", env="cw", a0=1.0, w0=2 * L, beta_f=0.6,
+                            z_focus=-3.0, phase0=0.7),
 }
 
 

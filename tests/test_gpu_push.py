@@ -157,6 +157,28 @@ def test_workload4_flying_focus_reduced(precision):
     assert np.max(np.abs(ref["ux"])) > 0.5
 
 
+# ------------------------------------------------------------ closed-form flying focus
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("beta_f", [-1.0, 0.5])
+def test_flying_focus_closed_form_push(precision, beta_f):
+    """Closed-form flying focus (a0 = 5, w0 = 3 lambda, longitudinal terms,
+    Gaussian envelope), 200 electrons around the focal region, 2500 steps."""
+    pulse = dict(kind="flying_cf", pol="x", env="gauss", env_len=30.0, a0=5.0, w0=3 * L, beta_f=beta_f,
+                 z_focus=0.0, t_focus=0.0, longitudinal=True)
+    rng = np.random.default_rng(23)
+    n = 200
+    parts = dict(x=rng.uniform(-1, 1, n) * 4 * L, y=rng.uniform(-1, 1, n) * 4 * L,
+                 z=rng.uniform(-1, 1, n) * 6 * L, ux=np.zeros(n), uy=np.zeros(n), uz=np.zeros(n))
+    t0, dt, n_steps = -40.0, 0.02, 2500
+    out, _, st = gpu_push(pulse, parts, t0, dt, n_steps, precision)
+    assert st == 0
+    ref = oracle.push(pulse, parts, t0, dt, n_steps, threads=THREADS)
+    _check(out, ref, precision)
+    assert np.max(np.abs(ref["ux"])) > 0.5
+
+
 # ------------------------------------------------------------ edge cases
 
 @pytest.mark.gpu

@@ -1,0 +1,62 @@
+"""The oracle's pins have teeth: each plausible slip planted in a copy of the
+oracle (on the CPU) makes at least one pin fail.
+
+Each case copies oracle/ to a temporary directory, applies one textual
+mutation to oracle.c, and runs the named pin tests against the mutated copy
+in a subprocess; the test passes when those pins fail."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = [
+    ("gouy phase sign", "  double phase = -0.5 * k * r2 * invR + gouy;",
+     "  double phase = -0.5 * k * r2 * invR - gouy;", "solve_paraxial_equation"),
+    ("wavefront curvature sign", "  double phase = -0.5 * k * r2 * invR + gouy;",
+     "  double phase = 0.5 * k * r2 * invR + gouy;", "solve_paraxial_equation"),
+    ("transposed cross product in the Boris rotation",
+     "  double uprime[3] = {um[0] + (um[1] * tau[2] - um[2] * tau[1]),",
+     "  double uprime[3] = {um[0] + (um[2] * tau[1] - um[1] * tau[2]),", "gyration"),
+    ("dropped half electric kick", "  for (int a = 0; a < 3; ++a) u[a] = up[a] + h * E[a];",
+     "  for (int a = 0; a < 3; ++a) u[a] = up[a];", "plane_wave_exact or pure_electric"),
+    ("dropped longitudinal E_z", "      EB[2] = creal((-I * s->vphi / p->omega) * (px * DX + py * DY));",
+     "      EB[2] = 0.0;", "maxwell_residual_scaling"),
+    ("Gaussian envelope width", "      return exp(-2.0 * log(2.0) * eta * eta / (p->env_len * p->env_len));",
+     "      return exp(-4.0 * log(2.0) * eta * eta / (p->env_len * p->env_len));", "envelope_widths"),
+    ("flying-focus group-delay sign",
+     "      s->fphi[j] = s->fphi[j - 1] + 0.5 * (tau_j + tau_m) * (s->fw[j] - s->fw[j - 1]);",
+     "      s->fphi[j] = s->fphi[j - 1] - 0.5 * (tau_j + tau_m) * (s->fw[j] - s->fw[j - 1]);",
+     "flying_focus_peak or flying_focus_table"),
+    ("trilinear weight swapped", "          double wt = (cx ? w[0] : 1.0 - w[0]) * (cy ? w[1] : 1.0 - w[1]) *",
+     "          double wt = (cx ? 1.0 - w[0] : w[0]) * (cy ? w[1] : 1.0 - w[1]) *", "trilinear"),
+    ("Laguerre sign", "    sum += (i % 2 == 0) ? term : -term;", "    sum += term;", "scipy_laguerre"),
+    ("LG extra Gouy order", "    phase += (double)(2 * p->lg_p + al) * gouy + (double)p->lg_l * atan2(y, x);",
+     "    phase += (double)(p->lg_p + al) * gouy + (double)p->lg_l * atan2(y, x);", "solve_paraxial_equation"),
+    ("Yee phase-velocity coefficient", "    s->vphi = 1.0 - (1.0 / 24.0) * (1.0 - cr * cr) * wdx * wdx;",
+     "    s->vphi = 1.0 - (1.0 / 12.0) * (1.0 - cr * cr) * wdx * wdx;", "yee"),
+    ("flying-focus profile wavenumber", "    k = (1.0 - p->beta_f) * s->k;", "    k = s->k;",
+     "reduced_paraxial"),
+]
+
+
+@pytest.mark.parametrize("name,old,new,selector", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new, selector):
+    work = tmp_path / "w"
+    work.mkdir()
+    shutil.copytree(os.path.join(ROOT, "oracle"), work / "oracle",
+                    ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    shutil.copytree(os.path.join(ROOT, "tests"), work / "tests", ignore=shutil.ignore_patterns("__pycache__"))
+    shutil.copytree(os.path.join(ROOT, "paper_2307_04843_gb300"), work / "paper_2307_04843_gb300",
+                    ignore=shutil.ignore_patterns("*.so", "__pycache__", "_build"))
+    src = (work / "oracle" / "oracle.c").read_text()
+    assert src.count(old) == 1, "mutation anchor not found: " + name
+    (work / "oracle" / "oracle.c").write_text(src.replace(old, new))
+    env = dict(os.environ, PYTHONPATH=str(work))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        "tests/test_oracle_pins.py", "-k", selector],
+                       cwd=str(work), env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, "pins did not catch: %s\n%s" % (name, r.stdout[-2000:])

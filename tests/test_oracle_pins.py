@@ -434,3 +434,81 @@ def test_set_gamma_sums():
     uz = np.array([0.0, 0.0, 2.0, 0.0, 4.0])
     s = oracle.set_gamma_sums(off, ux, np.zeros(5), uz)
     np.testing.assert_allclose(s, [1 + math.sqrt(2), 0.0, math.sqrt(5) + 1 + math.sqrt(26)], rtol=1e-15)
+
+
+# ------------------------------------------------- closed-form flying focus
+
+CF = dict(kind="flying_cf", pol="x", env="cw", a0=2.0, w0=3 * L, beta_f=-1.0, z_focus=5.0,
+          t_focus=2.0, longitudinal=True)
+
+
+def test_closed_form_flying_focus_reduces_to_gaussian_at_rest():
+    """beta_f = 0: the focus stands still and the pulse is the Gaussian beam."""
+    rng = np.random.default_rng(21)
+    for _ in range(10):
+        x, y, z, t = rng.uniform(-30, 30, 4)
+        np.testing.assert_allclose(oracle.fields(dict(CF, beta_f=0.0), x, y, z, t),
+                                   oracle.fields(dict(CF, kind="gauss"), x, y, z, t), atol=1e-13)
+
+
+@pytest.mark.parametrize("beta", [-1.0, 0.5, 0.9])
+def test_closed_form_flying_focus_solves_reduced_paraxial_equation(beta):
+    """Sec. 3.3: grad_perp^2 F - 2 i (omega/c)(1 - beta_f) dF/dxi = 0 with
+    xi = z - v_f t (the profile at fixed t, derivatives by 4th-order FD).
+    Using k instead of k (1 - beta_f) in the profile leaves an O(1) residual."""
+    p = dict(CF, beta_f=beta)
+    h = 0.02 * p["w0"]
+    t = 7.0
+    F = lambda x, y, z: oracle.profile(p, x, y, z, t=t)
+    for (x, y, z) in ((0.3 * p["w0"], -0.2 * p["w0"], 40.0), (-0.6 * p["w0"], 0.1 * p["w0"], -90.0)):
+        d2 = lambda f: (-f(2) + 16 * f(1) - 30 * f(0) + 16 * f(-1) - f(-2)) / (12 * h * h)
+        lap = d2(lambda s: F(x + s * h, y, z)) + d2(lambda s: F(x, y + s * h, z))
+        dz = (F(x, y, z - 2 * h) - 8 * F(x, y, z - h) + 8 * F(x, y, z + h) - F(x, y, z + 2 * h)) / (12 * h)
+        res = lap - 2j * (1.0 - beta) * dz
+        assert abs(res) < 1e-6 * abs(lap), (beta, abs(res), abs(lap))
+
+
+def test_closed_form_flying_focus_peak_and_rayleigh_range():
+    """On axis |F| peaks at xi = xi0 (z = z_f + v_f (t - t_f)) with value a0,
+    and falls to a0/sqrt(2) at a distance (1 - beta_f) z_R from it."""
+    for beta in (-1.0, 0.6):
+        p = dict(CF, beta_f=beta)
+        zR1 = (1 - beta) * 0.5 * p["w0"] ** 2
+        for t in (0.0, 50.0):
+            zc = p["z_focus"] + beta * (t - p["t_focus"])
+            assert abs(oracle.profile(p, 0.0, 0.0, zc, t=t)) == pytest.approx(p["a0"], rel=1e-14)
+            assert abs(oracle.profile(p, 0.0, 0.0, zc + zR1, t=t)) == pytest.approx(p["a0"] / math.sqrt(2), rel=1e-13)
+            assert abs(oracle.profile(p, 0.0, 0.0, zc - zR1, t=t)) == pytest.approx(p["a0"] / math.sqrt(2), rel=1e-13)
+
+
+def test_envelope_widths_closed_form():
+    """Gaussian envelope: intensity Gamma^2 is 1/2 at eta = +-T/2 (T = FWHM);
+    super-Gaussian: Gamma = 1/e at eta = tau for every order g."""
+    g = oracle.envelope(dict(kind="plane", env="gauss", env_len=30.0, a0=1.0), [15.0, -15.0, 0.0])
+    np.testing.assert_allclose(g ** 2, [0.5, 0.5, 1.0], rtol=1e-14)
+    for order in (1, 2, 4):
+        s = oracle.envelope(dict(kind="plane", env="sgauss", env_len=25.0, sg_order=order, a0=1.0), [25.0, -25.0])
+        np.testing.assert_allclose(s, math.exp(-1.0), rtol=1e-14)
+
+
+@pytest.mark.parametrize("pulse", [
+    dict(kind="gauss", pol="x", env="cw", a0=1.0, w0=3 * L, z_focus=4.0),
+    dict(kind="lg", pol="x", env="cw", a0=1.0, w0=3 * L, lg_p=1, lg_l=2, z_focus=-3.0),
+    dict(kind="lg", pol="x", env="cw", a0=1.0, w0=2 * L, lg_p=2, lg_l=-1, z_focus=0.0),
+], ids=["gauss", "lg12", "lg2m1"])
+def test_beam_profiles_solve_paraxial_equation(pulse):
+    """Eq. paraxial_diff (for +z): grad_perp^2 u - 2 i k du/dz = 0 holds
+    exactly for the Gaussian and Laguerre-Gaussian profiles; a wrong sign of
+    the Gouy phase or of the wavefront curvature leaves an O(1) residual
+    (the Maxwell residuals only change at the same O(eps^2) order)."""
+    h = 0.02 * pulse["w0"]
+    zR = 0.5 * pulse["w0"] ** 2
+    F = lambda x, y, z: oracle.profile(pulse, x, y, z)
+    d2 = lambda f: (-f(2) + 16 * f(1) - 30 * f(0) + 16 * f(-1) - f(-2)) / (12 * h * h)
+    for (x, y, z) in ((0.4 * pulse["w0"], -0.3 * pulse["w0"], 0.5 * zR),
+                      (-0.7 * pulse["w0"], 0.2 * pulse["w0"], -1.3 * zR),
+                      (0.1 * pulse["w0"], 0.9 * pulse["w0"], 0.05 * zR)):
+        lap = d2(lambda s: F(x + s * h, y, z)) + d2(lambda s: F(x, y + s * h, z))
+        dz = (F(x, y, z - 2 * h) - 8 * F(x, y, z - h) + 8 * F(x, y, z + h) - F(x, y, z + 2 * h)) / (12 * h)
+        res = lap - 2j * dz
+        assert abs(res) < 1e-5 * max(abs(lap), abs(2 * dz)), (abs(res), abs(lap))
