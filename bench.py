@@ -76,7 +76,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="core-seconds of oracle work")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="wall seconds of oracle work on all host cores (cpu_baseline)")
     return ap.parse_args()
 
 
@@ -146,16 +147,18 @@ def dist_info():
     return ws, rank, local
 
 
-def oracle_rate(pulse, parts, t0, dt, n_steps, core_seconds, threads, grid=None):
+def oracle_rate(pulse, parts, t0, dt, n_steps, wall_seconds, threads, grid=None):
     """CPU oracle throughput on a bounded sample of the workload's particles:
-    a probe sizes the sample to about `core_seconds` of single-core work."""
+    a threaded probe sizes the sample to about `wall_seconds` on `threads`
+    host cores."""
     import oracle
-    probe_n, probe_steps = 8, 100
+    probe_n, probe_steps = 2 * threads, 200
     sub = {k: v[:probe_n] for k, v in parts.items()}
+    oracle.push(pulse, {k: v[:threads] for k, v in parts.items()}, t0, dt, 4, grid=grid, threads=threads)
     t = time.perf_counter()
-    oracle.push(pulse, sub, t0, dt, probe_steps, grid=grid)
-    per = (time.perf_counter() - t) / (probe_n * probe_steps)
-    m = int(max(threads, min(len(parts["x"]), core_seconds / (per * n_steps))))
+    oracle.push(pulse, sub, t0, dt, probe_steps, grid=grid, threads=threads)
+    rate = probe_n * probe_steps / (time.perf_counter() - t)
+    m = int(max(threads, min(len(parts["x"]), wall_seconds * rate / n_steps)))
     m = max(threads, (m // threads) * threads)
     sub = {k: v[:m] for k, v in parts.items()}
     t = time.perf_counter()

@@ -8,9 +8,10 @@ dicts of physical parameters (the same dicts the product binding takes); this
 module maps them onto the oracle's own structure.
 
 Functions: ``fields``, ``push``, ``boris``, ``grid_sample``, ``gamma_hist``,
-``set_gamma_sums``, ``profile``, ``envelope``, ``state`` and
+``set_gamma_sums``, ``profile``, ``envelope``, ``state``,
 ``grad_fd`` (FP64 central finite differences with Richardson extrapolation of
-the per-set mean final gamma).
+the per-set mean final gamma), ``yee_nodes`` (E1, B1 at Yee-staggered grid
+nodes) and ``yee1d`` (the 1-D vacuum Yee scheme of Sec. 2.1).
 """
 from .core import (  # noqa: F401
     build,
@@ -27,4 +28,6 @@ from .core import (  # noqa: F401
     set_gamma_sums,
     mean_gamma,
     grad_fd,
+    yee_nodes,
+    yee1d,
 )

@@ -91,6 +91,11 @@ def lib():
         L.or_gamma_hist.restype = None
         L.or_set_gamma_sums.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), dp, dp, dp, dp]
         L.or_set_gamma_sums.restype = None
+        L.or_yee_nodes.argtypes = [ctypes.POINTER(_State), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   dp, dp, ctypes.c_double, dp]
+        L.or_yee_nodes.restype = None
+        L.or_yee1d.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64]
+        L.or_yee1d.restype = None
         _lib = L
     return _lib
 
@@ -269,3 +274,27 @@ def grad_fd(pulse, particles, t0, dt, n_steps, names=("a0", "w0", "z_focus"), re
         d2 = (J(p0 + h / 2) - J(p0 - h / 2)) / h
         g[name] = (4 * d2 - d1) / 3
     return g
+
+
+def yee_nodes(pulse, shape, lo, d, t):
+    """Analytic E1, B1 at the Yee-staggered nodes of a grid of shape
+    (nz, ny, nx), node (i, j, k) at lo + (i, j, k) * d; returns [6, nz, ny, nx]
+    (Ex, Ey, Ez, Bx, By, Bz), each at its own offset inside the cell."""
+    st = prepare(pulse)
+    nz, ny, nx = (int(v) for v in shape)
+    lo = np.asarray(lo, dtype=np.float64)
+    d = np.asarray(d, dtype=np.float64)
+    out = np.empty((6, nz, ny, nx))
+    lib().or_yee_nodes(ctypes.byref(st), nx, ny, nz, _dp(lo), _dp(d), float(t), _dp(out))
+    return out
+
+
+def yee1d(E, B, dz, dt, n_steps):
+    """n_steps of the 1-D vacuum Yee scheme on copies of E (E_x at z_k) and B
+    (B_y at z_{k+1/2}); returns the new (E, B)."""
+    E = np.array(E, dtype=np.float64)
+    B = np.array(B, dtype=np.float64)
+    if E.shape != B.shape or E.ndim != 1:
+        raise ValueError("E and B must be 1-D arrays of one length")
+    lib().or_yee1d(E.size, _dp(E), _dp(B), float(dz), float(dt), int(n_steps))
+    return E, B

@@ -409,3 +409,39 @@ void or_set_gamma_sums(int n_sets, const int64_t *off, const double *ux, const d
     sums[st] = acc;
   }
 }
+
+/* ------------------------------------------------------------ Yee grid */
+
+/* Offsets of Ex, Ey, Ez, Bx, By, Bz inside the Yee cell (Yee 1966), in cells. */
+static const double yee_offset[6][3] = {
+    {0.5, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.0, 0.5},
+    {0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}, {0.5, 0.5, 0.0},
+};
+
+void or_yee_nodes(const or_state *s, int nx, int ny, int nz, const double lo[3],
+                  const double d[3], double t, double *out) {
+  const int64_t plane = (int64_t)nx * ny * nz;
+  for (int c = 0; c < 6; ++c) {
+    for (int k = 0; k < nz; ++k) {
+      for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+          double x = lo[0] + (i + yee_offset[c][0]) * d[0];
+          double y = lo[1] + (j + yee_offset[c][1]) * d[1];
+          double z = lo[2] + (k + yee_offset[c][2]) * d[2];
+          double EB[6];
+          or_fields(s, x, y, z, t, EB);
+          out[c * plane + ((int64_t)k * ny + j) * nx + i] = EB[c];
+        }
+      }
+    }
+  }
+}
+
+void or_yee1d(int64_t nz, double *E, double *B, double dz, double dt, int64_t n_steps) {
+  const double r = dt / dz;
+  for (int64_t n = 0; n < n_steps; ++n) {
+    for (int64_t k = 0; k + 1 < nz; ++k) B[k] -= 0.5 * r * (E[k + 1] - E[k]);
+    for (int64_t k = 1; k < nz; ++k) E[k] -= r * (B[k] - B[k - 1]);
+    for (int64_t k = 0; k + 1 < nz; ++k) B[k] -= 0.5 * r * (E[k + 1] - E[k]);
+  }
+}

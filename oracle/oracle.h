@@ -131,6 +131,28 @@ void or_gamma_hist(int64_t n, const double *ux, const double *uy, const double *
 void or_set_gamma_sums(int n_sets, const int64_t *off, const double *ux, const double *uy,
                        const double *uz, double *sums);
 
+/* Yee-staggered samples of the analytic E1, B1 on a grid (Sec. 2.1 and
+ * Fig. 1: the analytic fields are set on the grid nodes every step and added
+ * to the internally advanced ones).  Node (i, j, k) sits at
+ * lo + (i dx, j dy, k dz); inside the cell the six components sit at the
+ * usual Yee offsets, in cells:
+ *   Ex (1/2, 0, 0), Ey (0, 1/2, 0), Ez (0, 0, 1/2),
+ *   Bx (0, 1/2, 1/2), By (1/2, 0, 1/2), Bz (1/2, 1/2, 0).
+ * An unused axis has n = 1 and d = 0.  E and B are both at time t (the scheme
+ * of Sec. 2.1 holds B at whole steps too).  out: [6][nz][ny][nx], x fastest. */
+void or_yee_nodes(const or_state *s, int nx, int ny, int nz, const double lo[3],
+                  const double d[3], double t, double *out);
+
+/* n_steps steps of the second-order Yee scheme in vacuum for a wave along z,
+ * in the three-substep form of Sec. 2.1 (the paper's x, E_y, B_z become z,
+ * E_x, B_y here): E[k] = E_x at z_k, B[k] = B_y at z_{k + 1/2}, both at whole
+ * time levels, r = dt / dz:
+ *   B[k] -= (r/2) (E[k+1] - E[k]),  k = 0 .. nz-2
+ *   E[k] -= r (B[k] - B[k-1]),       k = 1 .. nz-1
+ *   B[k] -= (r/2) (E[k+1] - E[k]),  k = 0 .. nz-2
+ * E[0] and B[nz-1] are never updated (fixed ends). */
+void or_yee1d(int64_t nz, double *E, double *B, double dz, double dt, int64_t n_steps);
+
 #ifdef __cplusplus
 }
 #endif

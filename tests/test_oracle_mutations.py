@@ -40,6 +40,16 @@ MUTATIONS = [
      "    s->vphi = 1.0 - (1.0 / 12.0) * (1.0 - cr * cr) * wdx * wdx;", "yee"),
     ("flying-focus profile wavenumber", "    k = (1.0 - p->beta_f) * s->k;", "    k = s->k;",
      "reduced_paraxial"),
+    ("Yee E update with a full-step B difference swapped",
+     "    for (int64_t k = 1; k < nz; ++k) E[k] -= r * (B[k] - B[k - 1]);",
+     "    for (int64_t k = 1; k < nz; ++k) E[k] += r * (B[k] - B[k - 1]);", "yee1d_scheme"),
+    ("Yee B half step taken as a full step",
+     "    for (int64_t k = 0; k + 1 < nz; ++k) B[k] -= 0.5 * r * (E[k + 1] - E[k]);\n  }",
+     "    for (int64_t k = 0; k + 1 < nz; ++k) B[k] -= r * (E[k + 1] - E[k]);\n  }", "yee1d_scheme"),
+    ("Ex sampled on the cell node instead of the x edge", "    {0.5, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.0, 0.5},",
+     "    {0.0, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.0, 0.5},", "staggering"),
+    ("Bx sampled at the By position", "    {0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}, {0.5, 0.5, 0.0},",
+     "    {0.5, 0.0, 0.5}, {0.5, 0.0, 0.5}, {0.5, 0.5, 0.0},", "staggering"),
 ]
 
 

@@ -512,3 +512,128 @@ def test_beam_profiles_solve_paraxial_equation(pulse):
         dz = (F(x, y, z - 2 * h) - 8 * F(x, y, z - h) + 8 * F(x, y, z + h) - F(x, y, z + 2 * h)) / (12 * h)
         res = lap - 2j * dz
         assert abs(res) < 1e-5 * max(abs(lap), abs(2 * dz)), (abs(res), abs(lap))
+
+
+# ------------------------------------------------------------ Yee grid (grid-node APT)
+
+def test_yee1d_scheme_propagates_exact_discrete_wave():
+    """The three-substep 1-D Yee scheme (Sec. 2.1) carries the discrete
+    monochromatic wave E_k^n = cos(w n dt - kap z_k),
+    B_{k+1/2}^n = cos(w dt / 2) cos(w n dt - kap z_{k+1/2}) exactly, with w
+    from the paper's dispersion relation sin^2(w dt/2) = (dt/dz)^2 sin^2(kap dz/2)
+    (Eq. dispersion) and B0 = cos(w dt/2) E0 (Eq. e_amp_full).  The fixed ends
+    contaminate at most 2 cells per step, so the interior is compared."""
+    for ppl, cr in ((12, 0.95), (30, 0.5), (7, 0.99)):
+        dz = L / ppl
+        dt = cr * dz
+        kap = 2 * math.pi / (ppl * dz) * 1.0
+        w = 2.0 / dt * math.asin(cr * math.sin(kap * dz / 2))
+        nz, n = 600, 60
+        z = dz * np.arange(nz)
+        E0 = np.cos(-kap * z)
+        B0 = math.cos(w * dt / 2) * np.cos(-kap * (z + dz / 2))
+        E, B = oracle.yee1d(E0, B0, dz, dt, n)
+        Ee = np.cos(w * n * dt - kap * z)
+        Be = math.cos(w * dt / 2) * np.cos(w * n * dt - kap * (z + dz / 2))
+        core = slice(2 * n + 2, nz - 2 * n - 2)
+        assert np.max(np.abs(E[core] - Ee[core])) < 1e-12, (ppl, cr)
+        assert np.max(np.abs(B[core] - Be[core])) < 1e-12, (ppl, cr)
+        # a wave with the continuous relation w = kap drifts visibly
+        assert abs(w - kap) * n * dt > 1e-4
+
+
+def _apt_vs_yee_errors(ppl, yee, g=4, tau=30.0, dist=40.0, cr=0.95):
+    """Super-Gaussian plane-wave pulse propagated `dist` wavelengths by the
+    1-D Yee scheme from the analytic initial condition, against the analytic
+    pulse on the same nodes: max |E| difference within one wavelength of the
+    envelope peak and of the rising-edge half-amplitude point."""
+    dz = L / ppl
+    dt = cr * dz
+    pulse = dict(kind="plane", pol="x", env="sgauss", sg_order=g, env_len=tau, a0=1.0,
+                 z_focus=0.0, t_focus=0.0, yee=yee, yee_dx=dz, yee_dt=dt)
+    vg = oracle.state(pulse)["vg"]
+    z0 = -2.5 * tau - 5 * L
+    nz = int((5 * tau + dist * L + 10 * L) / dz)
+    lo, d = (0.0, 0.0, z0), (0.0, 0.0, dz)
+    g0 = oracle.yee_nodes(pulse, (nz, 1, 1), lo, d, 0.0)
+    n = int(round(dist * L / dt))
+    E, _ = oracle.yee1d(g0[0, :, 0, 0], g0[4, :, 0, 0], dz, dt, n)
+    T = n * dt
+    Ea = oracle.yee_nodes(pulse, (nz, 1, 1), lo, d, T)[0, :, 0, 0]
+    z = z0 + dz * np.arange(nz)
+    diff = np.abs(E - Ea)
+    zp = vg * T
+    ze = vg * (T + tau * math.log(2) ** (1 / (2 * g)))
+    return diff[np.abs(z - zp) <= L].max(), diff[np.abs(z - ze) <= L].max()
+
+
+def test_apt_matches_yee_fourth_order_at_peak_second_on_rising_edge():
+    """Fig. 2e: with the Yee-matched v_phi, v_g and B0/E0 (Eqs. vphi, vg,
+    e_amp), the analytic pulse and the pulse carried by the Yee scheme differ
+    at fourth order in omega dz at the envelope peak and at second order on
+    the rising edge; with vacuum constants (v_phi = v_g = c, B0 = E0) the peak
+    difference is only second order."""
+    ppls = np.array([20.0, 30.0, 40.0, 60.0])
+    x = np.log(L / ppls)
+    res = np.array([_apt_vs_yee_errors(p, True) for p in ppls])
+    s_peak = np.polyfit(x, np.log(res[:, 0]), 1)[0]
+    s_edge = np.polyfit(x, np.log(res[:, 1]), 1)[0]
+    assert abs(s_peak - 4.0) < 0.2, s_peak
+    assert abs(s_edge - 2.0) < 0.2, s_edge
+    vac = np.array([_apt_vs_yee_errors(p, False)[0] for p in ppls])
+    s_vac = np.polyfit(x, np.log(vac), 1)[0]
+    assert abs(s_vac - 2.0) < 0.2, s_vac
+    assert np.all(vac > 10 * res[:, 0])
+
+
+def _div_h(pulse, P, d, t):
+    dd = np.array([d, d, d])
+    g = oracle.yee_nodes(pulse, (3, 3, 3), P - dd, dd, t)  # node (1,1,1) at P
+    Ex, Ey, Ez = g[0], g[1], g[2]
+    return ((Ex[1, 1, 1] - Ex[1, 1, 0]) + (Ey[1, 1, 1] - Ey[1, 0, 1]) + (Ez[1, 1, 1] - Ez[0, 1, 1])) / d
+
+
+def _faraday_h(pulse, P, d, t, dt=1e-3):
+    """dB/dt + curl_h E at the B nodes of cell (1,1,1), each B node placed at
+    P in turn (the time derivative by a fixed central difference)."""
+    dd = np.array([d, d, d])
+    out = []
+    for c, off in ((0, (1.0, 1.5, 1.5)), (1, (1.5, 1.0, 1.5)), (2, (1.5, 1.5, 1.0))):
+        lo = P - dd * np.array(off)
+        g = oracle.yee_nodes(pulse, (3, 3, 3), lo, dd, t)
+        Ex, Ey, Ez = g[0], g[1], g[2]
+        curl = [(Ez[1, 2, 1] - Ez[1, 1, 1]) / d - (Ey[2, 1, 1] - Ey[1, 1, 1]) / d,
+                (Ex[2, 1, 1] - Ex[1, 1, 1]) / d - (Ez[1, 1, 2] - Ez[1, 1, 1]) / d,
+                (Ey[1, 1, 2] - Ey[1, 1, 1]) / d - (Ex[1, 2, 1] - Ex[1, 1, 1]) / d][c]
+        bp = oracle.yee_nodes(pulse, (3, 3, 3), lo, dd, t + dt)[3 + c, 1, 1, 1]
+        bm = oracle.yee_nodes(pulse, (3, 3, 3), lo, dd, t - dt)[3 + c, 1, 1, 1]
+        out.append((bp - bm) / (2 * dt) + curl)
+    return np.array(out)
+
+
+def test_yee_node_staggering_centres_discrete_div_and_curl():
+    """On the staggered nodes the discrete divergence of E is centred on the
+    cell node and the discrete curl of E on each B node (the defining property
+    of the Yee lattice), so div_h E and the discrete Faraday residual
+    dB/dt + curl_h E converge at second order in the cell size to fixed
+    limits; a component sampled half a cell off would converge at first
+    order.  Ratio of successive differences for d = lambda/8 ... lambda/64."""
+    pulse = dict(kind="gauss", pol="cp", env="cw", a0=1.0, w0=1.5 * L, longitudinal=True)
+    P = np.array([0.31 * 1.5 * L, -0.22 * 1.5 * L, 0.4])
+    ds = [L / 8, L / 16, L / 32, L / 64]
+    for f in (_div_h, _faraday_h):
+        v = np.array([f(pulse, P, d, 0.7) for d in ds], dtype=np.float64).reshape(len(ds), -1)
+        diffs = np.abs(np.diff(v, axis=0))
+        ratios = diffs[:-1] / diffs[1:]
+        assert np.all(np.abs(ratios - 4.0) < 0.3), (f.__name__, ratios)
+
+
+def test_yee_nodes_special_cases():
+    """A 1-D grid (unused axes n = 1, d = 0) samples E at the whole nodes and B
+    at the half nodes of z; a CW plane wave gives Ex = cos(t - z) there."""
+    pulse = dict(kind="plane", pol="x", env="cw", a0=1.0)
+    g = oracle.yee_nodes(pulse, (5, 1, 1), (7.0, -3.0, 0.25), (0.0, 0.0, 0.5), 0.9)
+    z = 0.25 + 0.5 * np.arange(5)
+    assert np.allclose(g[0, :, 0, 0], np.cos(0.9 - z), atol=1e-15, rtol=0)
+    assert np.allclose(g[4, :, 0, 0], np.cos(0.9 - z - 0.25), atol=1e-15, rtol=0)
+    assert np.all(g[[1, 2, 3, 5]] == 0.0)
