@@ -43,7 +43,7 @@ MUFU_LANES = 16       # special-function operations per clock per SM
 SM_MAX_MHZ = 2070.0
 
 # FP32-pipe operations per particle-step, counted from the formulas each
-# kernel evaluates ("Roofline"), and MUFU operations.
+# kernel evaluates, and MUFU operations.
 # Workload 2 (Gaussian + longitudinal + grid, float-float phase): local
 # coordinates and phase 34, envelope 2, Gaussian profile + longitudinal +
 # assembly 28, trilinear gather from the cached cell 57, Boris 42,
@@ -54,11 +54,13 @@ ALGO = {
     3: dict(fp32=190, mufu=8),
     4: dict(fp32=2300, mufu=258),
     5: dict(fp32=125, mufu=7),
+    6: dict(fp32=125, mufu=7),
 }
 # DRAM bytes per particle-step of the workload-2 kernel from the committed
-# ncu capture (profiles/push_kernel_gauss_grid_packed_full.md); None when the
-# kernel changed after the capture.
-TRAFFIC_PER_PARTICLE_STEP = None
+# ncu capture of the 1.6e6-particle x 4000-step case, scaled by particle-steps
+# (an upper bound at 1e7 particles: more particles share each cached cell);
+# None when the kernel changed after the capture.
+TRAFFIC_PER_PARTICLE_STEP = 5.336  # (34.084e9 read + 0.064e9 written) / 6.4e9
 
 
 def parse():
@@ -67,7 +69,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4, 5, 6])
     ap.add_argument("--n", type=int, default=None, help="particles per GPU (default: the workload's)")
     ap.add_argument("--nsteps", type=int, default=None, help="Boris steps per call (default: the workload's)")
     ap.add_argument("--grid", type=int, default=256)
@@ -198,6 +200,16 @@ class Workload:
             self.off_host = off
             self.ws = torch.zeros(_lib.ap_batch_workspace_bytes(self.h.h) // 4, dtype=torch.int32, device="cuda")
             self.diag = dict(set_sum=torch.zeros(len(sets), dtype=torch.float64, device="cuda"))
+        elif idx == 6:
+            per = max(1, args.n // cfg["n_sets"]) if args.n else None
+            sets, self.parts, off = workloads.sweep_lines(cfg, per_set=per, seed=seed)
+            self.n = int(off[-1])
+            self.pulses = sets
+            self.h = _lib.Handle(sets)
+            self.off = torch.as_tensor(off).cuda()
+            self.off_host = off
+            self.ws = torch.zeros(_lib.ap_batch_workspace_bytes(self.h.h) // 4, dtype=torch.int32, device="cuda")
+            self.diag = dict(set_sum=torch.zeros(len(sets), dtype=torch.float64, device="cuda"))
         else:
             self.n = args.n or cfg["n"]
             self.parts = workloads.particles(cfg, n=self.n, seed=seed)
@@ -217,14 +229,11 @@ class Workload:
         self.init = _lib.to_device(self.parts, self.precision)
         self.work = {k: v.clone() for k, v in self.init.items()}
         self.tuned = None
-        if not args.no_autotune and idx != 5:
+        if not args.no_autotune and idx not in (5, 6):
             from paper_2307_04843_gb300 import autotune
-            cache = os.path.join(ROOT, "gpurun_out", "autotune.json") if os.path.isdir(
-                os.path.join(ROOT, "gpurun_out")) else None
             self.tuned = autotune.tune(self.h, self.init, self.t0, self.dt, self.precision, self.grid,
-                                       sample_n=min(self.n, 2_000_000), sample_steps=min(self.n_steps, 200),
-                                       cache_path=cache)
-        if idx == 5:
+                                       sample_n=min(self.n, 2_000_000), sample_steps=min(self.n_steps, 200))
+        if idx in (5, 6):
             self.stream = torch.cuda.Stream()
             self.graph = _lib.ap_batch_graph_create(self.h.h, self.work, self.off, None, self.t0, self.dt,
                                                     self.n_steps, self.precision, self.diag, self.ws,
@@ -263,7 +272,9 @@ def describe(wl, args):
                 "1024-bin gamma histogram, float-float phase",
              4: "flying-focus: 64 Gaussian spectral components, v_f=0.99, a0=5, float-float phase",
              5: "batched-gauss: 256 Gaussian sets, log-uniform counts, one persistent launch in a CUDA graph, "
-                "per-set mean gamma, float-float phase"}
+                "per-set mean gamma, float-float phase",
+             6: "ics-sweep-1d3v: 30 radii x 1e5 electrons (gamma 5088, 1D-3V) in a Gaussian a0=50, "
+                "w0=2.55 lambda, 15 fs, one batched launch in a CUDA graph, float-float phase"}
     cfg = {"workload": names[wl.idx], "particles_per_gpu": wl.n, "boris_steps_per_call": wl.n_steps,
            "dt": c["dt"], "l2": "inputs larger than L2 (36 B/particle state%s); no flush" %
            (", 402 MB grid + 537 MB node-interleaved copy" if wl.grid is not None else ""),
@@ -278,6 +289,62 @@ def describe(wl, args):
 
 
 # ---------------------------------------------------------------- our arm
+
+NODE_N = 256           # staggered grid edge for the node-evaluation rate
+NODE_OPS_PER_EVAL = 90  # FP32 operations of one Gaussian field evaluation with
+                        # longitudinal terms (phase unit 30, envelope 2,
+                        # profile + longitudinal + assembly 58), no push
+YEE_LINES, YEE_NZ, YEE_STEPS = 152, 8192, 2000
+
+
+def grid_node_rates(wl, stream):
+    """Rates of ap_eval_nodes (the workload's pulse onto a 256^3 Yee grid,
+    six float arrays, float-float phase) and ap_yee1d_run (float lines)."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3 / reps
+
+    n = NODE_N
+    f = [torch.empty((n, n, n), dtype=torch.float32, device="cuda") for _ in range(6)]
+    from paper_2307_04843_gb300 import workloads
+    lo, hi = workloads.grid_box(wl.cfg)
+    d = tuple((hi[a] - lo[a]) / (n - 1) for a in range(3))
+    sec = timed(lambda: wl.h.eval_nodes(f, lo, d, 0.0, precision="fp32"), 3)
+    nodes = float(n) ** 3
+    bytes_ = 24.0 * nodes
+    ops = 6 * NODE_OPS_PER_EVAL * nodes
+    peak_ops = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6
+    hbm = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            hbm = float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        pass
+    del f
+    E = torch.zeros((YEE_LINES, YEE_NZ), dtype=torch.float32, device="cuda")
+    B = torch.zeros_like(E)
+    E[:, YEE_NZ // 2] = 1.0
+    ysec = timed(lambda: _lib.ap_yee1d_run(E, B, 0.05, 0.0475, YEE_STEPS), 2)
+    return {
+        "eval_nodes": {"value": nodes / sec, "unit": "nodes/s", "ms": sec * 1e3,
+                       "grid": "%d^3, 6 staggered components, float arrays, float-float phase" % n,
+                       "alu_frac": ops / sec / peak_ops,
+                       "hbm_frac": (bytes_ / sec / 1e9 / hbm) if hbm else None,
+                       "ops_per_node": 6 * NODE_OPS_PER_EVAL, "bytes_per_node": 24},
+        "yee1d": {"value": YEE_LINES * YEE_NZ * YEE_STEPS / ysec, "unit": "node-steps/s",
+                  "ms": ysec * 1e3, "lines": YEE_LINES, "nz": YEE_NZ, "steps": YEE_STEPS,
+                  "dtype": "f32"},
+    }
 
 def run_ours(args):
     import torch
@@ -384,6 +451,12 @@ def run_ours(args):
         for prec in variants:
             variants[prec]["fp32_speedup"] = (units_rank / kern) / variants[prec]["value"]
 
+    # grid-node form: analytic E1/B1 on the staggered nodes of a 256^3 Yee
+    # grid (six float arrays), and independent 1-D vacuum Yee lines
+    grid_node = None
+    if rank == 0 and not args.no_variants and args.workload == 2:
+        grid_node = grid_node_rates(wl, stream)
+
     # the adjoint of the batched workload: forward + reverse sweep
     adjoint = None
     if rank == 0 and args.workload == 5:
@@ -443,6 +516,8 @@ def run_ours(args):
     }
     if adjoint is not None:
         line["adjoint"] = adjoint
+    if grid_node is not None:
+        line["grid_node"] = grid_node
     if rank == 0:
         print(json.dumps(line), flush=True)
     wl.close()

@@ -82,6 +82,10 @@ extern "C" {
 /* flags */
 #define AP_F_LONGITUDINAL 1u /* add E_z, B_z from div E = 0, div B = 0 (Sec. 3.1) */
 #define AP_F_YEE_DISP 2u     /* second-order Yee v_phi, v_g, B0/E0 (Eqs. vphi, vg, e_amp) */
+#define AP_F_1D3V 4u         /* reduced dimensionality (Sec. 3.2): the particles of this set
+                                keep their transverse position (a 1-D line at that x, y in
+                                the focusing pulse) while z and all three momentum
+                                components advance (1D-3V) */
 /* arithmetic of the push */
 #define AP_FP64 0            /* everything in double; u arrays are double */
 #define AP_FP32_PHASE64 1    /* fields and Boris in float; phase argument and position
@@ -172,6 +176,35 @@ typedef struct {
   double *set_gamma_sum;  /* [n_sets] (batched) or [1]: sum of final gamma per set */
   int32_t accumulate;
 } ap_diag;
+
+/* Yee-staggered grid that receives the analytic fields on its nodes
+ * (grid-node form of the technique: Sec. 2.1 and Fig. 1 set E1/B1 on the
+ * grid every step and add them to the internally advanced E2/B2).  Node
+ * (i, j, k) sits at lo + (i d[0], j d[1], k d[2]); inside the cell the
+ * components sit at the Yee offsets (in cells)
+ *   Ex (1/2,0,0)  Ey (0,1/2,0)  Ez (0,0,1/2)  Bx (0,1/2,1/2)  By (1/2,0,1/2)  Bz (1/2,1/2,0).
+ * An unused axis has n = 1 and d = 0 (a 1-D grid along z holds Ex on the
+ * whole nodes and By on the half nodes).  f[c]: device [nz][ny][nx], x
+ * fastest, caller-owned, float (f64 = 0) or double (f64 != 0), aligned to
+ * the element size; a NULL component is skipped. */
+typedef struct {
+  void *f[6];
+  int32_t nx, ny, nz;
+  int32_t f64;
+  double lo[3], d[3];
+} ap_yee_grid;
+
+/* Independent 1-D vacuum Yee lines (the internal field update of Sec. 2.1
+ * for a wave along z): E[l][k] = E_x at z_k, B[l][k] = B_y at z_{k+1/2},
+ * both at whole time levels; device [n_lines][nz], caller-owned, double for
+ * AP_FP64 and float for AP_FP32_PHASEFF. */
+typedef struct {
+  void *E, *B;
+  int32_t nz, n_lines;
+  double dz, dt;
+} ap_yee1d;
+
+#define AP_YEE1D_MAX_NODES 12288  /* nodes per line: the line lives in shared memory */
 
 /* Launch shape, chosen by the autotuner (0 = library default). */
 typedef struct {
@@ -317,6 +350,30 @@ int ap_sync_status(ap_handle h, void *stream);
 
 /* Number of sets in the handle, or AP_ERR_ARG. */
 int ap_num_sets(ap_handle h);
+
+/* Analytic E1/B1 of set `set` at time t on the staggered nodes of `g`
+ * (grid-node form, Sec. 2.1 and Fig. 1), each component at its own Yee
+ * offset, E and B both at t (the scheme of Sec. 2.1 keeps B at whole steps).
+ * accumulate = 0 stores E1/B1; nonzero adds them to what f[] holds (the
+ * total field E1 + E2 that the push interpolates).  precision as for
+ * ap_eval_fields; the result is rounded once to the array type.
+ * Errors: AP_ERR_ARG (bad set, sizes < 1 or above 2^24 per axis or 10^12
+ * nodes in all, negative or non-finite spacing), AP_ERR_ALIGN, AP_ERR_CUDA. */
+int ap_eval_nodes(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int32_t accumulate,
+                  int32_t precision, void *stream);
+
+/* n_steps steps of the second-order Yee scheme in vacuum on every line of
+ * `y`, in the three-substep form of Sec. 2.1 with r = dt/dz:
+ *   B[k] -= (r/2)(E[k+1] - E[k])   k = 0 .. nz-2
+ *   E[k] -= r (B[k] - B[k-1])      k = 1 .. nz-1
+ *   B[k] -= (r/2)(E[k+1] - E[k])   k = 0 .. nz-2
+ * E[0] and B[nz-1] are held fixed (the ends of the line).  Each product and
+ * difference is rounded separately in the stated order (no fused
+ * multiply-add).  All steps run in one launch, one block per line with the
+ * line in shared memory.  precision: AP_FP64 (double arrays) or
+ * AP_FP32_PHASEFF (float arrays).  Errors: AP_ERR_ARG (nz < 2 or above
+ * AP_YEE1D_MAX_NODES, n_lines < 0, n_steps < 0), AP_ERR_ALIGN, AP_ERR_CUDA. */
+int ap_yee1d_run(const ap_yee1d *y, int64_t n_steps, int32_t precision, void *stream);
 
 #ifdef __cplusplus
 }

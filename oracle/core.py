@@ -24,6 +24,7 @@ class _Pulse(ctypes.Structure):
         ("kind", ctypes.c_int), ("pol", ctypes.c_int), ("env", ctypes.c_int),
         ("sg_order", ctypes.c_int), ("lg_p", ctypes.c_int), ("lg_l", ctypes.c_int),
         ("n_comp", ctypes.c_int), ("longitudinal", ctypes.c_int), ("yee", ctypes.c_int),
+        ("one_d", ctypes.c_int),
         ("a0", ctypes.c_double), ("omega", ctypes.c_double), ("w0", ctypes.c_double),
         ("z_focus", ctypes.c_double), ("t_focus", ctypes.c_double),
         ("env_len", ctypes.c_double), ("phase0", ctypes.c_double),
@@ -111,6 +112,7 @@ def _pulse_struct(d):
     p.n_comp = int(d.get("n_comp", 0))
     p.longitudinal = 1 if d.get("longitudinal", False) else 0
     p.yee = 1 if d.get("yee", False) else 0
+    p.one_d = 1 if d.get("one_d", False) else 0
     for name in ("a0", "omega", "w0", "z_focus", "t_focus", "env_len", "phase0", "beta_f",
                  "bw_frac", "ff_length", "yee_dx", "yee_dt"):
         default = 1.0 if name == "omega" else 0.0

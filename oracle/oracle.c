@@ -374,7 +374,8 @@ int or_push(const or_state *s, const float *grid, int nx, int ny, int nz, const 
       }
       or_boris(u, EB, EB + 3, dt);
       double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-      for (int a = 0; a < 3; ++a) pos[a] += dt * u[a] / g;
+      /* 1D-3V (Sec. 3.2): only z moves; the momentum keeps all three components */
+      for (int a = s->p.one_d ? 2 : 0; a < 3; ++a) pos[a] += dt * u[a] / g;
       if (lf_max) {
         double dev = fabs((g - u[2]) - h0);
         if (dev > lf_max[st]) lf_max[st] = dev;

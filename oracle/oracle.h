@@ -64,6 +64,7 @@ typedef struct {
   int n_comp;        /* flying focus: number of spectral components */
   int longitudinal;  /* nonzero: add E_z, B_z from the divergence conditions */
   int yee;           /* nonzero: second-order Yee v_phi, v_g, B0/E0 (Eqs. vphi, vg, e_amp) */
+  int one_d;         /* nonzero: 1D-3V push (Sec. 3.2), transverse position held fixed */
   double a0, omega, w0;
   double z_focus, t_focus;  /* focus position; time at which the envelope peak is there.
                                flying focus: start z_a of the focal range and its time t_a */

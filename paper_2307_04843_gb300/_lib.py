@@ -30,10 +30,12 @@ ENVS = {"sin2": 0, "gauss": 1, "sgauss": 2, "cw": 3}
 PRECISIONS = {"fp64": 0, "fp32_phase64": 1, "fp32": 2, "fp32_phaseff": 2}
 AP_F_LONGITUDINAL = 1
 AP_F_YEE_DISP = 2
+AP_F_1D3V = 4
 AP_NPARAM = 4
 AP_OBJ_MEAN_GAMMA = 0
 AP_MAX_COMP = 128
 AP_MAX_SETS = 4096
+AP_YEE1D_MAX_NODES = 12288
 
 
 class ApPulseDesc(ctypes.Structure):
@@ -69,6 +71,21 @@ class ApDiag(ctypes.Structure):
         ("lightfront_max", ctypes.c_void_p), ("gamma_hist", ctypes.c_void_p),
         ("hist_bins", ctypes.c_int32), ("hist_lo", ctypes.c_double), ("hist_hi", ctypes.c_double),
         ("set_gamma_sum", ctypes.c_void_p), ("accumulate", ctypes.c_int32),
+    ]
+
+
+class ApYeeGrid(ctypes.Structure):
+    _fields_ = [
+        ("f", ctypes.c_void_p * 6), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("nz", ctypes.c_int32), ("f64", ctypes.c_int32),
+        ("lo", ctypes.c_double * 3), ("d", ctypes.c_double * 3),
+    ]
+
+
+class ApYee1d(ctypes.Structure):
+    _fields_ = [
+        ("E", ctypes.c_void_p), ("B", ctypes.c_void_p), ("nz", ctypes.c_int32),
+        ("n_lines", ctypes.c_int32), ("dz", ctypes.c_double), ("dt", ctypes.c_double),
     ]
 
 
@@ -111,6 +128,9 @@ SIGNATURES = {
                                        ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "ap_sync_status": (ctypes.c_int, [_vp, _vp]),
     "ap_num_sets": (ctypes.c_int, [_vp]),
+    "ap_eval_nodes": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ApYeeGrid), ctypes.c_double,
+                                     ctypes.c_int32, ctypes.c_int32, _vp]),
+    "ap_yee1d_run": (ctypes.c_int, [ctypes.POINTER(ApYee1d), ctypes.c_int64, ctypes.c_int32, _vp]),
 }
 
 _lib = None
@@ -162,7 +182,8 @@ def pulse_desc(d):
     p.lg_l = int(d.get("lg_l", 0))
     p.n_comp = int(d.get("n_comp", 0))
     p.flags = (AP_F_LONGITUDINAL if d.get("longitudinal", False) else 0) | \
-              (AP_F_YEE_DISP if d.get("yee", False) else 0)
+              (AP_F_YEE_DISP if d.get("yee", False) else 0) | \
+              (AP_F_1D3V if d.get("one_d", False) else 0)
     for name in ("a0", "omega", "w0", "z_focus", "t_focus", "env_len", "phase0", "beta_f",
                  "bw_frac", "ff_length", "yee_dx", "yee_dt"):
         setattr(p, name, float(d.get(name, 1.0 if name == "omega" else 0.0)))
@@ -392,6 +413,57 @@ def ap_num_sets(h):
     return lib().ap_num_sets(h)
 
 
+def yee_grid_struct(fields, lo, d):
+    """ap_yee_grid from a list of six CUDA tensors (or None) of one shape
+    (nz, ny, nx) and one dtype (float32 or float64), node (0,0,0) at lo,
+    spacing d."""
+    import torch
+    present = [f for f in fields if f is not None]
+    if len(fields) != 6 or not present:
+        raise ValueError("need six entries (tensor or None), at least one tensor")
+    shape, dtype = present[0].shape, present[0].dtype
+    for f in present:
+        if f.shape != shape or f.dtype != dtype or not f.is_cuda or not f.is_contiguous():
+            raise ValueError("node arrays must be contiguous CUDA tensors of one shape and dtype")
+    if dtype not in (torch.float32, torch.float64) or len(shape) != 3:
+        raise ValueError("node arrays must be float32 or float64 of shape (nz, ny, nx)")
+    g = ApYeeGrid()
+    for c in range(6):
+        g.f[c] = fields[c].data_ptr() if fields[c] is not None else None
+    g.nz, g.ny, g.nx = (int(v) for v in shape)
+    g.f64 = 1 if dtype == torch.float64 else 0
+    for a in range(3):
+        g.lo[a] = float(lo[a])
+        g.d[a] = float(d[a])
+    return g
+
+
+def ap_eval_nodes(h, set_index, fields, lo, d, t, accumulate=False, precision="fp64", stream=None):
+    gs = yee_grid_struct(fields, lo, d)
+    check("ap_eval_nodes", lib().ap_eval_nodes(h, set_index, ctypes.byref(gs), float(t),
+                                               1 if accumulate else 0, precision_id(precision),
+                                               _stream(stream)))
+
+
+def ap_yee1d_run(E, B, dz, dt, n_steps, stream=None):
+    """n_steps of the 1-D vacuum Yee scheme on CUDA tensors E, B of shape
+    (n_lines, nz) or (nz,), float64 (AP_FP64) or float32 (AP_FP32_PHASEFF)."""
+    import torch
+    if E.shape != B.shape or E.dtype != B.dtype or E.dim() not in (1, 2):
+        raise ValueError("E and B must have one shape (n_lines, nz) or (nz,) and one dtype")
+    if not (E.is_cuda and B.is_cuda and E.is_contiguous() and B.is_contiguous()):
+        raise ValueError("E and B must be contiguous CUDA tensors")
+    y = ApYee1d()
+    y.E, y.B = E.data_ptr(), B.data_ptr()
+    y.nz = int(E.shape[-1])
+    y.n_lines = int(E.shape[0]) if E.dim() == 2 else 1
+    y.dz, y.dt = float(dz), float(dt)
+    prec = {torch.float64: 0, torch.float32: 2}.get(E.dtype)
+    if prec is None:
+        raise ValueError("E and B must be float32 or float64")
+    check("ap_yee1d_run", lib().ap_yee1d_run(ctypes.byref(y), int(n_steps), prec, _stream(stream)))
+
+
 # ------------------------------------------------------------ convenience
 
 class Handle:
@@ -432,6 +504,10 @@ class Handle:
         EB = torch.empty((6, xyzt.shape[1]), dtype=torch.float64, device="cuda")
         ap_eval_fields(self.h, set_index, xyzt, EB, precision)
         return EB
+
+    def eval_nodes(self, fields, lo, d, t, accumulate=False, precision="fp64", set_index=0, stream=None):
+        """Analytic E1/B1 on the Yee-staggered nodes (see ap_eval_nodes)."""
+        ap_eval_nodes(self.h, set_index, fields, lo, d, t, accumulate, precision, stream)
 
     def status(self, stream=None):
         return ap_sync_status(self.h, stream)

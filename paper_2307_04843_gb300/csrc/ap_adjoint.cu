@@ -237,10 +237,12 @@ __device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P, const P
   R un[3] = {fma(h, E[0], bq[0]), fma(h, E[1], bq[1]), fma(h, E[2], bq[2])};
   R ign = rsqrt_r(R(1) + un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
   R v[3] = {un[0] * ign, un[1] * ign, un[2] * ign};
-  // position update: x' = x + dt u' / gamma'
-  R vl = v[0] * lx[0] + v[1] * lx[1] + v[2] * lx[2];
+  // position update: x'_k = x_k + dt_k u'_k / gamma', dt_k = (dt_xy, dt_xy, dt)
+  // (dt_xy = 0 for a 1D-3V set): d x'_k / d u'_j = dt_k ign (delta_kj - v_k v_j)
+  const R dtk[3] = {dt * P.adv_xy, dt * P.adv_xy, dt};
+  R vl = dtk[0] * v[0] * lx[0] + dtk[1] * v[1] * lx[1] + dtk[2] * v[2] * lx[2];
   R ub[3];
-  for (int k = 0; k < 3; ++k) ub[k] = lu[k] + dt * ign * (lx[k] - v[k] * vl);
+  for (int k = 0; k < 3; ++k) ub[k] = lu[k] + ign * (dtk[k] * lx[k] - v[k] * vl);
   // Boris reverse
   R Eb[3], Bb[3], ab[3], pb[3], sbar[3], tb[3];
   for (int k = 0; k < 3; ++k) Eb[k] = h * ub[k];
@@ -348,6 +350,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const Pulse<Real<PRE
     TimeBase<PREC> tb;
     tb.init(P, a.t0, a.dt);
     const R dtR = (R)a.dt;
+    const R dtxy = dtR * P.adv_xy;
     GridCache<R> gc;
     grid_cache_reset(gc);
     for (int seg = 0; seg < aa.n_seg; ++seg) {
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const Pulse<Real<PRE
         analytic_fields<KIND, PREC>(P, L, E, B);
         if constexpr (GRID) grid_gather<R>(a.grid, gc, L.x, L.y, pos.zr(), E, B);
         R ig = boris(u, E, B, dtR);
-        pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtR);
+        pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtxy, dtR);
       }
     }
     // ---- objective and seed
@@ -398,7 +401,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const Pulse<Real<PRE
         analytic_fields<KIND, PREC>(P, L, E, B);
         if constexpr (GRID) grid_gather<R>(a.grid, gc, L.x, L.y, pos.zr(), E, B);
         R ig = boris(u, E, B, dtR);
-        pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtR);
+        pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtxy, dtR);
       }
       R gs[kNp] = {R(0), R(0), R(0), R(0)};
       for (int k = cnt - 1; k >= 0; --k) {

@@ -122,7 +122,7 @@ int check_desc(const ap_pulse_desc &d) {
   if (d.flags & AP_F_YEE_DISP) {
     if (!(d.yee_dx > 0.0) || !(d.yee_dt > 0.0) || !(d.yee_dt < d.yee_dx)) return AP_ERR_ARG;
   }
-  if (d.flags & ~(AP_F_LONGITUDINAL | AP_F_YEE_DISP)) return AP_ERR_ARG;
+  if (d.flags & ~(AP_F_LONGITUDINAL | AP_F_YEE_DISP | AP_F_1D3V)) return AP_ERR_ARG;
   return AP_OK;
 }
 
@@ -135,6 +135,7 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
   P.lon = (d.flags & AP_F_LONGITUDINAL) && d.kind != AP_PLANE ? 1 : 0;
   P.sg_order = d.sg_order;
   P.yee = (d.flags & AP_F_YEE_DISP) ? 1 : 0;
+  P.adv_xy = (d.flags & AP_F_1D3V) ? 0.0 : 1.0;
   // Phase velocity, group velocity and B0/E0 (Eqs. vphi, vg, e_amp, Sec. 2.1;
   // vacuum values unless requested).
   double vphi = 1.0, vg = 1.0, br = 1.0;
@@ -264,6 +265,7 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
   for (int i = 0; i <= apt::kLgMaxP; ++i) F.lg_c[i] = (float)P.lg_c[i];
   F.lg_pref = (float)P.lg_pref;
   F.beta_f = (float)P.beta_f;
+  F.adv_xy = (float)P.adv_xy;
   F.inv_1mb = (float)P.inv_1mb;
   F.a0 = (float)P.a0;
   F.inv_w0 = (float)P.inv_w0;
@@ -451,6 +453,18 @@ int launch_eval(int kind, int precision, const Pulse<double> &pd, const Pulse<fl
   }
 }
 
+int launch_nodes(int kind, int precision, const Pulse<double> &pd, const Pulse<float> &pf,
+                 const NodeArgs &a, void *stream) {
+  switch (kind) {
+    case AP_PLANE: return launch_nodes_plane(precision, pd, pf, a, stream);
+    case AP_GAUSS: return launch_nodes_gauss(precision, pd, pf, a, stream);
+    case AP_LG: return launch_nodes_lg(precision, pd, pf, a, stream);
+    case AP_FLYING_SUM: return launch_nodes_flying(precision, pd, pf, a, stream);
+    case AP_FLYING_CF: return launch_nodes_flyingcf(precision, pd, pf, a, stream);
+    default: return AP_ERR_ARG;
+  }
+}
+
 int launch_batch(int kind, int precision, const Pulse<double> *dpd, const Pulse<float> *dpf,
                  const BatchArgs &a, void *stream) {
   switch (kind) {
@@ -558,6 +572,50 @@ int ap_eval_fields(ap_handle h, int32_t set, const double *xyzt, int64_t n, doub
   if (rc != AP_OK) return rc;
   apt::EvalArgs a{xyzt, n, EB_out, h->d_status};
   return apt::launch_eval(h->descs[set].kind, precision, h->pd[set], h->pf[set], a, stream);
+}
+
+int ap_eval_nodes(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int32_t accumulate,
+                  int32_t precision, void *stream) {
+  if (!h || !g || set < 0 || set >= h->n_sets) return AP_ERR_ARG;
+  if (precision < AP_FP64 || precision > AP_FP32_PHASEFF) return AP_ERR_ARG;
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !std::isfinite(t)) return AP_ERR_ARG;
+  // node indices are exact in float; the node count fits the index arithmetic
+  if (g->nx > (1 << 24) || g->ny > (1 << 24) || g->nz > (1 << 24)) return AP_ERR_ARG;
+  if ((double)g->nx * (double)g->ny * (double)g->nz > 1e12) return AP_ERR_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(g->lo[a]) || !std::isfinite(g->d[a]) || g->d[a] < 0.0) return AP_ERR_ARG;
+  const uintptr_t mask = g->f64 ? 7u : 3u;
+  bool any = false;
+  for (int c = 0; c < 6; ++c) {
+    if (!g->f[c]) continue;
+    if ((reinterpret_cast<uintptr_t>(g->f[c]) & mask) != 0) return AP_ERR_ALIGN;
+    any = true;
+  }
+  int rc = current_device_matches(h);
+  if (rc != AP_OK) return rc;
+  if (!any) return AP_OK;
+  apt::NodeArgs a;
+  std::memset(&a, 0, sizeof(a));
+  for (int c = 0; c < 6; ++c) {
+    a.f[c] = g->f[c];
+    if (g->f[c]) a.comp[a.n_comp++] = c;
+  }
+  a.nx = g->nx;
+  a.ny = g->ny;
+  a.nz = g->nz;
+  a.f64 = g->f64 ? 1 : 0;
+  a.accumulate = accumulate ? 1 : 0;
+  for (int c = 0; c < 3; ++c) {
+    a.lo[c] = g->lo[c];
+    a.d[c] = g->d[c];
+    a.lo_hi[c] = (float)g->lo[c];
+    a.lo_lo[c] = (float)(g->lo[c] - (double)a.lo_hi[c]);
+    a.d_hi[c] = (float)g->d[c];
+    a.d_lo[c] = (float)(g->d[c] - (double)a.d_hi[c]);
+  }
+  a.t = t;
+  a.sm_count = h->sm_count;
+  return apt::launch_nodes(h->descs[set].kind, precision, h->pd[set], h->pf[set], a, stream);
 }
 
 int ap_gather_push(ap_handle h, const ap_particles *p, const ap_grid *g, double t0, double dt,

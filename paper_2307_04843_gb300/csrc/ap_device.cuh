@@ -162,8 +162,9 @@ struct Pos<AP_FP64> {
   double x, y, z;
   __device__ void load(double X, double Y, double Z) { x = X; y = Y; z = Z; }
   __device__ void store(double *X, double *Y, double *Z) const { *X = x; *Y = y; *Z = z; }
-  __device__ void advance(double vx, double vy, double vz, double dt) {
-    x += dt * vx; y += dt * vy; z += dt * vz;
+  // dt_xy = dt, or 0 for a 1D-3V set
+  __device__ void advance(double vx, double vy, double vz, double dt_xy, double dt) {
+    x += dt_xy * vx; y += dt_xy * vy; z += dt * vz;
   }
   __device__ double xr() const { return x; }
   __device__ double yr() const { return y; }
@@ -176,8 +177,8 @@ struct Pos<AP_FP32_PHASE64> {
   __device__ void load(double X, double Y, double Z) { x = X; y = Y; z = Z; }
   __device__ void store(double *X, double *Y, double *Z) const { *X = x; *Y = y; *Z = z; }
   // dt u / gamma in float, accumulated in double
-  __device__ void advance(float vx, float vy, float vz, float dt) {
-    x += (double)(dt * vx); y += (double)(dt * vy); z += (double)(dt * vz);
+  __device__ void advance(float vx, float vy, float vz, float dt_xy, float dt) {
+    x += (double)(dt_xy * vx); y += (double)(dt_xy * vy); z += (double)(dt * vz);
   }
   __device__ float xr() const { return (float)x; }
   __device__ float yr() const { return (float)y; }
@@ -205,8 +206,9 @@ struct Pos<AP_FP32_PHASEFF> {
     p.lo = __fsub_rn(y, __fsub_rn(t, p.hi));
     p.hi = t;
   }
-  __device__ void advance(float vx, float vy, float vz, float dt) {
-    acc(x, __fmul_rn(dt, vx)); acc(y, __fmul_rn(dt, vy)); acc(z, __fmul_rn(dt, vz));
+  // a zero increment (1D-3V) leaves a normalised pair unchanged
+  __device__ void advance(float vx, float vy, float vz, float dt_xy, float dt) {
+    acc(x, __fmul_rn(dt_xy, vx)); acc(y, __fmul_rn(dt_xy, vy)); acc(z, __fmul_rn(dt, vz));
   }
   __device__ float xr() const { return __fadd_rn(x.hi, x.lo); }
   __device__ float yr() const { return __fadd_rn(y.hi, y.lo); }

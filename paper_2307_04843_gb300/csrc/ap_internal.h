@@ -46,6 +46,7 @@ struct Pulse {
   R lg_pref;                     // (sqrt(2) / w0)^{|l|}
   R a0, inv_w0, amp_unit;        // a0, 1/w0 and amp / a0 (adjoint: d/da0, d/dw0)
   R beta_f, inv_1mb;             // closed-form flying focus: v_f / c and 1 / (1 - beta_f)
+  R adv_xy;                      // 1, or 0 for 1D-3V sets (transverse position held)
   // carrier phase psi = omega (t - t_f) - k (z - z_f) + phase0 (double, host-exact)
   double omega, k, t_f, z_f, phase0;
   // float-float copies for AP_FP32_PHASEFF
@@ -113,6 +114,20 @@ struct EvalArgs {
   int *status;
 };
 
+// Staggered-node evaluation (ap_eval_nodes).  comp[0..n_comp) lists the
+// components present; lo and d also as float-float pairs for the
+// float-float arithmetic.
+struct NodeArgs {
+  void *f[6];
+  int nx, ny, nz;
+  int f64, accumulate;
+  int comp[6], n_comp;
+  double lo[3], d[3];
+  float lo_hi[3], lo_lo[3], d_hi[3], d_lo[3];
+  double t;
+  int sm_count;
+};
+
 // One launcher per pulse kind; precision selects the template instance.
 // `pulse_d` / `pulse_f` are host copies; `dpulse_*` device copies (batched).
 int launch_push(int kind, int precision, const Pulse<double> &pd, const Pulse<float> &pf,
@@ -121,6 +136,8 @@ int launch_eval(int kind, int precision, const Pulse<double> &pd, const Pulse<fl
                 const EvalArgs &a, void *stream);
 int launch_batch(int kind, int precision, const Pulse<double> *dpd, const Pulse<float> *dpf,
                  const BatchArgs &a, void *stream);
+int launch_nodes(int kind, int precision, const Pulse<double> &pd, const Pulse<float> &pf,
+                 const NodeArgs &a, void *stream);
 
 // per-kind entry points (ap_push_<kind>.cu)
 #define APT_DECLARE_KIND(K)                                                                       \
@@ -129,7 +146,9 @@ int launch_batch(int kind, int precision, const Pulse<double> *dpd, const Pulse<
   int launch_eval_##K(int precision, const Pulse<double> &pd, const Pulse<float> &pf,             \
                       const EvalArgs &a, void *stream);                                           \
   int launch_batch_##K(int precision, const Pulse<double> *dpd, const Pulse<float> *dpf,          \
-                       const BatchArgs &a, void *stream);
+                       const BatchArgs &a, void *stream);                                         \
+  int launch_nodes_##K(int precision, const Pulse<double> &pd, const Pulse<float> &pf,            \
+                       const NodeArgs &a, void *stream);
 APT_DECLARE_KIND(plane)
 APT_DECLARE_KIND(gauss)
 APT_DECLARE_KIND(lg)

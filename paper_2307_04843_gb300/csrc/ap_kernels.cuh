@@ -3,6 +3,8 @@
 // ap_push_<kind>.cu (AP_KIND_ID / AP_KIND_NAME set before inclusion).
 #pragma once
 
+#include <type_traits>
+
 #include "ap_device.cuh"
 
 namespace apt {
@@ -63,6 +65,7 @@ __device__ __forceinline__ double push_one(const Pulse<Real<PREC>> &P, const Pus
   TimeBase<PREC> tb;
   tb.init(P, a.t0, a.dt);
   const R dtR = (R)a.dt;
+  const R dtxy = dtR * P.adv_xy;
   const R h0 = R(1) / rsqrt_r(fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], R(1))))) - u[2];
   typename CacheOf<PREC, GRID>::type gc;
   if constexpr (GRID && !std::is_same<R, double>::value) grid_slots_init(gc, slots);
@@ -87,7 +90,7 @@ __device__ __forceinline__ double push_one(const Pulse<Real<PREC>> &P, const Pus
       analytic_fields<KIND, PREC>(P, L, E, B);
       if constexpr (GRID) grid_eval(gc, E, B);
       R ig = boris(u, E, B, dtR);
-      pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtR);
+      pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtxy, dtR);
       if (lf) {
         R dev = valid ? fabs((R(1) / ig - u[2]) - h0) : R(0);
         warp_max_to(lf + s0 + k, dev, 0xffffffffu);
@@ -268,6 +271,75 @@ __global__ void __launch_bounds__(256) eval_kernel(const __grid_constant__ Pulse
   }
 }
 
+// Analytic fields on the staggered nodes of a Yee grid (ap_eval_nodes).
+// blockIdx.y picks one present component c; threads stride over the nodes,
+// x fastest, so every store is coalesced.  Component c is sampled at
+// lo + (idx + off_c) d with the Yee offsets off = Ex (1/2,0,0), Ey (0,1/2,0),
+// Ez (0,0,1/2), Bx (0,1/2,1/2), By (1/2,0,1/2), Bz (1/2,1/2,0); E and B both
+// at time t.  The node index advances by the fixed grid stride with carries
+// (one division per thread), and in the float-float variant the node
+// position is formed in float-float arithmetic, so the loop issues no
+// double-precision instruction.
+__device__ __forceinline__ FF node_coord_ff(float f, float lo_hi, float lo_lo, float d_hi, float d_lo) {
+  FF p = two_prod(f, d_hi);
+  p.lo = __fmaf_rn(f, d_lo, p.lo);
+  FF s = two_sum(lo_hi, p.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(lo_lo, p.lo));
+  const float hi = __fadd_rn(s.hi, s.lo);
+  return {hi, __fsub_rn(s.lo, __fsub_rn(hi, s.hi))};
+}
+
+template <int KIND, int PREC, typename T>
+__global__ void __launch_bounds__(256) nodes_kernel(const __grid_constant__ Pulse<Real<PREC>> P,
+                                                    const __grid_constant__ NodeArgs a) {
+  using R = Real<PREC>;
+  using W = typename std::conditional<(sizeof(T) > sizeof(R)), T, R>::type;
+  const int c = a.comp[blockIdx.y];
+  T *__restrict__ f = static_cast<T *>(a.f[c]);
+  const float ox = (c == 0 || c == 4 || c == 5) ? 0.5f : 0.0f;
+  const float oy = (c == 1 || c == 3 || c == 5) ? 0.5f : 0.0f;
+  const float oz = (c == 2 || c == 3 || c == 4) ? 0.5f : 0.0f;
+  const long long nxy = (long long)a.nx * a.ny;
+  const long long total = nxy * a.nz;
+  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= total) return;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  // node (i, j, k) of n and the stride split the same way
+  long long k = n / nxy;
+  int j = (int)((n - k * nxy) / a.nx);
+  int i = (int)(n - k * nxy - (long long)j * a.nx);
+  const long long sk = stride / nxy;
+  const int sj = (int)((stride - sk * nxy) / a.nx);
+  const int si = (int)(stride - sk * nxy - (long long)sj * a.nx);
+  TimeBase<PREC> tb;
+  tb.init(P, a.t, 0.0);
+  const typename TimeBase<PREC>::Step st = tb.at(0);
+  for (; n < total; n += stride) {
+    Pos<PREC> pos;
+    if constexpr (PREC == AP_FP32_PHASEFF) {
+      pos.x = node_coord_ff((float)i + ox, a.lo_hi[0], a.lo_lo[0], a.d_hi[0], a.d_lo[0]);
+      pos.y = node_coord_ff((float)j + oy, a.lo_hi[1], a.lo_lo[1], a.d_hi[1], a.d_lo[1]);
+      pos.z = node_coord_ff((float)k + oz, a.lo_hi[2], a.lo_lo[2], a.d_hi[2], a.d_lo[2]);
+    } else {
+      pos.load(fma((double)i + ox, a.d[0], a.lo[0]), fma((double)j + oy, a.d[1], a.lo[1]),
+               fma((double)k + oz, a.d[2], a.lo[2]));
+    }
+    Local<R> L = local_coords<PREC>(P, st, pos);
+    R E[3], B[3];
+    analytic_fields<KIND, PREC>(P, L, E, B);
+    const R v = c == 0 ? E[0] : c == 1 ? E[1] : c == 2 ? E[2] : c == 3 ? B[0] : c == 4 ? B[1] : B[2];
+    f[n] = a.accumulate ? (T)((W)f[n] + (W)v) : (T)v;
+    // advance (i, j, k) by the stride
+    i += si;
+    int cj = 0;
+    if (i >= a.nx) { i -= a.nx; cj = 1; }
+    j += sj + cj;
+    long long ck = 0;
+    if (j >= a.ny) { j -= a.ny; ck = 1; }
+    k += sk + ck;
+  }
+}
+
 // ------------------------------------------------------------ launchers
 
 template <typename K>
@@ -320,6 +392,22 @@ int launch_eval_t(const Pulse<Real<PREC>> &P, const EvalArgs &a, void *stream) {
   return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }
 
+template <int KIND, int PREC>
+int launch_nodes_t(const Pulse<Real<PREC>> &P, const NodeArgs &a, void *stream) {
+  const long long total = (long long)a.nx * a.ny * a.nz;
+  const int block = 256;
+  long long gx = (total + block - 1) / block;
+  // enough resident threads per component to fill the GPU, then grid-stride
+  long long cap = ((long long)a.sm_count * 8 + a.n_comp - 1) / a.n_comp;
+  if (gx > cap) gx = cap;
+  if (gx < 1) gx = 1;
+  const dim3 grid((unsigned)gx, (unsigned)a.n_comp);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (a.f64) nodes_kernel<KIND, PREC, double><<<grid, block, 0, s>>>(P, a);
+  else nodes_kernel<KIND, PREC, float><<<grid, block, 0, s>>>(P, a);
+  return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+}
+
 template <int KIND, int PREC, bool GRID>
 int launch_batch_t(const Pulse<Real<PREC>> *sets, const BatchArgs &ba, void *stream) {
   auto kern = batch_kernel<KIND, PREC, GRID>;
@@ -361,6 +449,15 @@ int launch_batch_t(const Pulse<Real<PREC>> *sets, const BatchArgs &ba, void *str
       case AP_FP64: return launch_eval_t<KID, AP_FP64>(pd, a, stream);                            \
       case AP_FP32_PHASE64: return launch_eval_t<KID, AP_FP32_PHASE64>(pf, a, stream);            \
       case AP_FP32_PHASEFF: return launch_eval_t<KID, AP_FP32_PHASEFF>(pf, a, stream);            \
+      default: return AP_ERR_ARG;                                                                 \
+    }                                                                                             \
+  }                                                                                               \
+  int launch_nodes_##K(int precision, const Pulse<double> &pd, const Pulse<float> &pf,            \
+                       const NodeArgs &a, void *stream) {                                         \
+    switch (precision) {                                                                          \
+      case AP_FP64: return launch_nodes_t<KID, AP_FP64>(pd, a, stream);                           \
+      case AP_FP32_PHASE64: return launch_nodes_t<KID, AP_FP32_PHASE64>(pf, a, stream);           \
+      case AP_FP32_PHASEFF: return launch_nodes_t<KID, AP_FP32_PHASEFF>(pf, a, stream);           \
       default: return AP_ERR_ARG;                                                                 \
     }                                                                                             \
   }                                                                                               \

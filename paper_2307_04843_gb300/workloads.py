@@ -21,7 +21,13 @@ Fig. 7) examples:
               64 Gaussian components, v_f = 0.99, a0 = 5, 6000 steps;
   5 batch  -- 256 Gaussian sets, a0 ~ U[2, 20], w0 ~ U[2, 6] lambda,
               z_f ~ U[-10, 10] lambda, log-uniform counts in [1e4, 2e5],
-              2000 steps, mean final gamma per set and its gradient.
+              2000 steps, mean final gamma per set and its gradient;
+  6 sweep  -- reduced-dimensionality inverse Compton (Sec. 3.2, Fig. 6):
+              30 one-dimensional (1D-3V) electron lines at radii
+              (s + 1/2) 0.1 lambda in a focused Gaussian, a0 = 50, 3-lambda
+              intensity FWHM spot, 15-fs (4.5-cycle) intensity FWHM, and a
+              2.6-GeV (gamma 5088) counter-propagating beam of 15-fs
+              duration; 1e5 electrons per line, 4000 steps, one set per line.
 """
 import math
 
@@ -88,7 +94,20 @@ def config(index):
                         count=(1e4, 2e5)),
             box=((-10 * L, 10 * L), (-10 * L, 10 * L), (-20 * L, 20 * L)), grid=None,
             diag=dict(set_sums=True))
-    raise ValueError("workload index must be 1..5")
+    if index == 6:
+        cycle = 1.0 / 3.3356409519815204  # 1 fs in units of the laser period (lambda = 1 um)
+        fwhm_t = 15.0 * cycle * L         # 15 fs in 1 / omega0
+        return dict(
+            name="ics-sweep-1d3v", index=6, n_sets=30, per_set=100_000, n_steps=4000, dt=DT,
+            t0=-40.0, precision="fp32",
+            pulse=dict(kind="gauss", pol="x", env="gauss", env_len=fwhm_t, a0=50.0, omega=1.0,
+                       w0=3 * L / math.sqrt(2 * math.log(2)), z_focus=0.0, t_focus=0.0, phase0=0.0,
+                       longitudinal=True, one_d=True),
+            radius_step=0.1 * L,
+            beam=dict(gamma=2600.0 / 0.51099895, sigma_z=fwhm_t / (2 * math.sqrt(2 * math.log(2))),
+                      z_center=40.0),
+            box=None, grid=None, diag=dict(set_sums=True))
+    raise ValueError("workload index must be 1..6")
 
 
 def seed_for(index):
@@ -152,6 +171,26 @@ def batch_sets(cfg, seed=None):
         d.update(a0=float(a0[s]), w0=float(w0[s]), z_focus=float(zf[s]))
         sets.append(d)
     return sets, counts
+
+
+def sweep_lines(cfg, per_set=None, seed=None):
+    """Pulse sets and particles of the radial sweep (workload 6): set s holds
+    `per_set` electrons on the line x = (s + 1/2) dr, y = 0, with z drawn
+    from N(z_center, sigma_z) and u = (0, 0, -sqrt(gamma^2 - 1)).  Returns
+    (list of pulse dicts, particle dict, int64 offsets [n_sets + 1])."""
+    seed = seed_for(cfg["index"]) if seed is None else seed
+    m = cfg["per_set"] if per_set is None else int(per_set)
+    S = cfg["n_sets"]
+    b = cfg["beam"]
+    g = _rng(seed).standard_normal((S, m))
+    r = (np.arange(S) + 0.5) * cfg["radius_step"]
+    n = S * m
+    x = np.repeat(r, m)
+    z = (b["z_center"] + b["sigma_z"] * g).reshape(n)
+    uz = -math.sqrt(b["gamma"] ** 2 - 1.0)
+    parts = dict(x=x, y=np.zeros(n), z=z, ux=np.zeros(n), uy=np.zeros(n), uz=np.full(n, uz))
+    off = (np.arange(S + 1) * m).astype(np.int64)
+    return [dict(cfg["pulse"]) for _ in range(S)], parts, off
 
 
 def scaled_counts(counts, total):

@@ -87,6 +87,30 @@ def test_null_and_count_arguments(L):
     L.ap_graph_destroy(None)
 
 
+def test_node_and_yee_arguments_rejected_on_host(L):
+    """Argument checks of ap_eval_nodes and ap_yee1d_run run before any CUDA
+    call (no GPU needed)."""
+    g = _lib.ApYeeGrid()
+    g.nx = g.ny = g.nz = 4
+    assert L.ap_eval_nodes(None, 0, ctypes.byref(g), 0.0, 0, 0, None) == _lib.AP_ERR_ARG
+    y = _lib.ApYee1d()
+    y.nz, y.n_lines, y.dz, y.dt = 100, 1, 0.1, 0.05
+    assert L.ap_yee1d_run(None, 10, 0, None) == _lib.AP_ERR_ARG
+    assert L.ap_yee1d_run(ctypes.byref(y), -1, 0, None) == _lib.AP_ERR_ARG
+    assert L.ap_yee1d_run(ctypes.byref(y), 10, 1, None) == _lib.AP_ERR_ARG  # FP32 with double phase: no
+    for nz in (1, _lib.AP_YEE1D_MAX_NODES + 1):
+        y.nz = nz
+        assert L.ap_yee1d_run(ctypes.byref(y), 10, 0, None) == _lib.AP_ERR_ARG
+    y.nz, y.dz = 100, 0.0
+    assert L.ap_yee1d_run(ctypes.byref(y), 10, 0, None) == _lib.AP_ERR_ARG
+    y.dz, y.n_lines = 0.1, 0
+    assert L.ap_yee1d_run(ctypes.byref(y), 10, 0, None) == _lib.AP_OK  # nothing to do
+    y.n_lines = 1
+    assert L.ap_yee1d_run(ctypes.byref(y), 10, 0, None) == _lib.AP_ERR_ARG  # NULL arrays
+    y.E, y.B = 8, 20  # misaligned for double (never dereferenced: rejected first)
+    assert L.ap_yee1d_run(ctypes.byref(y), 10, 0, None) == _lib.AP_ERR_ALIGN
+
+
 def test_build_is_up_to_date_after_build(L):
     assert build.up_to_date()
     assert os.path.exists(build.LIB)

@@ -149,6 +149,24 @@ def test_adjoint_flying_focus_closed_form_vs_oracle_fd(precision):
 
 
 @pytest.mark.gpu
+def test_adjoint_one_d_lines_vs_oracle_fd():
+    """1D-3V set (transverse position held): the position update and its
+    reverse use dt only along z."""
+    pulse = dict(kind="gauss", pol="x", env="gauss", env_len=12.0, a0=6.0, w0=2.0 * L, z_focus=0.5,
+                 t_focus=0.0, longitudinal=True, one_d=True)
+    rng = np.random.default_rng(29)
+    n = 30
+    parts = dict(x=rng.uniform(-1, 1, n) * L, y=rng.uniform(-1, 1, n) * L, z=rng.uniform(-1, 1, n) * L,
+                 ux=rng.normal(0, 0.2, n), uy=rng.normal(0, 0.2, n), uz=rng.normal(0, 0.2, n))
+    off = np.array([0, n], dtype=np.int64)
+    t0, dt, n_steps, K = -8.0, 0.02, 600, 128
+    _, dJ = _run_adjoint([pulse], off, parts, t0, dt, n_steps, K, "fp64")
+    g = oracle.grad_fd(pulse, parts, t0, dt, n_steps, names=NAMES, rel_h=1e-4, scale=dict(z_focus=L))
+    for k, name in enumerate(NAMES):
+        assert abs(dJ[0, k] - g[name]) <= 1e-3 * max(abs(g[name]), 1e-8), (name, dJ[0, k], g[name])
+
+
+@pytest.mark.gpu
 def test_adjoint_with_linear_grid_field():
     """A grid holding linear fields (trilinear interpolation is then exact and
     smooth across cells) enters the trajectory and the position adjoint."""

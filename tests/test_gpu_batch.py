@@ -102,3 +102,35 @@ def test_batched_argument_errors():
         ws = torch.zeros(64, dtype=torch.int32, device="cuda")
         with pytest.raises(_lib.APError):
             _lib.ap_gather_push_batched(h.h, dev, d_off[:-1], None, 0.0, 0.02, 5, "fp32", None, ws)
+
+
+# ------------------------------------------------------------ radial sweep (1D-3V)
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_one_d_radial_sweep_matches_oracle(precision):
+    """Workload-6 shape (Sec. 3.2, Fig. 6): 30 one-dimensional lines at radii
+    (s + 1/2) 0.1 lambda, gamma 5088 counter-propagating through a Gaussian
+    with a0 = 50, one set per line in one batched launch; 40 electrons per
+    line, the 2000 steps up to the crossing of the beam centre and the pulse
+    peak (the largest momentum excursion).  The transverse position stays
+    where it started (to the float-float representation of the state in the
+    FP32 path); momenta and per-line sums of gamma match the oracle."""
+    cfg = workloads.config(6)
+    sets, parts, off = workloads.sweep_lines(cfg, per_set=40)
+    n_steps = 2000
+    out, sums, st = _run_batched(sets, off, parts, cfg["t0"], cfg["dt"], n_steps, precision)
+    assert st == 0
+    # held exactly in FP64; the float-float state returns its 48-bit copy of x
+    tol = 0.0 if precision == "fp64" else 2.0 ** -46
+    for k in ("x", "y"):
+        assert np.all(np.abs(out[k] - parts[k]) <= tol * np.abs(parts[k])), k
+    ref = oracle.push(sets[0], parts, cfg["t0"], cfg["dt"], n_steps, threads=THREADS)
+    e = rel_u_err(out, ref)
+    med, mx = (1e-10, 1e-7) if precision == "fp64" else (1e-4, 1e-3)
+    assert np.median(e) <= med and np.max(e) <= mx, (np.median(e), np.max(e))
+    ref_sums = oracle.set_gamma_sums(off, ref["ux"], ref["uy"], ref["uz"])
+    np.testing.assert_allclose(sums, ref_sums, rtol=1e-10 if precision == "fp64" else 1e-5)
+    # the pulse drives the lines, harder near the axis
+    ux_max = [np.max(np.abs(ref["ux"][off[s]:off[s + 1]])) for s in (0, len(sets) - 1)]
+    assert ux_max[0] > 10.0 and ux_max[0] > 2.0 * ux_max[1], ux_max

@@ -48,6 +48,9 @@ MUTATIONS = [
      "    for (int64_t k = 0; k + 1 < nz; ++k) B[k] -= r * (E[k + 1] - E[k]);\n  }", "yee1d_scheme"),
     ("Ex sampled on the cell node instead of the x edge", "    {0.5, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.0, 0.5},",
      "    {0.0, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.0, 0.5},", "staggering"),
+    ("1D-3V push moves the transverse position",
+     "      for (int a = s->p.one_d ? 2 : 0; a < 3; ++a) pos[a] += dt * u[a] / g;",
+     "      for (int a = 0; a < 3; ++a) pos[a] += dt * u[a] / g;", "one_d"),
     ("Bx sampled at the By position", "    {0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}, {0.5, 0.5, 0.0},",
      "    {0.5, 0.0, 0.5}, {0.5, 0.0, 0.5}, {0.5, 0.5, 0.0},", "staggering"),
 ]

@@ -637,3 +637,28 @@ def test_yee_nodes_special_cases():
     assert np.allclose(g[0, :, 0, 0], np.cos(0.9 - z), atol=1e-15, rtol=0)
     assert np.allclose(g[4, :, 0, 0], np.cos(0.9 - z - 0.25), atol=1e-15, rtol=0)
     assert np.all(g[[1, 2, 3, 5]] == 0.0)
+
+
+# ------------------------------------------------------------ reduced dimensionality
+
+def test_one_d_push_is_the_3d_push_for_a_plane_wave():
+    """1D-3V (Sec. 3.2): the transverse position is held while z and the
+    three momentum components advance.  A plane wave does not depend on x, y,
+    so z and u match the 3-D push exactly and x, y keep their initial values;
+    in a focused beam the held x changes the trajectory."""
+    rng = np.random.default_rng(4)
+    n = 6
+    parts = dict(x=rng.uniform(-1, 1, n) * L, y=rng.uniform(-1, 1, n) * L, z=rng.uniform(0, 1, n) * L,
+                 ux=rng.normal(0, 0.1, n), uy=rng.normal(0, 0.1, n), uz=rng.normal(0, 0.1, n))
+    pw = dict(kind="plane", pol="cp", env="sin2", env_len=4, a0=3.0)
+    a = oracle.push(pw, parts, 0.0, 0.02, 1500)
+    b = oracle.push(dict(pw, one_d=True), parts, 0.0, 0.02, 1500)
+    for k in ("z", "ux", "uy", "uz"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(b["x"], parts["x"]) and np.array_equal(b["y"], parts["y"])
+    assert np.max(np.abs(a["x"] - parts["x"])) > 0.1  # the 3-D push does move x
+    gb = dict(kind="gauss", pol="x", env="gauss", env_len=10.0, a0=5.0, w0=1.0 * L, longitudinal=True)
+    c = oracle.push(gb, parts, -8.0, 0.02, 900)
+    d = oracle.push(dict(gb, one_d=True), parts, -8.0, 0.02, 900)
+    assert np.array_equal(d["x"], parts["x"])
+    assert np.max(np.abs(c["ux"] - d["ux"])) > 1e-3
