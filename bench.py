@@ -154,13 +154,13 @@ def oracle_rate(pulse, parts, t0, dt, n_steps, wall_seconds, threads, grid=None)
     a threaded probe sizes the sample to about `wall_seconds` on `threads`
     host cores."""
     import oracle
-    probe_n, probe_steps = 2 * threads, 200
+    # probe: 64 particles per core over all steps, then scale to the target
+    probe_n = min(len(parts["x"]), 64 * threads)
     sub = {k: v[:probe_n] for k, v in parts.items()}
-    oracle.push(pulse, {k: v[:threads] for k, v in parts.items()}, t0, dt, 4, grid=grid, threads=threads)
     t = time.perf_counter()
-    oracle.push(pulse, sub, t0, dt, probe_steps, grid=grid, threads=threads)
-    rate = probe_n * probe_steps / (time.perf_counter() - t)
-    m = int(max(threads, min(len(parts["x"]), wall_seconds * rate / n_steps)))
+    oracle.push(pulse, sub, t0, dt, n_steps, grid=grid, threads=threads)
+    wall0 = time.perf_counter() - t
+    m = int(max(threads, min(len(parts["x"]), probe_n * wall_seconds / max(wall0, 1e-3))))
     m = max(threads, (m // threads) * threads)
     sub = {k: v[:m] for k, v in parts.items()}
     t = time.perf_counter()
