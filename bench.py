@@ -60,7 +60,11 @@ ALGO = {
 # ncu capture of the 1.6e6-particle x 4000-step case, scaled by particle-steps
 # (an upper bound at 1e7 particles: more particles share each cached cell);
 # None when the kernel changed after the capture.
-TRAFFIC_PER_PARTICLE_STEP = 5.336  # (34.084e9 read + 0.064e9 written) / 6.4e9
+TRAFFIC_PER_PARTICLE_STEP = {
+    "nodes": 5.336,  # (34.084e9 read + 0.064e9 written) / 6.4e9
+    "cells": 6.124,  # (39.128e9 read + 0.065e9 written) / 6.4e9
+    "arrays": None,
+}
 
 
 def parse():
@@ -73,7 +77,9 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="particles per GPU (default: the workload's)")
     ap.add_argument("--nsteps", type=int, default=None, help="Boris steps per call (default: the workload's)")
     ap.add_argument("--grid", type=int, default=256)
-    ap.add_argument("--soa-grid", action="store_true", help="gather from the six component arrays")
+    ap.add_argument("--grid-layout", default="cells", choices=["cells", "nodes", "arrays"],
+                    help="grid read by the push: per-cell coefficients, node-interleaved copy, "
+                         "or the six component arrays")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -224,7 +230,8 @@ class Workload:
         if cfg.get("grid") is not None:
             lo, hi = workloads.grid_box(cfg)
             g = workloads.grid_field(cfg["box"], args.grid, torch_device="cuda")
-            self.grid = (g, lo, hi) if args.soa_grid else _lib.pack_grid((g, lo, hi))
+            self.grid = (g, lo, hi) if args.grid_layout == "arrays" else \
+                _lib.pack_grid((g, lo, hi), layout=args.grid_layout)
             self.grid_host = (g, lo, hi)
         self.init = _lib.to_device(self.parts, self.precision)
         self.work = {k: v.clone() for k, v in self.init.items()}
@@ -277,11 +284,15 @@ def describe(wl, args):
                 "w0=2.55 lambda, 15 fs, one batched launch in a CUDA graph, float-float phase"}
     cfg = {"workload": names[wl.idx], "particles_per_gpu": wl.n, "boris_steps_per_call": wl.n_steps,
            "dt": c["dt"], "l2": "inputs larger than L2 (36 B/particle state%s); no flush" %
-           (", 402 MB grid + 537 MB node-interleaved copy" if wl.grid is not None else ""),
+           ((", 402 MB grid" + {"cells": " + 3.2 GB cell-coefficient copy",
+                                "nodes": " + 537 MB node-interleaved copy", "arrays": ""}[args.grid_layout])
+            if wl.grid is not None else ""),
            "parallelism": "dp%d (independent shards)" % dist_info()[0]}
     if wl.grid is not None:
         cfg["grid"] = args.grid
-        cfg["grid_layout"] = "six component arrays" if args.soa_grid else "node-interleaved (ap_grid_pack)"
+        cfg["grid_layout"] = {"cells": "per-cell trilinear coefficients (ap_grid_pack, AP_PACK_CELLS)",
+                              "nodes": "node-interleaved (ap_grid_pack, AP_PACK_NODES)",
+                              "arrays": "six component arrays"}[args.grid_layout]
     if wl.tuned:
         cfg["launch"] = {"block": wl.tuned["block"], "blocks_per_sm": wl.tuned["blocks_per_sm"],
                          "autotuned": True}
@@ -495,8 +506,8 @@ def run_ours(args):
         peak_ops = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12  # TOP/s
         achieved = al["fp32"] * rate_k / 1e12
         traffic = None
-        if args.workload == 2 and TRAFFIC_PER_PARTICLE_STEP is not None and not args.soa_grid:
-            traffic = TRAFFIC_PER_PARTICLE_STEP * units_rank
+        if args.workload == 2 and TRAFFIC_PER_PARTICLE_STEP.get(args.grid_layout) is not None:
+            traffic = TRAFFIC_PER_PARTICLE_STEP[args.grid_layout] * units_rank
         roofline = {"bound": "alu", "pipe": "fp32", "achieved": achieved, "peak": peak_ops, "unit": "TOP/s",
                     "frac": achieved / peak_ops, "traffic": traffic,
                     "algo_ops_per_particle_step": al["fp32"], "kernel_ms": kern * 1e3,

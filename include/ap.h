@@ -152,16 +152,28 @@ typedef struct {
  * [nz][ny][nx] with x fastest; nodes at lo + i (hi - lo)/(n - 1).  Positions
  * outside [lo, hi] are clamped to the box.  n >= 2 along every axis; the
  * f[] arrays need 4-byte alignment, `packed` 16-byte alignment.
- * `packed` (nullable) is a node-interleaved copy made by ap_grid_pack,
- * [nz][ny][nx][8] floats (Ex, Ey, Ez, Bx, By, Bz, 0, 0: one 32-byte sector
- * per node); when set, the push reads it instead of f[] (which may then be
- * NULL) and a cell refetch touches 8 sectors instead of 24. */
+ * `packed` (nullable) is a copy made by ap_grid_pack in the layout named by
+ * `packed_layout`:
+ *   AP_PACK_NODES: [nz][ny][nx][8] floats (Ex, Ey, Ez, Bx, By, Bz, 0, 0: one
+ *     32-byte sector per node); a cell refetch touches 8 sectors instead of
+ *     24; used by every precision, f[] may then be NULL;
+ *   AP_PACK_CELLS: [nz-1][ny-1][nx-1][48] floats, per cell and component the
+ *     trilinear coefficients (a0..a7) of
+ *       F = a0 + a1 wx + a2 wy + a3 wz + a4 wx wy + a5 wy wz + a6 wx wz + a7 wx wy wz
+ *     (w the position inside the cell, 0..1), each computed in double from
+ *     the corners and rounded once: one contiguous 192-byte record per cell;
+ *     the float pushes read it (7 FMA per component), the FP64 push and the
+ *     adjoint read f[], which must then be given. */
 typedef struct {
   const float *f[6];
   int32_t nx, ny, nz;
   double lo[3], hi[3];
   const float *packed;
+  int32_t packed_layout;
 } ap_grid;
+
+#define AP_PACK_NODES 0
+#define AP_PACK_CELLS 1
 
 /* Optional diagnostics, device memory, caller-owned; every pointer nullable.
  * Unless `accumulate` is nonzero the call zeroes the buffers it writes first. */
@@ -237,12 +249,14 @@ int ap_init_pulse(const ap_pulse_desc *descs, int32_t n_sets, ap_handle *out);
 /* Releases the handle and its device buffers (synchronises the device). */
 void ap_destroy(ap_handle h);
 
-/* Bytes of the node-interleaved grid copy (32 per node), 0 for a bad grid. */
+/* Bytes of the packed grid copy in layout g->packed_layout (AP_PACK_NODES:
+ * 32 per node; AP_PACK_CELLS: 192 per cell), 0 for a bad grid or layout. */
 size_t ap_grid_packed_bytes(const ap_grid *g);
 
-/* Writes the node-interleaved copy of g->f[] into `packed` (device,
- * caller-owned, ap_grid_packed_bytes(g) bytes, 16-byte aligned) on `stream`.
- * The gathered values are those of Sec. 2.1's grid field, only the layout
+/* Writes the packed copy of g->f[] in layout g->packed_layout into `packed`
+ * (device, caller-owned, ap_grid_packed_bytes(g) bytes, 16-byte aligned) on
+ * `stream`.  The interpolated field is that of Sec. 2.1's grid; only the
+ * layout (and, for AP_PACK_CELLS, the rounding of the coefficient form)
  * differs.  Errors: AP_ERR_ARG, AP_ERR_ALIGN, AP_ERR_CUDA. */
 int ap_grid_pack(const ap_grid *g, float *packed, void *stream);
 

@@ -31,6 +31,9 @@ PRECISIONS = {"fp64": 0, "fp32_phase64": 1, "fp32": 2, "fp32_phaseff": 2}
 AP_F_LONGITUDINAL = 1
 AP_F_YEE_DISP = 2
 AP_F_1D3V = 4
+AP_PACK_NODES = 0
+AP_PACK_CELLS = 1
+PACK_LAYOUTS = {"nodes": AP_PACK_NODES, "cells": AP_PACK_CELLS}
 AP_NPARAM = 4
 AP_OBJ_MEAN_GAMMA = 0
 AP_MAX_COMP = 128
@@ -62,7 +65,7 @@ class ApGrid(ctypes.Structure):
     _fields_ = [
         ("f", ctypes.c_void_p * 6), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
         ("nz", ctypes.c_int32), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
-        ("packed", ctypes.c_void_p),
+        ("packed", ctypes.c_void_p), ("packed_layout", ctypes.c_int32),
     ]
 
 
@@ -234,13 +237,15 @@ def particles_struct(p, precision, set_offsets=None):
 
 
 def grid_struct(grid):
-    """ap_grid from (tensor [6, nz, ny, nx] float32 CUDA, lo, hi[, packed]) or
-    None; `packed` is the node-interleaved copy made by ``pack_grid``."""
+    """ap_grid from (tensor [6, nz, ny, nx] float32 CUDA, lo, hi[, packed[,
+    layout]]) or None; `packed` is the copy made by ``pack_grid`` in `layout`
+    ("nodes", the default, or "cells")."""
     if grid is None:
         return None
     import torch
     g, lo, hi = grid[:3]
     packed = grid[3] if len(grid) > 3 else None
+    layout = PACK_LAYOUTS[grid[4]] if len(grid) > 4 else AP_PACK_NODES
     if g.dtype != torch.float32 or not g.is_cuda or not g.is_contiguous() or g.dim() != 4 or g.shape[0] != 6:
         raise ValueError("grid must be a contiguous CUDA float32 tensor [6, nz, ny, nx]")
     s = ApGrid()
@@ -250,6 +255,7 @@ def grid_struct(grid):
     for a in range(3):
         s.lo[a] = float(lo[a])
         s.hi[a] = float(hi[a])
+    s.packed_layout = layout
     if packed is not None:
         if packed.dtype != torch.float32 or not packed.is_cuda or packed.numel() * 4 != ap_grid_packed_bytes(s):
             raise ValueError("packed grid must be the CUDA float32 tensor made by pack_grid")
@@ -261,19 +267,21 @@ def ap_grid_packed_bytes(gs):
     return lib().ap_grid_packed_bytes(ctypes.byref(gs))
 
 
-def ap_grid_pack(grid, packed, stream=None):
-    gs = grid_struct(grid[:3])
+def ap_grid_pack(grid, packed, stream=None, layout="nodes"):
+    gs = grid_struct(tuple(grid[:3]) + (None, layout))
     check("ap_grid_pack", lib().ap_grid_pack(ctypes.byref(gs), _ptr(packed), _stream(stream)))
 
 
-def pack_grid(grid, stream=None):
-    """Node-interleaved copy of a grid (g, lo, hi); returns (g, lo, hi, packed)."""
+def pack_grid(grid, stream=None, layout="nodes"):
+    """Packed copy of a grid (g, lo, hi) in `layout` ("nodes": 32 B per node;
+    "cells": per-cell trilinear coefficients, 192 B per cell); returns
+    (g, lo, hi, packed, layout)."""
     import torch
     g, lo, hi = grid[:3]
-    gs = grid_struct((g, lo, hi))
+    gs = grid_struct((g, lo, hi, None, layout))
     packed = torch.empty(ap_grid_packed_bytes(gs) // 4, dtype=torch.float32, device=g.device)
-    ap_grid_pack((g, lo, hi), packed, stream)
-    return (g, lo, hi, packed)
+    ap_grid_pack((g, lo, hi), packed, stream, layout)
+    return (g, lo, hi, packed, layout)
 
 
 def diag_struct(diag):

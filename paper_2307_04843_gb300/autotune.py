@@ -25,9 +25,19 @@ def default_cache_path():
                           os.path.join(os.path.expanduser("~"), ".cache", "apt_autotune.json"))
 
 
+def _grid_tag(grid):
+    """The grid read by the push: none, the component arrays, or a packed copy
+    in its layout (the layouts differ in registers and shared memory)."""
+    if grid is None:
+        return "nogrid"
+    if len(grid) > 3 and grid[3] is not None:
+        return "grid-" + (grid[4] if len(grid) > 4 else "nodes")
+    return "grid-arrays"
+
+
 def _key(gpu, kind, precision, grid, n):
     bucket = int(math.log2(max(1, n)))
-    return "%s|%s|%s|grid%d|n2^%d" % (gpu, kind, precision, 1 if grid is not None else 0, bucket)
+    return "%s|%s|%s|%s|n2^%d" % (gpu, kind, precision, _grid_tag(grid), bucket)
 
 
 def _load(path):

@@ -504,6 +504,10 @@ int ap_push_adjoint(ap_handle h, const ap_particles *p0, const ap_grid *g, doubl
   std::memset(&aa, 0, sizeof(aa));
   rc = apt::handle_push_args(h, p0, g, t0, dt, n_steps, precision, &aa.base, stream);
   if (rc != AP_OK) return rc;
+  if (aa.base.grid.cells) {
+    rc = apt::drop_cell_layout(aa.base.grid);
+    if (rc != AP_OK) return rc;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(dJ_dparams, 0, sizeof(double) * AP_NPARAM * ns, s) != cudaSuccess ||
       (J_out && cudaMemsetAsync(J_out, 0, sizeof(double) * ns, s) != cudaSuccess) ||

@@ -314,12 +314,15 @@ int make_grid(const ap_grid *g, apt::GridView &v) {
   if (!g) return AP_OK;
   if (g->nx < 2 || g->ny < 2 || g->nz < 2) return AP_ERR_ARG;
   const int n[3] = {g->nx, g->ny, g->nz};
+  if (g->packed_layout != AP_PACK_NODES && g->packed_layout != AP_PACK_CELLS) return AP_ERR_ARG;
+  const bool cells = g->packed && g->packed_layout == AP_PACK_CELLS;
   if (g->packed) {
     if (!aligned16(g->packed)) return AP_ERR_ALIGN;
-    v.packed = reinterpret_cast<const float4 *>(g->packed);
+    if (cells) v.cells = reinterpret_cast<const float4 *>(g->packed);
+    else v.packed = reinterpret_cast<const float4 *>(g->packed);
   }
   for (int c = 0; c < 6; ++c) {
-    if (!g->f[c] && !g->packed) return AP_ERR_ARG;
+    if (!g->f[c] && !v.packed && !cells) return AP_ERR_ARG;
     if (g->f[c] && (reinterpret_cast<uintptr_t>(g->f[c]) & 3u)) return AP_ERR_ALIGN;
     v.f[c] = g->f[c];
   }
@@ -395,6 +398,12 @@ int fill_push_args(ap_handle_s *h, const ap_particles *p, const ap_grid *g, doub
   rc = make_grid(g, a.grid);
   if (rc != AP_OK) return rc;
   a.grid_on = g != nullptr;
+  // the double push interpolates the raw corners: the coefficient copy is
+  // float-rounded, so it reads the component arrays instead
+  if (a.grid.cells && precision == AP_FP64) {
+    rc = apt::drop_cell_layout(a.grid);
+    if (rc != AP_OK) return rc;
+  }
   rc = make_diag(diag, n_steps, n_sets_diag, a.diag, stream);
   if (rc != AP_OK) return rc;
   a.status = h->d_status;
@@ -407,6 +416,13 @@ int fill_push_args(ap_handle_s *h, const ap_particles *p, const ap_grid *g, doub
 }  // namespace
 
 namespace apt {
+
+int drop_cell_layout(GridView &v) {
+  for (int c = 0; c < 6; ++c)
+    if (!v.f[c]) return AP_ERR_ARG;
+  v.cells = nullptr;
+  return AP_OK;
+}
 
 // Accessors used by the adjoint translation unit.
 int handle_info(ap_handle h, int *device, int *sm_count, int *n_sets, int *uniform_kind,

@@ -836,6 +836,74 @@ __device__ __forceinline__ void grid_eval(const GridSlots &gc, float E[3], float
   B[0] += o[3]; B[1] += o[4]; B[2] += o[5];
 }
 
+// ------------------------------------- shared-memory cell-coefficient cache
+// With the per-cell coefficient copy (AP_PACK_CELLS) a thread keeps the 48
+// coefficients of its current cell in 12 shared-memory slots (slot 2c holds
+// a0..a3 and slot 2c+1 a4..a7 of component c), refetched as 12 contiguous
+// 16-byte cp.async copies of one 192-byte record, and evaluates each
+// component with 7 FMA:
+//   F = a0 + a3 wz + wy (a2 + a5 wz) + wx (a1 + a6 wz + wy (a4 + a7 wz)).
+struct CellSlots {
+  float ox, oy, oz;  // lower corner of the cached cell in grid units
+  float wx, wy, wz;  // weights of the current step
+  unsigned s0;       // shared-window address of this thread's slot 0
+  unsigned step;     // bytes between consecutive slots of one thread
+};
+
+__device__ __forceinline__ void grid_slots_init(CellSlots &gc, void *slots_base) {
+  gc.ox = gc.oy = gc.oz = -16.0f;
+  gc.s0 = (unsigned)__cvta_generic_to_shared(slots_base) + 16u * threadIdx.x;
+  gc.step = 16u * blockDim.x;
+}
+
+// Every lane of the warp calls this together (warp-uniform refetch branch).
+__device__ __forceinline__ void grid_fetch(const GridView &g, CellSlots &gc, float x, float y,
+                                           float z) {
+  const float fx = grid_unit<float>(x, g.inv_d[0], g.off[0], g.nx);
+  const float fy = grid_unit<float>(y, g.inv_d[1], g.off[1], g.ny);
+  const float fz = grid_unit<float>(z, g.inv_d[2], g.off[2], g.nz);
+  float wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
+  const bool need = !(wx >= 0.0f && wx <= 1.0f && wy >= 0.0f && wy <= 1.0f && wz >= 0.0f && wz <= 1.0f);
+  if (__any_sync(0xffffffffu, need) && need) {
+    auto corner = [](float f, int n, int &i) {
+      float c = __fsub_rn(__fadd_rn(__fsub_rn(f, 0.5f), kRoundMagic), kRoundMagic);
+      c = fminf(fmaxf(c, 0.0f), (float)(n - 2));
+      i = __float_as_int(__fadd_rn(c, kRoundMagic)) - __float_as_int(kRoundMagic);
+      return c;
+    };
+    int ix, iy, iz;
+    gc.ox = corner(fx, g.nx, ix);
+    gc.oy = corner(fy, g.ny, iy);
+    gc.oz = corner(fz, g.nz, iz);
+    wx = fx - gc.ox;
+    wy = fy - gc.oy;
+    wz = fz - gc.oz;
+    const size_t cell = ((size_t)iz * (g.ny - 1) + iy) * (g.nx - 1) + ix;
+    const float4 *src = g.cells + 12 * cell;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) cp_async16(gc.s0 + k * gc.step, src + k);
+  }
+  gc.wx = wx;
+  gc.wy = wy;
+  gc.wz = wz;
+}
+
+__device__ __forceinline__ void grid_eval(const CellSlots &gc, float E[3], float B[3]) {
+  cp_async_wait_all();  // this thread's copies (if any) have landed
+  const float wx = gc.wx, wy = gc.wy, wz = gc.wz;
+  float o[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const float4 a = lds128(gc.s0 + (2 * c) * gc.step);
+    const float4 b = lds128(gc.s0 + (2 * c + 1) * gc.step);
+    const float X = fmaf(b.z, wz, fmaf(fmaf(b.w, wz, b.x), wy, a.y));  // a1 + a6 wz + wy (a4 + a7 wz)
+    const float Y = fmaf(b.y, wz, a.z);                                // a2 + a5 wz
+    o[c] = fmaf(X, wx, fmaf(Y, wy, fmaf(a.w, wz, a.x)));              // a0 + a3 wz + wy Y + wx X
+  }
+  E[0] += o[0]; E[1] += o[1]; E[2] += o[2];
+  B[0] += o[3]; B[1] += o[4]; B[2] += o[5];
+}
+
 // ------------------------------------------------------------ Boris push
 // Relativistic Boris step (Boris 1970) for charge -1, mass 1: half electric
 // kick, rotation about B with tan(angle/2) = |tau|, half electric kick.

@@ -62,6 +62,7 @@ struct Pulse {
 struct GridView {
   const float *f[6];
   const float4 *packed;   // node-interleaved [nz][ny][nx][2] float4, or null
+  const float4 *cells;    // per-cell trilinear coefficients [nz-1][ny-1][nx-1][12] float4, or null
   int nx, ny, nz;
   float lo[3], inv_d[3];  // node spacing d = (hi - lo)/(n - 1)
   double lo_d[3], inv_d_d[3];
@@ -155,6 +156,10 @@ APT_DECLARE_KIND(lg)
 APT_DECLARE_KIND(flying)
 APT_DECLARE_KIND(flyingcf)
 #undef APT_DECLARE_KIND
+
+// The FP64 push and the adjoint read raw corners: they use f[] instead of a
+// per-cell coefficient copy (AP_ERR_ARG when f[] is missing).
+int drop_cell_layout(GridView &v);
 
 // status bits written by kernels
 constexpr int kStatusNonfinite = 1;

@@ -19,19 +19,41 @@ constexpr int kStepChunk = 32;
 __host__ __device__ constexpr size_t step_table_bytes(int threads) { return 16u * (size_t)threads; }
 __host__ __device__ constexpr size_t grid_slot_bytes(int threads) { return 256u * (size_t)threads; }
 
+// Grid modes of the push kernels: no grid, corner values (component arrays
+// or the node-interleaved copy), per-cell coefficients (float kernels only).
+constexpr int kGridNone = 0;
+constexpr int kGridNodes = 1;
+constexpr int kGridCells = 2;
+
 // Grid cell cache of a variant: registers for double, shared memory for float.
-template <int PREC, bool GRID>
+template <int PREC, int GRID>
 struct CacheOf {
   using type = GridCache<Real<PREC>>;
 };
 template <>
-struct CacheOf<AP_FP32_PHASE64, true> {
+struct CacheOf<AP_FP32_PHASE64, kGridNodes> {
   using type = GridSlots;
 };
 template <>
-struct CacheOf<AP_FP32_PHASEFF, true> {
+struct CacheOf<AP_FP32_PHASEFF, kGridNodes> {
   using type = GridSlots;
 };
+template <>
+struct CacheOf<AP_FP32_PHASE64, kGridCells> {
+  using type = CellSlots;
+};
+template <>
+struct CacheOf<AP_FP32_PHASEFF, kGridCells> {
+  using type = CellSlots;
+};
+
+// shared-memory bytes of the cell cache per block of T threads
+template <int PREC, int GRID>
+__host__ __device__ constexpr size_t grid_cache_bytes(int threads) {
+  return PREC == AP_FP64 || GRID == kGridNone ? 0
+         : GRID == kGridCells                ? 192u * (size_t)threads
+                                             : grid_slot_bytes(threads);
+}
 
 // One particle through n_steps fused steps: load (a2), per step the local
 // coordinates and phase (a3), envelope and profile (a4-a7), grid gather
@@ -42,7 +64,7 @@ struct CacheOf<AP_FP32_PHASEFF, true> {
 // never wait for each other).  `valid` is false for padding threads, which
 // run the loop on a dummy particle so that warp operations see every lane.
 // Returns the final gamma (double) of a valid particle, 0 otherwise.
-template <int KIND, int PREC, bool GRID>
+template <int KIND, int PREC, int GRID>
 __device__ __forceinline__ double push_one(const Pulse<Real<PREC>> &P, const PushArgs &a,
                                            long long i, bool valid, StepFF *s_steps,
                                            void *slots) {
@@ -137,8 +159,8 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
 // trip count is uniform across the block), one particle per thread, every
 // step fused.  Dynamic shared memory: step tables, grid slots (float grid
 // kernels), then the histogram (hist_off bytes in).
-template <int KIND, int PREC, bool GRID>
-__global__ void __launch_bounds__(256)
+template <int KIND, int PREC, int GRID>
+__global__ void __launch_bounds__(256, GRID == kGridCells ? 3 : 1)
     push_kernel(const __grid_constant__ Pulse<Real<PREC>> P, const __grid_constant__ PushArgs a,
                 unsigned hist_off) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -179,7 +201,7 @@ __global__ void __launch_bounds__(256)
 // tile count and no block waits on another.
 // Dynamic shared memory: step tables, grid slots (float grid kernels), then
 // the [n_sets + 1] tile prefix (prefix_off bytes in).
-template <int KIND, int PREC, bool GRID>
+template <int KIND, int PREC, int GRID>
 __global__ void __launch_bounds__(256) batch_kernel(const Pulse<Real<PREC>> *__restrict__ sets,
                                                     const __grid_constant__ BatchArgs ba,
                                                     unsigned prefix_off) {
@@ -351,11 +373,9 @@ inline int occupancy_blocks(K kernel, int block, size_t smem) {
 }
 
 // dynamic shared memory before the kernel-specific tail (histogram / prefix)
-template <int PREC, bool GRID>
+template <int PREC, int GRID>
 inline size_t push_smem_head(int block) {
-  size_t s = step_table_bytes(block);
-  if (GRID && PREC != AP_FP64) s += grid_slot_bytes(block);
-  return s;
+  return step_table_bytes(block) + grid_cache_bytes<PREC, GRID>(block);
 }
 
 template <typename K>
@@ -367,7 +387,7 @@ inline int set_smem(K kern, size_t smem) {
              : AP_ERR_CUDA;
 }
 
-template <int KIND, int PREC, bool GRID>
+template <int KIND, int PREC, int GRID>
 int launch_push_t(const Pulse<Real<PREC>> &P, const PushArgs &a, void *stream) {
   auto kern = push_kernel<KIND, PREC, GRID>;
   const int block = a.shape.block;
@@ -408,7 +428,7 @@ int launch_nodes_t(const Pulse<Real<PREC>> &P, const NodeArgs &a, void *stream) 
   return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }
 
-template <int KIND, int PREC, bool GRID>
+template <int KIND, int PREC, int GRID>
 int launch_batch_t(const Pulse<Real<PREC>> *sets, const BatchArgs &ba, void *stream) {
   auto kern = batch_kernel<KIND, PREC, GRID>;
   const int block = ba.base.shape.block;
@@ -422,6 +442,25 @@ int launch_batch_t(const Pulse<Real<PREC>> *sets, const BatchArgs &ba, void *str
   return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }
 
+// grid mode of a call: none, corners, or (float kernels) per-cell coefficients
+template <int KIND, int PREC>
+int launch_push_mode(const Pulse<Real<PREC>> &P, const PushArgs &a, void *stream) {
+  if (!a.grid_on) return launch_push_t<KIND, PREC, kGridNone>(P, a, stream);
+  if constexpr (PREC != AP_FP64) {
+    if (a.grid.cells) return launch_push_t<KIND, PREC, kGridCells>(P, a, stream);
+  }
+  return launch_push_t<KIND, PREC, kGridNodes>(P, a, stream);
+}
+
+template <int KIND, int PREC>
+int launch_batch_mode(const Pulse<Real<PREC>> *sets, const BatchArgs &ba, void *stream) {
+  if (!ba.base.grid_on) return launch_batch_t<KIND, PREC, kGridNone>(sets, ba, stream);
+  if constexpr (PREC != AP_FP64) {
+    if (ba.base.grid.cells) return launch_batch_t<KIND, PREC, kGridCells>(sets, ba, stream);
+  }
+  return launch_batch_t<KIND, PREC, kGridNodes>(sets, ba, stream);
+}
+
 }  // namespace apt
 
 // Per-kind launchers: dispatch on precision and grid.
@@ -431,14 +470,11 @@ int launch_batch_t(const Pulse<Real<PREC>> *sets, const BatchArgs &ba, void *str
                       const PushArgs &a, void *stream) {                                          \
     switch (precision) {                                                                          \
       case AP_FP64:                                                                               \
-        return a.grid_on ? launch_push_t<KID, AP_FP64, true>(pd, a, stream)                       \
-                         : launch_push_t<KID, AP_FP64, false>(pd, a, stream);                     \
+        return launch_push_mode<KID, AP_FP64>(pd, a, stream);                                     \
       case AP_FP32_PHASE64:                                                                       \
-        return a.grid_on ? launch_push_t<KID, AP_FP32_PHASE64, true>(pf, a, stream)               \
-                         : launch_push_t<KID, AP_FP32_PHASE64, false>(pf, a, stream);             \
+        return launch_push_mode<KID, AP_FP32_PHASE64>(pf, a, stream);                             \
       case AP_FP32_PHASEFF:                                                                       \
-        return a.grid_on ? launch_push_t<KID, AP_FP32_PHASEFF, true>(pf, a, stream)               \
-                         : launch_push_t<KID, AP_FP32_PHASEFF, false>(pf, a, stream);             \
+        return launch_push_mode<KID, AP_FP32_PHASEFF>(pf, a, stream);                             \
       default:                                                                                    \
         return AP_ERR_ARG;                                                                        \
     }                                                                                             \
@@ -465,14 +501,11 @@ int launch_batch_t(const Pulse<Real<PREC>> *sets, const BatchArgs &ba, void *str
                        const BatchArgs &a, void *stream) {                                        \
     switch (precision) {                                                                          \
       case AP_FP64:                                                                               \
-        return a.base.grid_on ? launch_batch_t<KID, AP_FP64, true>(dpd, a, stream)                \
-                              : launch_batch_t<KID, AP_FP64, false>(dpd, a, stream);              \
+        return launch_batch_mode<KID, AP_FP64>(dpd, a, stream);                                   \
       case AP_FP32_PHASE64:                                                                       \
-        return a.base.grid_on ? launch_batch_t<KID, AP_FP32_PHASE64, true>(dpf, a, stream)        \
-                              : launch_batch_t<KID, AP_FP32_PHASE64, false>(dpf, a, stream);      \
+        return launch_batch_mode<KID, AP_FP32_PHASE64>(dpf, a, stream);                           \
       case AP_FP32_PHASEFF:                                                                       \
-        return a.base.grid_on ? launch_batch_t<KID, AP_FP32_PHASEFF, true>(dpf, a, stream)        \
-                              : launch_batch_t<KID, AP_FP32_PHASEFF, false>(dpf, a, stream);      \
+        return launch_batch_mode<KID, AP_FP32_PHASEFF>(dpf, a, stream);                           \
       default:                                                                                    \
         return AP_ERR_ARG;                                                                        \
     }                                                                                             \

@@ -313,3 +313,67 @@ def test_packed_grid_layout_gives_identical_results(precision):
     b, _, _ = gpu_push(cfg["pulse"], parts, -10.0, 0.02, 800, precision, grid=packed)
     for k in a:
         np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.gpu
+def test_cell_coefficient_layout_reconstructs_corners():
+    """AP_PACK_CELLS holds, per cell and component, the monomial coefficients
+    of the trilinear interpolant: summing them back at the 8 corners gives the
+    grid values to float rounding (each coefficient rounded once from double)."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    cfg = workloads.config(2)
+    g, lo, hi = _grid_small(cfg, n=17)
+    nz, ny, nx = g.shape[1:]
+    packed = _lib.pack_grid((torch.as_tensor(g).cuda(), lo, hi), layout="cells")
+    a = packed[3].view(nz - 1, ny - 1, nx - 1, 6, 8).double().cpu().numpy()
+    f = g.astype(np.float64)
+    for (i, j, k) in ((0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0), (0, 0, 1), (1, 0, 1), (0, 1, 1), (1, 1, 1)):
+        val = (a[..., 0] + i * a[..., 1] + j * a[..., 2] + k * a[..., 3] + i * j * a[..., 4] + j * k * a[..., 5]
+               + i * k * a[..., 6] + i * j * k * a[..., 7])
+        ref = np.moveaxis(f[:, k:k + nz - 1, j:j + ny - 1, i:i + nx - 1], 0, -1)
+        assert np.max(np.abs(val - ref)) <= 3 * 2.0 ** -24, (i, j, k)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp32", "fp32_phase64", "fp64"])
+def test_cell_coefficient_layout_push_matches_oracle(precision):
+    """The float pushes read the per-cell coefficients (7 FMA per component);
+    the FP64 push falls back to the component arrays.  Workload-2 shape on a
+    40^3 grid, 300 particles, 4000 steps, against the oracle."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    cfg = workloads.config(2)
+    parts = workloads.particles(cfg, n=300)
+    g, lo, hi = _grid_small(cfg)
+    gd = torch.as_tensor(g).cuda()
+    packed = _lib.pack_grid((gd, lo, hi), layout="cells")
+    out, _, st = gpu_push(cfg["pulse"], parts, cfg["t0"], cfg["dt"], cfg["n_steps"], precision, grid=packed)
+    assert st == 0
+    ref = oracle.push(cfg["pulse"], parts, cfg["t0"], cfg["dt"], cfg["n_steps"], grid=(g, lo, hi), threads=THREADS)
+    _check(out, ref, precision)
+    if precision == "fp64":  # identical to the component-array push
+        a, _, _ = gpu_push(cfg["pulse"], parts, cfg["t0"], cfg["dt"], cfg["n_steps"], precision, grid=(gd, lo, hi))
+        for k in a:
+            np.testing.assert_array_equal(a[k], out[k])
+
+
+@pytest.mark.gpu
+def test_cell_layout_without_arrays_rejected_for_fp64():
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    cfg = workloads.config(2)
+    g, lo, hi = _grid_small(cfg, n=9)
+    gd = torch.as_tensor(g).cuda()
+    packed = _lib.pack_grid((gd, lo, hi), layout="cells")
+    gs = _lib.grid_struct(packed)
+    for c in range(6):
+        gs.f[c] = None
+    parts = _lib.to_device(workloads.particles(cfg, n=10), "fp64")
+    with _lib.Handle(cfg["pulse"]) as h:
+        ps = _lib.particles_struct(parts, "fp64")
+        import ctypes
+        rc = _lib.lib().ap_gather_push(h.h, ctypes.byref(ps), ctypes.byref(gs), 0.0, 0.02, 5, 0, None,
+                                       _lib._stream(None))
+        assert rc == _lib.AP_ERR_ARG
+        assert h.status() == 0
