@@ -295,6 +295,8 @@ def describe(wl, args):
                               "arrays": "six component arrays"}[args.grid_layout]
     if wl.tuned:
         cfg["launch"] = {"block": wl.tuned["block"], "blocks_per_sm": wl.tuned["blocks_per_sm"],
+                         "grid_cache": ("registers" if wl.tuned.get("grid_cache") else "shared memory")
+                         if wl.grid is not None else None,
                          "autotuned": True}
     return cfg
 

@@ -222,7 +222,9 @@ typedef struct {
 typedef struct {
   int32_t block;          /* threads per block, multiple of 32, <= 1024 */
   int32_t blocks_per_sm;  /* persistent kernels: resident blocks per SM */
-  int32_t ppt;            /* particles per thread (1 or 2) */
+  int32_t grid_cache;     /* float pushes with a AP_PACK_CELLS grid: where a thread keeps its
+                             current cell, 0 shared memory (12 slots, cp.async refetch),
+                             1 registers (48 registers, load refetch) */
 } ap_launch_cfg;
 
 typedef struct ap_handle_s *ap_handle;

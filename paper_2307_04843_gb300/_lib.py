@@ -93,7 +93,7 @@ class ApYee1d(ctypes.Structure):
 
 
 class ApLaunchCfg(ctypes.Structure):
-    _fields_ = [("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("ppt", ctypes.c_int32)]
+    _fields_ = [("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("grid_cache", ctypes.c_int32)]
 
 
 # every entry point declared in include/ap.h: name -> (restype, argtypes)
@@ -331,8 +331,8 @@ def ap_destroy(h):
     lib().ap_destroy(h)
 
 
-def ap_set_launch(h, block=0, blocks_per_sm=0, ppt=0):
-    cfg = ApLaunchCfg(block, blocks_per_sm, ppt)
+def ap_set_launch(h, block=0, blocks_per_sm=0, grid_cache=0):
+    cfg = ApLaunchCfg(block, blocks_per_sm, grid_cache)
     check("ap_set_launch", lib().ap_set_launch(h, ctypes.byref(cfg)))
 
 
@@ -498,8 +498,8 @@ class Handle:
     def __exit__(self, *exc):
         self.close()
 
-    def set_launch(self, block=0, blocks_per_sm=0, ppt=0):
-        ap_set_launch(self.h, block, blocks_per_sm, ppt)
+    def set_launch(self, block=0, blocks_per_sm=0, grid_cache=0):
+        ap_set_launch(self.h, block, blocks_per_sm, grid_cache)
 
     def push(self, particles, t0, dt, n_steps, precision="fp32", grid=None, diag=None, stream=None):
         ap_gather_push(self.h, particles, grid, t0, dt, n_steps, precision, diag, stream)

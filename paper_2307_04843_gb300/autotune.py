@@ -5,8 +5,11 @@ arithmetic, grid on/off -- register counts range from ~40 to ~130 per
 thread) and on the problem size.  ``tune`` times a short push of a sample of
 the caller's particles for each candidate shape with CUDA events and keeps
 the fastest; results are cached in a JSON file keyed by GPU name, kind,
-precision, grid flag and a size bucket.  Every shape gives bit-identical
+precision, grid layout and a size bucket.  Every shape gives bit-identical
 particle states (the per-particle arithmetic does not depend on the launch).
+With a per-cell coefficient grid the sweep also tries keeping the cell in
+registers instead of shared memory (``grid_cache``), which trades occupancy
+for shared-memory traffic; both give bit-identical states too.
 """
 import json
 import math
@@ -71,14 +74,15 @@ def tune(handle, particles, t0, dt, precision="fp32", grid=None, sample_n=2_000_
         cache = _load(path)
     if not force and key in cache:
         best = cache[key]
-        handle.set_launch(best["block"], best["blocks_per_sm"])
+        handle.set_launch(best["block"], best["blocks_per_sm"], best.get("grid_cache", 0))
         return dict(best, cached=True)
+    caches = (0, 1) if _grid_tag(grid) == "grid-cells" and precision != "fp64" else (0,)
     m = int(min(n, sample_n))
     sample = {k: v[:m].clone() for k, v in particles.items()}
     work = {k: v.clone() for k, v in sample.items()}
     results = []
-    for block, bps in candidates:
-        handle.set_launch(block, bps)
+    for (block, bps), gc in [(c, g) for g in caches for c in candidates]:
+        handle.set_launch(block, bps, gc)
         for k in work:
             work[k].copy_(sample[k])
         handle.push(work, t0, dt, 8, precision=precision, grid=grid)  # warm (module load, caches)
@@ -91,11 +95,11 @@ def tune(handle, particles, t0, dt, precision="fp32", grid=None, sample_n=2_000_
         b.record()
         torch.cuda.synchronize()
         sec = a.elapsed_time(b) / 1e3
-        results.append((m * sample_steps / sec, block, bps))
-    rate, block, bps = max(results)
-    handle.set_launch(block, bps)
-    best = dict(block=block, blocks_per_sm=bps, rate=rate,
-                sweep=[dict(block=b_, blocks_per_sm=p_, rate=r_) for r_, b_, p_ in results])
+        results.append((m * sample_steps / sec, block, bps, gc))
+    rate, block, bps, gc = max(results)
+    handle.set_launch(block, bps, gc)
+    best = dict(block=block, blocks_per_sm=bps, grid_cache=gc, rate=rate,
+                sweep=[dict(block=b_, blocks_per_sm=p_, grid_cache=g_, rate=r_) for r_, b_, p_, g_ in results])
     with _lock:
         cache = _load(path)
         cache[key] = best

@@ -24,7 +24,7 @@ struct ap_handle_s {
   Pulse<double> *d_pd = nullptr;
   Pulse<float> *d_pf = nullptr;
   int *d_status = nullptr;
-  apt::LaunchShape shape{0, 0, 1};
+  apt::LaunchShape shape{0, 0, 0};
 };
 
 struct ap_graph_s {
@@ -568,13 +568,13 @@ int ap_num_sets(ap_handle h) { return h ? h->n_sets : AP_ERR_ARG; }
 int ap_set_launch(ap_handle h, const ap_launch_cfg *cfg) {
   if (!h) return AP_ERR_ARG;
   if (!cfg) {
-    h->shape = apt::LaunchShape{0, 0, 1};
+    h->shape = apt::LaunchShape{0, 0, 0};
     return AP_OK;
   }
   if (cfg->block != 0 && (cfg->block < 32 || cfg->block > 256 || (cfg->block & 31))) return AP_ERR_ARG;
   if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 64) return AP_ERR_ARG;
-  if (cfg->ppt != 0 && cfg->ppt != 1) return AP_ERR_ARG;
-  h->shape = apt::LaunchShape{cfg->block, cfg->blocks_per_sm, 1};
+  if (cfg->grid_cache != 0 && cfg->grid_cache != 1) return AP_ERR_ARG;
+  h->shape = apt::LaunchShape{cfg->block, cfg->blocks_per_sm, cfg->grid_cache};
   return AP_OK;
 }
 

@@ -904,6 +904,66 @@ __device__ __forceinline__ void grid_eval(const CellSlots &gc, float E[3], float
   B[0] += o[3]; B[1] += o[4]; B[2] += o[5];
 }
 
+// The same coefficients held in 48 registers instead (grid_cache = 1): a
+// refetch is 12 16-byte loads into the cache registers, issued at the start
+// of the step and consumed after the analytic field; no shared memory.
+struct CellRegs {
+  float ox, oy, oz;
+  float wx, wy, wz;
+  float4 c[12];
+};
+
+__device__ __forceinline__ void grid_slots_init(CellRegs &gc, void *) {
+  gc.ox = gc.oy = gc.oz = -16.0f;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) gc.c[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+__device__ __forceinline__ void grid_fetch(const GridView &g, CellRegs &gc, float x, float y,
+                                           float z) {
+  const float fx = grid_unit<float>(x, g.inv_d[0], g.off[0], g.nx);
+  const float fy = grid_unit<float>(y, g.inv_d[1], g.off[1], g.ny);
+  const float fz = grid_unit<float>(z, g.inv_d[2], g.off[2], g.nz);
+  float wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
+  const bool need = !(wx >= 0.0f && wx <= 1.0f && wy >= 0.0f && wy <= 1.0f && wz >= 0.0f && wz <= 1.0f);
+  if (__any_sync(0xffffffffu, need) && need) {
+    auto corner = [](float f, int n, int &i) {
+      float c = __fsub_rn(__fadd_rn(__fsub_rn(f, 0.5f), kRoundMagic), kRoundMagic);
+      c = fminf(fmaxf(c, 0.0f), (float)(n - 2));
+      i = __float_as_int(__fadd_rn(c, kRoundMagic)) - __float_as_int(kRoundMagic);
+      return c;
+    };
+    int ix, iy, iz;
+    gc.ox = corner(fx, g.nx, ix);
+    gc.oy = corner(fy, g.ny, iy);
+    gc.oz = corner(fz, g.nz, iz);
+    wx = fx - gc.ox;
+    wy = fy - gc.oy;
+    wz = fz - gc.oz;
+    const size_t cell = ((size_t)iz * (g.ny - 1) + iy) * (g.nx - 1) + ix;
+    const float4 *src = g.cells + 12 * cell;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) gc.c[k] = __ldg(src + k);
+  }
+  gc.wx = wx;
+  gc.wy = wy;
+  gc.wz = wz;
+}
+
+__device__ __forceinline__ void grid_eval(const CellRegs &gc, float E[3], float B[3]) {
+  const float wx = gc.wx, wy = gc.wy, wz = gc.wz;
+  float o[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const float4 a = gc.c[2 * c], b = gc.c[2 * c + 1];
+    const float X = fmaf(b.z, wz, fmaf(fmaf(b.w, wz, b.x), wy, a.y));
+    const float Y = fmaf(b.y, wz, a.z);
+    o[c] = fmaf(X, wx, fmaf(Y, wy, fmaf(a.w, wz, a.x)));
+  }
+  E[0] += o[0]; E[1] += o[1]; E[2] += o[2];
+  B[0] += o[3]; B[1] += o[4]; B[2] += o[5];
+}
+
 // ------------------------------------------------------------ Boris push
 // Relativistic Boris step (Boris 1970) for charge -1, mass 1: half electric
 // kick, rotation about B with tan(angle/2) = |tau|, half electric kick.

@@ -82,7 +82,7 @@ struct DiagView {
 struct LaunchShape {
   int block;
   int blocks_per_sm;
-  int ppt;
+  int grid_cache;  // 0: cell in shared memory, 1: in registers (AP_PACK_CELLS only)
 };
 
 // Host-side launchers implemented in the per-kind translation units.

@@ -24,6 +24,7 @@ __host__ __device__ constexpr size_t grid_slot_bytes(int threads) { return 256u 
 constexpr int kGridNone = 0;
 constexpr int kGridNodes = 1;
 constexpr int kGridCells = 2;
+constexpr int kGridCellsReg = 3;  // per-cell coefficients cached in registers
 
 // Grid cell cache of a variant: registers for double, shared memory for float.
 template <int PREC, int GRID>
@@ -46,13 +47,21 @@ template <>
 struct CacheOf<AP_FP32_PHASEFF, kGridCells> {
   using type = CellSlots;
 };
+template <>
+struct CacheOf<AP_FP32_PHASE64, kGridCellsReg> {
+  using type = CellRegs;
+};
+template <>
+struct CacheOf<AP_FP32_PHASEFF, kGridCellsReg> {
+  using type = CellRegs;
+};
 
 // shared-memory bytes of the cell cache per block of T threads
 template <int PREC, int GRID>
 __host__ __device__ constexpr size_t grid_cache_bytes(int threads) {
-  return PREC == AP_FP64 || GRID == kGridNone ? 0
-         : GRID == kGridCells                ? 192u * (size_t)threads
-                                             : grid_slot_bytes(threads);
+  return PREC == AP_FP64 || GRID == kGridNone || GRID == kGridCellsReg ? 0
+         : GRID == kGridCells                                         ? 192u * (size_t)threads
+                                                                      : grid_slot_bytes(threads);
 }
 
 // One particle through n_steps fused steps: load (a2), per step the local
@@ -160,7 +169,7 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
 // step fused.  Dynamic shared memory: step tables, grid slots (float grid
 // kernels), then the histogram (hist_off bytes in).
 template <int KIND, int PREC, int GRID>
-__global__ void __launch_bounds__(256, GRID == kGridCells ? 3 : 1)
+__global__ void __launch_bounds__(256, GRID == kGridCells ? 3 : GRID == kGridCellsReg ? 2 : 1)
     push_kernel(const __grid_constant__ Pulse<Real<PREC>> P, const __grid_constant__ PushArgs a,
                 unsigned hist_off) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -447,7 +456,9 @@ template <int KIND, int PREC>
 int launch_push_mode(const Pulse<Real<PREC>> &P, const PushArgs &a, void *stream) {
   if (!a.grid_on) return launch_push_t<KIND, PREC, kGridNone>(P, a, stream);
   if constexpr (PREC != AP_FP64) {
-    if (a.grid.cells) return launch_push_t<KIND, PREC, kGridCells>(P, a, stream);
+    if (a.grid.cells)
+      return a.shape.grid_cache ? launch_push_t<KIND, PREC, kGridCellsReg>(P, a, stream)
+                                : launch_push_t<KIND, PREC, kGridCells>(P, a, stream);
   }
   return launch_push_t<KIND, PREC, kGridNodes>(P, a, stream);
 }
@@ -456,7 +467,9 @@ template <int KIND, int PREC>
 int launch_batch_mode(const Pulse<Real<PREC>> *sets, const BatchArgs &ba, void *stream) {
   if (!ba.base.grid_on) return launch_batch_t<KIND, PREC, kGridNone>(sets, ba, stream);
   if constexpr (PREC != AP_FP64) {
-    if (ba.base.grid.cells) return launch_batch_t<KIND, PREC, kGridCells>(sets, ba, stream);
+    if (ba.base.grid.cells)
+      return ba.base.shape.grid_cache ? launch_batch_t<KIND, PREC, kGridCellsReg>(sets, ba, stream)
+                                      : launch_batch_t<KIND, PREC, kGridCells>(sets, ba, stream);
   }
   return launch_batch_t<KIND, PREC, kGridNodes>(sets, ba, stream);
 }

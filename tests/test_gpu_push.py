@@ -377,3 +377,27 @@ def test_cell_layout_without_arrays_rejected_for_fp64():
                                        _lib._stream(None))
         assert rc == _lib.AP_ERR_ARG
         assert h.status() == 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp32", "fp32_phase64"])
+def test_cell_cache_in_registers_or_shared_memory_identical(precision):
+    """The autotuner may keep a thread's grid cell in registers or in shared
+    memory, with any block shape: the per-particle arithmetic is the same, so
+    the states are bit-identical; the batched kernel too."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    cfg = workloads.config(2)
+    parts = workloads.particles(cfg, n=3000)
+    g, lo, hi = _grid_small(cfg, n=33)
+    packed = _lib.pack_grid((torch.as_tensor(g).cuda(), lo, hi), layout="cells")
+    base, _, _ = gpu_push(cfg["pulse"], parts, -10.0, 0.02, 600, precision, grid=packed)
+    with _lib.Handle(cfg["pulse"]) as h:
+        for block, bps, gc in ((128, 0, 1), (64, 2, 1), (256, 0, 0), (96, 0, 1)):
+            h.set_launch(block, bps, gc)
+            dev = _lib.to_device(parts, precision)
+            h.push(dev, -10.0, 0.02, 600, precision=precision, grid=packed)
+            out = _lib.to_host(dev)
+            for k in base:
+                np.testing.assert_array_equal(out[k], base[k], err_msg=str((block, bps, gc, k)))
+        assert h.status() == 0
