@@ -62,7 +62,7 @@ ALGO = {
 # None when the kernel changed after the capture.
 TRAFFIC_PER_PARTICLE_STEP = {
     "nodes": 5.336,  # (34.084e9 read + 0.064e9 written) / 6.4e9
-    "cells": 6.124,  # (39.128e9 read + 0.065e9 written) / 6.4e9
+    "cells": 6.061,  # (38.729e9 read + 0.064e9 written) / 6.4e9, cell in registers
     "arrays": None,
 }
 
@@ -81,6 +81,8 @@ def parse():
                     help="grid read by the push: per-cell coefficients, node-interleaved copy, "
                          "or the six component arrays")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch", default=None,
+                    help="fixed launch shape BLOCK[,BLOCKS_PER_SM[,GRID_CACHE]] instead of the autotuner's")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -236,7 +238,11 @@ class Workload:
         self.init = _lib.to_device(self.parts, self.precision)
         self.work = {k: v.clone() for k, v in self.init.items()}
         self.tuned = None
-        if not args.no_autotune and idx not in (5, 6):
+        if args.launch:
+            shape = [int(v) for v in args.launch.split(",")] + [0, 0]
+            self.h.set_launch(shape[0], shape[1], shape[2])
+            self.tuned = {"block": shape[0], "blocks_per_sm": shape[1], "grid_cache": shape[2], "fixed": True}
+        elif not args.no_autotune and idx not in (5, 6):
             from paper_2307_04843_gb300 import autotune
             self.tuned = autotune.tune(self.h, self.init, self.t0, self.dt, self.precision, self.grid,
                                        sample_n=min(self.n, 2_000_000), sample_steps=min(self.n_steps, 200))
@@ -297,7 +303,7 @@ def describe(wl, args):
         cfg["launch"] = {"block": wl.tuned["block"], "blocks_per_sm": wl.tuned["blocks_per_sm"],
                          "grid_cache": ("registers" if wl.tuned.get("grid_cache") else "shared memory")
                          if wl.grid is not None else None,
-                         "autotuned": True}
+                         "autotuned": not wl.tuned.get("fixed", False)}
     return cfg
 
 
