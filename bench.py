@@ -349,6 +349,11 @@ def grid_node_rates(wl, stream):
             hbm = float(json.load(fh)["hbm_gbs"])
     except (OSError, KeyError, ValueError):
         pass
+    # a plane wave (fields depend on z and t only): one evaluation per row of
+    # nodes, streamed along it; all six arrays written
+    plane = dict(kind="plane", pol="x", env="sgauss", sg_order=4, env_len=30.0, a0=1.0)
+    with _lib.Handle(plane) as hp:
+        psec = timed(lambda: hp.eval_nodes(f, lo, d, 0.0, precision="fp32"), 3)
     del f
     E = torch.zeros((YEE_LINES, YEE_NZ), dtype=torch.float32, device="cuda")
     B = torch.zeros_like(E)
@@ -360,6 +365,10 @@ def grid_node_rates(wl, stream):
                        "alu_frac": ops / sec / peak_ops,
                        "hbm_frac": (bytes_ / sec / 1e9 / hbm) if hbm else None,
                        "ops_per_node": 6 * NODE_OPS_PER_EVAL, "bytes_per_node": 24},
+        "eval_nodes_plane": {"value": nodes / psec, "unit": "nodes/s", "ms": psec * 1e3,
+                             "grid": "%d^3, 6 staggered components, float arrays, plane wave" % n,
+                             "hbm_frac": (bytes_ / psec / 1e9 / hbm) if hbm else None,
+                             "bytes_per_node": 24},
         "yee1d": {"value": YEE_LINES * YEE_NZ * YEE_STEPS / ysec, "unit": "node-steps/s",
                   "ms": ysec * 1e3, "lines": YEE_LINES, "nz": YEE_NZ, "steps": YEE_STEPS,
                   "dtype": "f32"},

@@ -216,7 +216,7 @@ typedef struct {
   double dz, dt;
 } ap_yee1d;
 
-#define AP_YEE1D_MAX_NODES 12288  /* nodes per line: the line lives in shared memory */
+#define AP_YEE1D_MAX_NODES 12288  /* nodes per line: the line stays on chip (registers) */
 
 /* Launch shape, chosen by the autotuner (0 = library default). */
 typedef struct {
@@ -373,7 +373,7 @@ int ap_num_sets(ap_handle h);
  * accumulate = 0 stores E1/B1; nonzero adds them to what f[] holds (the
  * total field E1 + E2 that the push interpolates).  precision as for
  * ap_eval_fields; the result is rounded once to the array type.
- * Errors: AP_ERR_ARG (bad set, sizes < 1 or above 2^24 per axis or 10^12
+ * Errors: AP_ERR_ARG (bad set, sizes < 1 or above 2^23 per axis or 10^12
  * nodes in all, negative or non-finite spacing), AP_ERR_ALIGN, AP_ERR_CUDA. */
 int ap_eval_nodes(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int32_t accumulate,
                   int32_t precision, void *stream);
@@ -386,7 +386,8 @@ int ap_eval_nodes(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int3
  * E[0] and B[nz-1] are held fixed (the ends of the line).  Each product and
  * difference is rounded separately in the stated order (no fused
  * multiply-add).  All steps run in one launch, one block per line with the
- * line in shared memory.  precision: AP_FP64 (double arrays) or
+ * line on chip: in registers, a few consecutive nodes per thread (double
+ * lines longer than 6144 nodes: in shared memory).  precision: AP_FP64 (double arrays) or
  * AP_FP32_PHASEFF (float arrays).  Errors: AP_ERR_ARG (nz < 2 or above
  * AP_YEE1D_MAX_NODES, n_lines < 0, n_steps < 0), AP_ERR_ALIGN, AP_ERR_CUDA. */
 int ap_yee1d_run(const ap_yee1d *y, int64_t n_steps, int32_t precision, void *stream);

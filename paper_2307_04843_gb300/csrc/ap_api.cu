@@ -595,8 +595,9 @@ int ap_eval_nodes(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int3
   if (!h || !g || set < 0 || set >= h->n_sets) return AP_ERR_ARG;
   if (precision < AP_FP64 || precision > AP_FP32_PHASEFF) return AP_ERR_ARG;
   if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !std::isfinite(t)) return AP_ERR_ARG;
-  // node indices are exact in float; the node count fits the index arithmetic
-  if (g->nx > (1 << 24) || g->ny > (1 << 24) || g->nz > (1 << 24)) return AP_ERR_ARG;
+  // node indices (and index + grid stride) are exact in float; the node
+  // count fits the index arithmetic
+  if (g->nx > (1 << 23) || g->ny > (1 << 23) || g->nz > (1 << 23)) return AP_ERR_ARG;
   if ((double)g->nx * (double)g->ny * (double)g->nz > 1e12) return AP_ERR_ARG;
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(g->lo[a]) || !std::isfinite(g->d[a]) || g->d[a] < 0.0) return AP_ERR_ARG;
@@ -612,10 +613,18 @@ int ap_eval_nodes(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int3
   if (!any) return AP_OK;
   apt::NodeArgs a;
   std::memset(&a, 0, sizeof(a));
+  // plane waves: E_z = B_z = 0, and E_x, B_y (E_y, B_x) vanish with p_x (p_y);
+  // adding an identically zero component is skipped
+  const apt::Pulse<double> &P = h->pd[set];
+  const bool px0 = P.px_re == 0.0 && P.px_im == 0.0, py0 = P.py_re == 0.0 && P.py_im == 0.0;
+  const bool zero[6] = {px0, py0, true, py0, px0, true};
   for (int c = 0; c < 6; ++c) {
     a.f[c] = g->f[c];
-    if (g->f[c]) a.comp[a.n_comp++] = c;
+    if (!g->f[c]) continue;
+    if (accumulate && P.kind == AP_PLANE && zero[c]) continue;
+    a.comp[a.n_comp++] = c;
   }
+  if (a.n_comp == 0) return AP_OK;
   a.nx = g->nx;
   a.ny = g->ny;
   a.nz = g->nz;

@@ -335,22 +335,31 @@ __global__ void __launch_bounds__(256) nodes_kernel(const __grid_constant__ Puls
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= total) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  // node (i, j, k) of n and the stride split the same way
-  long long k = n / nxy;
-  int j = (int)((n - k * nxy) / a.nx);
-  int i = (int)(n - k * nxy - (long long)j * a.nx);
-  const long long sk = stride / nxy;
-  const int sj = (int)((stride - sk * nxy) / a.nx);
-  const int si = (int)(stride - sk * nxy - (long long)sj * a.nx);
+  // node (i, j, k) of n and the stride split the same way; every index is
+  // below 2^23 (checked on the host), so index + stride stays exact in float
+  int k = (int)(n / nxy);
+  int j = (int)((n - (long long)k * nxy) / a.nx);
+  int i = (int)(n - (long long)k * nxy - (long long)j * a.nx);
+  const long long sk64 = stride / nxy;
+  const int sj = (int)((stride - sk64 * nxy) / a.nx);
+  const int si = (int)(stride - sk64 * nxy - (long long)sj * a.nx);
+  const int sk = (int)(sk64 < (1 << 30) ? sk64 : (1 << 30));
+  // float copies of the indices, advanced alongside (int -> float
+  // conversions run on the double-precision pipe)
+  float fi = (float)i, fj = (float)j, fk = (float)k;
+  const float fsi = (float)si, fsj = (float)sj, fsk = (float)sk;
+  const float fnx = (float)a.nx, fny = (float)a.ny;
   TimeBase<PREC> tb;
   tb.init(P, a.t, 0.0);
   const typename TimeBase<PREC>::Step st = tb.at(0);
   for (; n < total; n += stride) {
     Pos<PREC> pos;
     if constexpr (PREC == AP_FP32_PHASEFF) {
-      pos.x = node_coord_ff((float)i + ox, a.lo_hi[0], a.lo_lo[0], a.d_hi[0], a.d_lo[0]);
-      pos.y = node_coord_ff((float)j + oy, a.lo_hi[1], a.lo_lo[1], a.d_hi[1], a.d_lo[1]);
-      pos.z = node_coord_ff((float)k + oz, a.lo_hi[2], a.lo_lo[2], a.d_hi[2], a.d_lo[2]);
+      // the transverse coordinates enter the fields in float; only z feeds
+      // the carrier phase and needs the float-float sum
+      pos.x = FF{fmaf(fi + ox, a.d_hi[0], a.lo_hi[0]), 0.0f};
+      pos.y = FF{fmaf(fj + oy, a.d_hi[1], a.lo_hi[1]), 0.0f};
+      pos.z = node_coord_ff(fk + oz, a.lo_hi[2], a.lo_lo[2], a.d_hi[2], a.d_lo[2]);
     } else {
       pos.load(fma((double)i + ox, a.d[0], a.lo[0]), fma((double)j + oy, a.d[1], a.lo[1]),
                fma((double)k + oz, a.d[2], a.lo[2]));
@@ -360,14 +369,17 @@ __global__ void __launch_bounds__(256) nodes_kernel(const __grid_constant__ Puls
     analytic_fields<KIND, PREC>(P, L, E, B);
     const R v = c == 0 ? E[0] : c == 1 ? E[1] : c == 2 ? E[2] : c == 3 ? B[0] : c == 4 ? B[1] : B[2];
     f[n] = a.accumulate ? (T)((W)f[n] + (W)v) : (T)v;
-    // advance (i, j, k) by the stride
+    // advance (i, j, k) by the stride (k only grows until the loop ends)
     i += si;
+    fi += fsi;
     int cj = 0;
-    if (i >= a.nx) { i -= a.nx; cj = 1; }
+    if (i >= a.nx) { i -= a.nx; fi -= fnx; cj = 1; }
     j += sj + cj;
-    long long ck = 0;
-    if (j >= a.ny) { j -= a.ny; ck = 1; }
-    k += sk + ck;
+    fj += fsj + (cj ? 1.0f : 0.0f);
+    int ck = 0;
+    if (j >= a.ny) { j -= a.ny; fj -= fny; ck = 1; }
+    k = min(k + sk + ck, 1 << 30);
+    fk += fsk + (ck ? 1.0f : 0.0f);
   }
 }
 
@@ -421,10 +433,61 @@ int launch_eval_t(const Pulse<Real<PREC>> &P, const EvalArgs &a, void *stream) {
   return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }
 
+// Plane waves (Eqs. plane_func, plane_b) depend on z and t only: one field
+// evaluation per row of nx nodes (every lane of the row's warp computes the
+// same value), then the warp streams it along the row, so for nx >= 32 the
+// kernel is bound by the stores, not the arithmetic.
+template <int PREC, typename T>
+__global__ void __launch_bounds__(256) nodes_plane_kernel(const __grid_constant__ Pulse<Real<PREC>> P,
+                                                          const __grid_constant__ NodeArgs a) {
+  using R = Real<PREC>;
+  using W = typename std::conditional<(sizeof(T) > sizeof(R)), T, R>::type;
+  const int c = a.comp[blockIdx.y];
+  T *__restrict__ f = static_cast<T *>(a.f[c]);
+  const float oz = (c == 2 || c == 3 || c == 4) ? 0.5f : 0.0f;
+  const long long rows = (long long)a.ny * a.nz;
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  TimeBase<PREC> tb;
+  tb.init(P, a.t, 0.0);
+  const typename TimeBase<PREC>::Step st = tb.at(0);
+  for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+    const int k = (int)(r / a.ny);
+    Pos<PREC> pos;
+    if constexpr (PREC == AP_FP32_PHASEFF) {
+      pos.x = FF{0.0f, 0.0f};
+      pos.y = FF{0.0f, 0.0f};
+      pos.z = node_coord_ff((float)k + oz, a.lo_hi[2], a.lo_lo[2], a.d_hi[2], a.d_lo[2]);
+    } else {
+      pos.load(0.0, 0.0, fma((double)k + oz, a.d[2], a.lo[2]));
+    }
+    Local<R> L = local_coords<PREC>(P, st, pos);
+    R E[3], B[3];
+    analytic_fields<AP_PLANE, PREC>(P, L, E, B);
+    const R v = c == 0 ? E[0] : c == 1 ? E[1] : c == 2 ? E[2] : c == 3 ? B[0] : c == 4 ? B[1] : B[2];
+    T *row = f + r * a.nx;
+    for (int i = lane; i < a.nx; i += 32) row[i] = a.accumulate ? (T)((W)row[i] + (W)v) : (T)v;
+  }
+}
+
 template <int KIND, int PREC>
 int launch_nodes_t(const Pulse<Real<PREC>> &P, const NodeArgs &a, void *stream) {
   const long long total = (long long)a.nx * a.ny * a.nz;
   const int block = 256;
+  if constexpr (KIND == AP_PLANE) {
+    if (a.nx >= 32) {
+      const long long rows = (long long)a.ny * a.nz;
+      long long gx = (rows + 7) / 8;  // 8 warps (rows) per block
+      long long cap = ((long long)a.sm_count * 8 + a.n_comp - 1) / a.n_comp;
+      if (gx > cap) gx = cap;
+      if (gx < 1) gx = 1;
+      const dim3 grid((unsigned)gx, (unsigned)a.n_comp);
+      cudaStream_t s = static_cast<cudaStream_t>(stream);
+      if (a.f64) nodes_plane_kernel<PREC, double><<<grid, block, 0, s>>>(P, a);
+      else nodes_plane_kernel<PREC, float><<<grid, block, 0, s>>>(P, a);
+      return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+    }
+  }
   long long gx = (total + block - 1) / block;
   // enough resident threads per component to fill the GPU, then grid-stride
   long long cap = ((long long)a.sm_count * 8 + a.n_comp - 1) / a.n_comp;

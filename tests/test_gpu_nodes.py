@@ -127,8 +127,8 @@ def test_nodes_bad_arguments():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("nz,n_lines,n_steps", [(2, 1, 3), (1000, 3, 400), (4099, 2, 150),
-                                                (12288, 1, 40)])
+@pytest.mark.parametrize("nz,n_lines,n_steps", [(2, 1, 3), (1000, 3, 400), (2048, 2, 100), (4099, 2, 150),
+                                                (6000, 1, 60), (6145, 1, 50), (12288, 1, 40)])
 def test_yee1d_double_bit_exact(nz, n_lines, n_steps):
     import torch
     from paper_2307_04843_gb300 import _lib
@@ -210,3 +210,65 @@ def test_fig2e_fourth_order_peak_second_order_edge_on_gpu():
     for p, (ep, ee) in zip(ppls, res):
         op, oe = _apt_vs_yee_errors(p, True)
         assert abs(ep - op) <= 1e-6 * op + 1e-13 and abs(ee - oe) <= 1e-6 * oe + 1e-13, (p, ep, op, ee, oe)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,f64", [("fp64", True), ("fp32", False)])
+@pytest.mark.parametrize("pol", ["x", "cp"])
+def test_plane_wave_rows_match_oracle(precision, f64, pol):
+    """Plane waves depend on z and t only: for rows of >= 32 nodes one field
+    evaluation per row is streamed along it.  Store and accumulate both
+    match the oracle on every node (accumulating skips components that are
+    identically zero, which leaves them as they were)."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    pulse = dict(kind="plane", pol=pol, env="sgauss", sg_order=4, env_len=20.0, a0=2.0, t_focus=5.0,
+                 yee=True, yee_dx=L / 40, yee_dt=0.5 * L / 40)
+    shape = (13, 5, 70)  # rows of 70 nodes: two full warps and a ragged third
+    lo, d, t = (0.3, -0.7, -2.0 * L), (0.2, 0.3, 0.31 * L), 6.5
+    ref = oracle.yee_nodes(pulse, shape, lo, d, t)
+    dtype = torch.float64 if f64 else torch.float32
+    tol = 1e-10 * pulse["a0"] if precision == "fp64" else 4e-6 * pulse["a0"]
+    with _lib.Handle(pulse) as h:
+        f = _grid(shape, dtype)
+        h.eval_nodes(f, lo, d, t, precision=precision)
+        got = np.stack([x.double().cpu().numpy() for x in f])
+        assert np.max(np.abs(got - ref)) <= tol
+        prior = np.random.default_rng(8).standard_normal((6,) + shape)
+        f = _grid(shape, dtype, fill=prior)
+        h.eval_nodes(f, lo, d, t, accumulate=True, precision=precision)
+        got = np.stack([x.double().cpu().numpy() for x in f])
+        assert np.max(np.abs(got - (prior.astype(dtype == torch.float32 and np.float32 or np.float64) + ref))) <= tol + 1e-6
+        assert h.status() == 0
+    assert np.max(np.abs(ref)) > 0.5
+
+
+def _yee_float32_reference(E, B, dz, dt, n_steps):
+    """The scheme with every product and difference rounded to float32 in
+    the stated order (numpy float32 arithmetic, no fused multiply-add)."""
+    E = np.array(E, dtype=np.float32)
+    B = np.array(B, dtype=np.float32)
+    r = np.float32(dt / dz)
+    hr = np.float32(0.5 * (dt / dz))
+    for _ in range(n_steps):
+        B[:-1] = B[:-1] - hr * (E[1:] - E[:-1])
+        E[1:] = E[1:] - r * (B[1:] - B[:-1])
+        B[:-1] = B[:-1] - hr * (E[1:] - E[:-1])
+    return E, B
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("nz", [700, 3001, 6144, 12288])
+def test_yee1d_float_bit_exact_all_blockings(nz):
+    """Every register blocking (1, 4, 8 and 16 nodes per thread) gives the
+    same float result as the plain per-node update."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    rng = np.random.default_rng(nz)
+    E0 = rng.standard_normal(nz).astype(np.float32)
+    B0 = rng.standard_normal(nz).astype(np.float32)
+    E = torch.as_tensor(E0).cuda()
+    B = torch.as_tensor(B0).cuda()
+    _lib.ap_yee1d_run(E, B, 0.05, 0.0475, 37)
+    Er, Br = _yee_float32_reference(E0, B0, 0.05, 0.0475, 37)
+    assert np.array_equal(E.cpu().numpy(), Er) and np.array_equal(B.cpu().numpy(), Br)
