@@ -34,22 +34,27 @@ constexpr int kAdjBlock = 128;
 constexpr int kAdjBlocksPerSm = 4;
 constexpr int kAdjMaxK = 256;
 constexpr int kAdjStateBytes = 48;  // one saved state: 6 doubles or 9 floats
-constexpr int kTan = 5;  // tangents: x, y, z - z_f, w0, beta_f
+// tangents: x, y, z - z_f, w0 and, for the closed-form flying focus only,
+// beta_f (the other kinds do not depend on it: a fifth tangent would be
+// dead arithmetic in every dual operation)
+template <int KIND>
+__host__ __device__ constexpr int tangents() { return KIND == AP_FLYING_CF ? 5 : 4; }
 constexpr int kNp = 4;   // parameters: a0, w0, z_f, beta_f
 
 // Pulse view with the w0-dependent constants as duals (tangent slot 3) and,
 // for the closed-form flying focus, the beta_f-dependent ones (slot 4).
-template <typename R>
+template <typename R, int NT>
 struct PulseAD {
   int32_t kind, pol, env, lon, lg_p, lg_al, lg_sgn, sg_order;
   R amp, bratio, lonE, lonB, env_a, env_b, px_re, px_im, py_re, py_im;
   R lg_c[kLgMaxP + 1];
-  Dual<R, kTan> inv_w0sq, inv_zR, lg_pref, beta_f;
+  Dual<R, NT> inv_w0sq, inv_zR, lg_pref, beta_f;
 };
 
-template <typename R>
-__device__ __forceinline__ PulseAD<R> make_ad(const Pulse<R> &P) {
-  PulseAD<R> A;
+template <int NT, typename R>
+__device__ __forceinline__ PulseAD<R, NT> make_ad(const Pulse<R> &P) {
+  using D = Dual<R, NT>;
+  PulseAD<R, NT> A;
   A.kind = P.kind; A.pol = P.pol; A.env = P.env; A.lon = P.lon;
   A.lg_p = P.lg_p; A.lg_al = P.lg_al; A.lg_sgn = P.lg_sgn; A.sg_order = P.sg_order;
   A.amp = P.amp_unit;  // unit a0: the physical field is a0 times this one
@@ -59,13 +64,16 @@ __device__ __forceinline__ PulseAD<R> make_ad(const Pulse<R> &P) {
   for (int i = 0; i <= kLgMaxP; ++i) A.lg_c[i] = P.lg_c[i];
   const R iw = P.inv_w0;
   // d(1/w0^2)/dw0 = -2/w0^3; z_R ~ w0^2; (sqrt2/w0)^|l| ~ w0^-|l|
-  A.inv_w0sq = Dual<R, kTan>::seed(P.inv_w0sq, 3, R(-2) * P.inv_w0sq * iw);
-  A.inv_zR = Dual<R, kTan>::seed(P.inv_zR, 3, R(-2) * P.inv_zR * iw);
-  A.lg_pref = Dual<R, kTan>::seed(P.lg_pref, 3, -R(P.lg_al) * P.lg_pref * iw);
-  // closed-form flying focus: zeta = ((z - z_f) - beta_f (t - t_f)) / z_R',
-  // 1/z_R' = 1 / ((1 - beta_f) z_R) -> d/dbeta_f = (1/z_R') / (1 - beta_f)
-  A.beta_f = Dual<R, kTan>::seed(P.beta_f, 4, P.kind == AP_FLYING_CF ? R(1) : R(0));
-  if (P.kind == AP_FLYING_CF) A.inv_zR.d[4] = P.inv_zR * P.inv_1mb;
+  A.inv_w0sq = D::seed(P.inv_w0sq, 3, R(-2) * P.inv_w0sq * iw);
+  A.inv_zR = D::seed(P.inv_zR, 3, R(-2) * P.inv_zR * iw);
+  A.lg_pref = D::seed(P.lg_pref, 3, -R(P.lg_al) * P.lg_pref * iw);
+  A.beta_f = D(P.beta_f);
+  if constexpr (NT == 5) {
+    // closed-form flying focus: zeta = ((z - z_f) - beta_f (t - t_f)) / z_R',
+    // 1/z_R' = 1 / ((1 - beta_f) z_R) -> d/dbeta_f = (1/z_R') / (1 - beta_f)
+    A.beta_f.d[4] = R(1);
+    A.inv_zR.d[4] = P.inv_zR * P.inv_1mb;
+  }
   return A;
 }
 
@@ -163,9 +171,9 @@ __device__ __forceinline__ void grid_value_grad(const GridView &g, GridCache<R> 
   }
 }
 
-template <int KIND, typename R>
-__device__ __forceinline__ void fields_ad(const PulseAD<R> &A, const Local<Dual<R, kTan>> &L,
-                                          Dual<R, kTan> E[3], Dual<R, kTan> B[3]) {
+template <int KIND, typename R, int NT>
+__device__ __forceinline__ void fields_ad(const PulseAD<R, NT> &A, const Local<Dual<R, NT>> &L,
+                                          Dual<R, NT> E[3], Dual<R, NT> B[3]) {
   if constexpr (KIND == AP_PLANE) fields_plane(A, L, E, B);
   else if constexpr (KIND == AP_GAUSS) fields_gauss(A, L, E, B);
   else if constexpr (KIND == AP_FLYING_CF) fields_gauss<true>(A, L, E, B);
@@ -176,13 +184,15 @@ __device__ __forceinline__ void fields_ad(const PulseAD<R> &A, const Local<Dual<
 // lx, lu of the state after the step (updated in place to the state before),
 // gradient accumulators g[0..3] = d/d(a0, w0, z_f, beta_f).
 template <int KIND, int PREC, bool GRID>
-__device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P, const PulseAD<Real<PREC>> &A,
+__device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P,
+                                             const PulseAD<Real<PREC>, tangents<KIND>()> &A,
                                              const AdjArgs &aa, const typename TimeBase<PREC>::Step &st,
                                              const Pos<PREC> &pos, const Real<PREC> u[3],
                                              Real<PREC> lx[3], Real<PREC> lu[3], Real<PREC> g[kNp],
                                              GridCache<Real<PREC>> &gc) {
   using R = Real<PREC>;
-  using DR = Dual<R, kTan>;
+  constexpr int NT = tangents<KIND>();
+  using DR = Dual<R, NT>;
   const R dt = (R)aa.base.dt;
   const R h = R(-0.5) * dt;
   const R a0 = P.a0;
@@ -200,7 +210,7 @@ __device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P, const P
   LD.phi_hi = DR(R(0));
   LD.phi_lo = DR(R(0));
   DR Ed[3], Bd[3];
-  fields_ad<KIND, R>(A, LD, Ed, Bd);
+  fields_ad<KIND, R, NT>(A, LD, Ed, Bd);
   R F[6], dFx[6][3], dFth[6][kNp];  // field, d/dx, d/d(a0, w0, z_f, beta_f)
   const DR *Fd[6] = {&Ed[0], &Ed[1], &Ed[2], &Bd[0], &Bd[1], &Bd[2]};
   for (int c = 0; c < 6; ++c) {
@@ -212,7 +222,8 @@ __device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P, const P
     dFth[c][0] = f.v;
     dFth[c][1] = a0 * f.d[3];
     dFth[c][2] = -a0 * f.d[2];
-    dFth[c][3] = a0 * f.d[4];
+    if constexpr (NT == 5) dFth[c][3] = a0 * f.d[4];
+    else dFth[c][3] = R(0);
   }
   if constexpr (GRID) {
     GridGrad<R> gg;
@@ -380,7 +391,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const Pulse<Real<PRE
     for (int k = 0; k < 3; ++k) lu[k] = valid ? (R)((double)u[k] / (gN * Ns)) : R(0);
     double Jv = valid ? gN / Ns : 0.0;
     double gacc[kNp] = {0.0, 0.0, 0.0, 0.0};
-    const PulseAD<R> A = make_ad(P);
+    const PulseAD<R, tangents<KIND>()> A = make_ad<tangents<KIND>()>(P);
     // ---- reverse sweep over segments
     for (int seg = aa.n_seg - 1; seg >= 0; --seg) {
       const long long s0 = (long long)seg * aa.K;

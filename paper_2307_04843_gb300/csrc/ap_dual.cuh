@@ -3,11 +3,11 @@
 //
 // Dual<R, N> carries a value and N tangents.  The field functions of
 // ap_device.cuh are templated on the scalar type, so instantiating them with
-// Dual<float, 5> seeded in (x, y, z - z_f, w0, beta_f) yields the fields and
-// their derivatives with respect to the particle position, the focal position
-// (d/dz_f = -d/d(z - z_f)), the waist and the focal velocity of the
-// closed-form flying focus in one pass, with exactly the arithmetic of the
-// forward push for the value part.
+// Dual<float, 4> seeded in (x, y, z - z_f, w0) -- Dual<float, 5> with beta_f
+// added for the closed-form flying focus -- yields the fields and their
+// derivatives with respect to the particle position, the focal position
+// (d/dz_f = -d/d(z - z_f)), the waist and the focal velocity in one pass,
+// with exactly the arithmetic of the forward push for the value part.
 #pragma once
 
 #include <type_traits>
@@ -191,6 +191,11 @@ __device__ __forceinline__ Dual<R, N> cos_r(const Dual<R, N> &a) {
 }
 
 // reduction by whole turns changes no derivative
+template <>
+__device__ __forceinline__ Dual<float, 4> reduce_angle<Dual<float, 4>>(Dual<float, 4> a) {
+  a.v = reduce_f(a.v);
+  return a;
+}
 template <>
 __device__ __forceinline__ Dual<float, 5> reduce_angle<Dual<float, 5>>(Dual<float, 5> a) {
   a.v = reduce_f(a.v);

@@ -118,3 +118,33 @@ def test_eval_fields_empty_and_bad_set():
         _lib.ap_eval_fields(h.h, 0, xyzt, EB, "fp64")
         with pytest.raises(_lib.APError):
             _lib.ap_eval_fields(h.h, 1, xyzt, EB, "fp64")
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind,extra", [("gauss", {}), ("lg", dict(lg_p=1, lg_l=2, pol="cp"))])
+def test_gpu_fields_maxwell_residual_slopes(kind, extra):
+    """The GPU FP64 fields (ap_eval_fields) give the same Maxwell-residual
+    slopes as the oracle: O(eps^2) with the longitudinal terms, div E = O(eps)
+    without, eps = 1/(k w0) over w0 in {4, 8, 16, 32} lambda."""
+    from paper_2307_04843_gb300 import _lib
+    from test_oracle_pins import _residuals
+    C = np.random.default_rng(5).uniform(-1, 1, (6, 4))
+    ws = np.array([4, 8, 16, 32])
+    res = {True: [], False: []}
+    for lon in (True, False):
+        for w in ws:
+            w0 = w * L
+            zR = 0.5 * w0 * w0
+            p = dict(kind=kind, pol="x", env="cw", a0=1.0, w0=w0, longitudinal=lon, z_focus=0.0)
+            p.update(extra)
+            pts = [(0.7 * w0 * c[0], 0.7 * w0 * c[1], zR * c[2], 3 * c[3]) for c in C]
+            with _lib.Handle(p) as h:
+                f = lambda x, y, z, t: h.eval_fields(x, y, z, t, precision="fp64").cpu().numpy()
+                res[lon].append(_residuals(p, pts, fields=f))
+    eps = 1.0 / (ws * L)
+    on, off = np.array(res[True]), np.array(res[False])
+    slope = lambda col: np.polyfit(np.log(eps), np.log(col), 1)[0]
+    assert 1.75 < slope(on[:, 0]) < 2.3 and 1.75 < slope(on[:, 1]) < 2.3
+    assert slope(on[:, 2]) > 1.75 and slope(on[:, 3]) > 1.75
+    assert 0.7 < slope(off[:, 2]) < 1.35
+    assert np.all(on[:, 2] < 0.1 * off[:, 2])
