@@ -47,7 +47,7 @@ template <typename R, int NT>
 struct PulseAD {
   int32_t kind, pol, env, lon, lg_p, lg_al, lg_sgn, sg_order;
   R amp, bratio, lonE, lonB, env_a, env_b, px_re, px_im, py_re, py_im;
-  R lg_c[kLgMaxP + 1];
+  R lg_r[6][kLgMaxP];
   Dual<R, NT> inv_w0sq, inv_zR, lg_pref, beta_f;
 };
 
@@ -61,7 +61,8 @@ __device__ __forceinline__ PulseAD<R, NT> make_ad(const Pulse<R> &P) {
   A.bratio = P.bratio; A.lonE = P.lonE; A.lonB = P.lonB;
   A.env_a = P.env_a; A.env_b = P.env_b;
   A.px_re = P.px_re; A.px_im = P.px_im; A.py_re = P.py_re; A.py_im = P.py_im;
-  for (int i = 0; i <= kLgMaxP; ++i) A.lg_c[i] = P.lg_c[i];
+  for (int r = 0; r < 6; ++r)
+    for (int k = 0; k < kLgMaxP; ++k) A.lg_r[r][k] = P.lg_r[r][k];
   const R iw = P.inv_w0;
   // d(1/w0^2)/dw0 = -2/w0^3; z_R ~ w0^2; (sqrt2/w0)^|l| ~ w0^-|l|
   A.inv_w0sq = D::seed(P.inv_w0sq, 3, R(-2) * P.inv_w0sq * iw);

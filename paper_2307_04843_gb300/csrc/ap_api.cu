@@ -197,7 +197,15 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
     P.lg_p = d.lg_p;
     P.lg_al = a;
     P.lg_sgn = d.lg_l < 0 ? -1 : 1;
-    laguerre_coeffs(d.lg_p, a, P.lg_c);
+    for (int k = 0; k < apt::kLgMaxP; ++k) {
+      const double k1 = (double)(k + 1);
+      for (int r = 0; r < 2; ++r) {
+        const double aa = (double)(a + r);
+        P.lg_r[3 * r + 0][k] = (2.0 * k + 1.0 + aa) / k1;
+        P.lg_r[3 * r + 1][k] = 1.0 / k1;
+        P.lg_r[3 * r + 2][k] = ((double)k + aa) / k1;
+      }
+    }
     P.lg_pref = std::pow(std::sqrt(2.0) / d.w0, (double)a);
     P.amp_unit = 1.0 / lg_peak(d.lg_p, a);
     P.amp = d.a0 * P.amp_unit;
@@ -262,7 +270,8 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
   F.env_a = (float)P.env_a; F.env_b = (float)P.env_b;
   F.px_re = (float)P.px_re; F.px_im = (float)P.px_im;
   F.py_re = (float)P.py_re; F.py_im = (float)P.py_im;
-  for (int i = 0; i <= apt::kLgMaxP; ++i) F.lg_c[i] = (float)P.lg_c[i];
+  for (int r = 0; r < 6; ++r)
+    for (int k = 0; k < apt::kLgMaxP; ++k) F.lg_r[r][k] = (float)P.lg_r[r][k];
   F.lg_pref = (float)P.lg_pref;
   F.beta_f = (float)P.beta_f;
   F.adv_xy = (float)P.adv_xy;

@@ -486,11 +486,23 @@ __device__ __forceinline__ void fields_lg(const PT &P, const Local<R> &L, R E[3]
   Cx<R> q{inv, zeta * inv};
   R a = (L.x * L.x + L.y * L.y) * P.inv_w0sq;
   R s = R(2) * a * q.re;
-  // Laguerre polynomial and derivative by Horner
-  R Lp = P.lg_c[P.lg_p], dL = R(0);
-  for (int i = P.lg_p - 1; i >= 0; --i) {
-    dL = fma(dL, s, Lp);
-    Lp = fma(Lp, s, P.lg_c[i]);
+  // L_p^{|l|}(s) and dL/ds = -L_{p-1}^{|l|+1}(s) by the three-term recurrence,
+  // which stays accurate where the monomial sum cancels (large s, large p)
+  R Lp = R(1), Lm = R(0);
+  for (int k = 0; k < P.lg_p; ++k) {
+    R Ln = fma(fma(-P.lg_r[1][k], s, P.lg_r[0][k]), Lp, -P.lg_r[2][k] * Lm);
+    Lm = Lp;
+    Lp = Ln;
+  }
+  R dL = R(0);
+  if (P.lon && P.lg_p > 0) {
+    R Dp = R(1), Dm = R(0);
+    for (int k = 0; k + 1 < P.lg_p; ++k) {
+      R Dn = fma(fma(-P.lg_r[4][k], s, P.lg_r[3][k]), Dp, -P.lg_r[5][k] * Dm);
+      Dm = Dp;
+      Dp = Dn;
+    }
+    dL = -Dp;
   }
   // (x + i sgn y)^{|l|} and its (|l| - 1)th power
   Cx<R> xi{L.x, P.lg_sgn >= 0 ? L.y : -L.y};

@@ -42,7 +42,11 @@ struct Pulse {
   R inv_zR;         // 1 / z_R
   R env_a, env_b;   // envelope constants (see ap_device.cuh)
   R px_re, px_im, py_re, py_im;  // polarisation vector p
-  R lg_c[kLgMaxP + 1];           // L_p^{|l|}(s) = sum_i lg_c[i] s^i
+  // Laguerre three-term recurrence (k+1) L_{k+1} = (2k+1+a-s) L_k - (k+a) L_{k-1}
+  // as L_{k+1} = (lg_r[0][k] - lg_r[1][k] s) L_k - lg_r[2][k] L_{k-1}, for
+  // a = |l| (rows 0-2) and a = |l| + 1 (rows 3-5, the derivative
+  // dL_p^a/ds = -L_{p-1}^{a+1})
+  R lg_r[6][kLgMaxP];
   R lg_pref;                     // (sqrt(2) / w0)^{|l|}
   R a0, inv_w0, amp_unit;        // a0, 1/w0 and amp / a0 (adjoint: d/da0, d/dw0)
   R beta_f, inv_1mb;             // closed-form flying focus: v_f / c and 1 / (1 - beta_f)

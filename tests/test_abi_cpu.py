@@ -56,6 +56,9 @@ def _init_rc(L, d, n=1):
     dict(kind="lg", w0=1.0, lg_l=-9),
     dict(kind="flying", w0=1.0, n_comp=1, beta_f=0.99, ff_length=10.0),
     dict(kind="flying", w0=1.0, n_comp=500, beta_f=0.99, ff_length=10.0),
+    dict(kind="flying", w0=1.0, n_comp=129, beta_f=0.99, ff_length=10.0),  # AP_MAX_COMP + 1
+    dict(kind="flying_cf", w0=1.0, beta_f=1.0),                  # focus at the speed of light
+    dict(kind="flying_cf", w0=1.0, beta_f=float("inf")),
     dict(kind="flying", w0=1.0, n_comp=8, beta_f=0.0, ff_length=10.0),
     dict(kind="plane", yee=True, yee_dx=0.1, yee_dt=0.2),       # Courant number > 1
     dict(kind="plane", a0=float("nan")),

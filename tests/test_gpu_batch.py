@@ -134,3 +134,32 @@ def test_one_d_radial_sweep_matches_oracle(precision):
     # the pulse drives the lines, harder near the axis
     ux_max = [np.max(np.abs(ref["ux"][off[s]:off[s + 1]])) for s in (0, len(sets) - 1)]
     assert ux_max[0] > 10.0 and ux_max[0] > 2.0 * ux_max[1], ux_max
+
+
+@pytest.mark.gpu
+def test_maximum_number_of_sets():
+    """AP_MAX_SETS = 4096 pulse sets in one batched launch, counts 0..3
+    (empty sets included): every particle equals the single-set push of its
+    own set, and per-set sums match the returned states."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    cfg = workloads.config(5)
+    base, _ = workloads.batch_sets(cfg)
+    S = _lib.AP_MAX_SETS
+    rng = np.random.default_rng(41)
+    sets = [dict(base[s % len(base)], a0=float(rng.uniform(2, 20))) for s in range(S)]
+    counts = rng.integers(0, 4, S)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    parts = workloads.particles_uniform(cfg["box"], int(off[-1]), 77)
+    n_steps = 60
+    out, sums, st = _run_batched(sets, off, parts, cfg["t0"], cfg["dt"], n_steps, "fp32")
+    assert st == 0
+    own = oracle.set_gamma_sums(off, out["ux"], out["uy"], out["uz"])
+    np.testing.assert_allclose(sums, own, rtol=1e-12)
+    assert np.all(sums[counts == 0] == 0.0)
+    from support import gpu_push
+    for s in rng.choice(np.flatnonzero(counts > 0), 12, replace=False):
+        sub = {k: v[off[s]:off[s + 1]] for k, v in parts.items()}
+        single, _, _ = gpu_push(sets[s], sub, cfg["t0"], cfg["dt"], n_steps, "fp32")
+        for k in single:
+            np.testing.assert_array_equal(out[k][off[s]:off[s + 1]], single[k])

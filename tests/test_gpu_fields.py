@@ -148,3 +148,28 @@ def test_gpu_fields_maxwell_residual_slopes(kind, extra):
     assert slope(on[:, 2]) > 1.75 and slope(on[:, 3]) > 1.75
     assert 0.7 < slope(off[:, 2]) < 1.35
     assert np.all(on[:, 2] < 0.1 * off[:, 2])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_maximum_table_sizes(precision):
+    """The largest descriptions the ABI accepts: a flying focus of
+    AP_MAX_COMP = 128 components and LG_pl with p = |l| = 8 (the Laguerre
+    table limit) out to 3.75 w0, where the monomial form of L_8^8 cancels
+    terms 1e4 times its value (the kernels use the three-term recurrence).
+    Bounds: FP32 128 summed float terms 8e-5 a0, LG 4e-6 a0; FP64 LG 1e-9 a0,
+    the accuracy of the oracle's finite-difference longitudinal terms for a
+    mode with this much transverse structure."""
+    from paper_2307_04843_gb300 import _lib
+    ff = dict(kind="flying", pol="x", a0=1.0, w0=2 * L, n_comp=_lib.AP_MAX_COMP, bw_frac=0.05, beta_f=0.95,
+              ff_length=60 * L, longitudinal=True)
+    lg = dict(kind="lg", pol="cp", env="cw", a0=1.0, w0=4 * L, lg_p=8, lg_l=-8, longitudinal=True)
+    for pulse, tol in ((ff, 8e-5 if precision == "fp32" else 1e-10), (lg, 4e-6 if precision == "fp32" else 1e-9)):
+        x, y, z, t = _points(pulse, 193, seed=17)
+        if pulse["kind"] == "lg":  # the outer rings of LG_88 lie near 4 w0
+            x, y = 2.5 * x, 2.5 * y
+        ref = oracle.fields(pulse, x, y, z, t)
+        with _lib.Handle(pulse) as h:
+            got = h.eval_fields(x, y, z, t, precision=precision).cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= tol * pulse["a0"], (pulse["kind"], np.max(np.abs(got - ref)))
+        assert np.max(np.abs(ref)) > 0.05
