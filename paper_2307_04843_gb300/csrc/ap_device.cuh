@@ -787,7 +787,9 @@ __device__ __forceinline__ void grid_fetch(const GridView &g, GridSlots &gc, flo
   const float fy = grid_unit<float>(y, g.inv_d[1], g.off[1], g.ny);
   const float fz = grid_unit<float>(z, g.inv_d[2], g.off[2], g.nz);
   float wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
-  const bool need = !(wx >= 0.0f && wx <= 1.0f && wy >= 0.0f && wy <= 1.0f && wz >= 0.0f && wz <= 1.0f);
+  // inside the cached cell (faces included) iff max |w - 1/2| <= 1/2
+  const float dev = fmaxf(fabsf(wx - 0.5f), fmaxf(fabsf(wy - 0.5f), fabsf(wz - 0.5f)));
+  const bool need = !(dev <= 0.5f);
   if (__any_sync(0xffffffffu, need) && need) {
     // lower cell corner without the conversion pipe (see the register cache)
     auto corner = [](float f, int n, int &i) {
@@ -875,7 +877,9 @@ __device__ __forceinline__ void grid_fetch(const GridView &g, CellSlots &gc, flo
   const float fy = grid_unit<float>(y, g.inv_d[1], g.off[1], g.ny);
   const float fz = grid_unit<float>(z, g.inv_d[2], g.off[2], g.nz);
   float wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
-  const bool need = !(wx >= 0.0f && wx <= 1.0f && wy >= 0.0f && wy <= 1.0f && wz >= 0.0f && wz <= 1.0f);
+  // inside the cached cell (faces included) iff max |w - 1/2| <= 1/2
+  const float dev = fmaxf(fabsf(wx - 0.5f), fmaxf(fabsf(wy - 0.5f), fabsf(wz - 0.5f)));
+  const bool need = !(dev <= 0.5f);
   if (__any_sync(0xffffffffu, need) && need) {
     auto corner = [](float f, int n, int &i) {
       float c = __fsub_rn(__fadd_rn(__fsub_rn(f, 0.5f), kRoundMagic), kRoundMagic);
@@ -937,7 +941,9 @@ __device__ __forceinline__ void grid_fetch(const GridView &g, CellRegs &gc, floa
   const float fy = grid_unit<float>(y, g.inv_d[1], g.off[1], g.ny);
   const float fz = grid_unit<float>(z, g.inv_d[2], g.off[2], g.nz);
   float wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
-  const bool need = !(wx >= 0.0f && wx <= 1.0f && wy >= 0.0f && wy <= 1.0f && wz >= 0.0f && wz <= 1.0f);
+  // inside the cached cell (faces included) iff max |w - 1/2| <= 1/2
+  const float dev = fmaxf(fabsf(wx - 0.5f), fmaxf(fabsf(wy - 0.5f), fabsf(wz - 0.5f)));
+  const bool need = !(dev <= 0.5f);
   if (__any_sync(0xffffffffu, need) && need) {
     auto corner = [](float f, int n, int &i) {
       float c = __fsub_rn(__fadd_rn(__fsub_rn(f, 0.5f), kRoundMagic), kRoundMagic);

@@ -104,30 +104,37 @@ __device__ __forceinline__ double push_one(const Pulse<Real<PREC>> &P, const Pus
   double *lf = a.diag.lf;
   StepFF *wsteps = s_steps + (threadIdx.x >> 5) * kStepChunk;
   const int lane = threadIdx.x & 31;
-  for (long long s0 = 0; s0 < a.n_steps; s0 += kStepChunk) {
-    const int cnt = (int)(a.n_steps - s0 < kStepChunk ? a.n_steps - s0 : kStepChunk);
-    if constexpr (PREC == AP_FP32_PHASEFF) {
-      __syncwarp();  // no lane still reads the previous chunk
-      if (lane < cnt) wsteps[lane] = tb.at(s0 + lane);
-      __syncwarp();
-    }
-    for (int k = 0; k < cnt; ++k) {
-      typename TimeBase<PREC>::Step st;
-      if constexpr (PREC == AP_FP32_PHASEFF) st = wsteps[k];
-      else st = tb.at(s0 + k);
-      Local<R> L = local_coords<PREC>(P, st, pos);
-      if constexpr (GRID) grid_fetch(a.grid, gc, L.x, L.y, pos.zr());
-      R E[3], B[3];
-      analytic_fields<KIND, PREC>(P, L, E, B);
-      if constexpr (GRID) grid_eval(gc, E, B);
-      R ig = boris(u, E, B, dtR);
-      pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtxy, dtR);
-      if (lf) {
-        R dev = valid ? fabs((R(1) / ig - u[2]) - h0) : R(0);
-        warp_max_to(lf + s0 + k, dev, 0xffffffffu);
+  // the step loop, compiled twice: with the per-step light-front diagnostic
+  // and without it (its test would otherwise cost every step an issue slot)
+  auto steps = [&](auto with_lf) {
+    constexpr bool LF = decltype(with_lf)::value;
+    for (long long s0 = 0; s0 < a.n_steps; s0 += kStepChunk) {
+      const int cnt = (int)(a.n_steps - s0 < kStepChunk ? a.n_steps - s0 : kStepChunk);
+      if constexpr (PREC == AP_FP32_PHASEFF) {
+        __syncwarp();  // no lane still reads the previous chunk
+        if (lane < cnt) wsteps[lane] = tb.at(s0 + lane);
+        __syncwarp();
+      }
+      for (int k = 0; k < cnt; ++k) {
+        typename TimeBase<PREC>::Step st;
+        if constexpr (PREC == AP_FP32_PHASEFF) st = wsteps[k];
+        else st = tb.at(s0 + k);
+        Local<R> L = local_coords<PREC>(P, st, pos);
+        if constexpr (GRID) grid_fetch(a.grid, gc, L.x, L.y, pos.zr());
+        R E[3], B[3];
+        analytic_fields<KIND, PREC>(P, L, E, B);
+        if constexpr (GRID) grid_eval(gc, E, B);
+        R ig = boris(u, E, B, dtR);
+        pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtxy, dtR);
+        if constexpr (LF) {
+          R dev = valid ? fabs((R(1) / ig - u[2]) - h0) : R(0);
+          warp_max_to(lf + s0 + k, dev, 0xffffffffu);
+        }
       }
     }
-  }
+  };
+  if (lf) steps(std::true_type{});
+  else steps(std::false_type{});
   if (!valid) return 0.0;
   pos.store(a.x + i, a.y + i, a.z + i);
   R *ux = static_cast<R *>(a.ux);
