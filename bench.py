@@ -62,7 +62,7 @@ ALGO = {
 # None when the kernel changed after the capture.
 TRAFFIC_PER_PARTICLE_STEP = {
     "nodes": 5.336,  # (34.084e9 read + 0.064e9 written) / 6.4e9
-    "cells": 6.061,  # (38.729e9 read + 0.064e9 written) / 6.4e9, cell in registers
+    "cells": 6.058,  # (38.707e9 read + 0.064e9 written) / 6.4e9, cell in registers
     "arrays": None,
 }
 
