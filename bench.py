@@ -316,6 +316,38 @@ NODE_OPS_PER_EVAL = 90  # FP32 operations of one Gaussian field evaluation with
 YEE_LINES, YEE_NZ, YEE_STEPS = 152, 8192, 2000
 
 
+def closed_form_rate(wl, stream, sum_rate):
+    """The same electrons and steps under the closed-form flying focus
+    (Sec. 3.3: one Gaussian whose focus moves at v_f) instead of the
+    64-component sum: focus at the middle of the focal range at the time it
+    is there, same a0, w0, v_f and longitudinal terms, no envelope."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    p = wl.pulses[0]
+    zm = p["z_focus"] + 0.5 * p["ff_length"]
+    tm = p["t_focus"] + 0.5 * p["ff_length"] / p["beta_f"]
+    cf = dict(kind="flying_cf", pol=p.get("pol", "x"), env="cw", a0=p["a0"], w0=p["w0"], beta_f=p["beta_f"],
+              z_focus=zm, t_focus=tm, longitudinal=p.get("longitudinal", False))
+    with _lib.Handle(cf) as h:
+        d = {k: v.clone() for k, v in wl.init.items()}
+        h.push(d, wl.t0, wl.dt, 50, precision=wl.precision)
+        for k in d:
+            d[k].copy_(wl.init[k])
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.push(d, wl.t0, wl.dt, wl.n_steps, precision=wl.precision)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        st = h.status()
+    if st != 0:
+        raise RuntimeError("closed-form flying focus: device status %d" % st)
+    rate = wl.n * wl.n_steps / sec
+    return {"value": rate, "unit": UNIT, "sample": "the workload's %d electrons x %d steps" % (wl.n, wl.n_steps),
+            "vs_64_component_sum": rate / sum_rate}
+
+
 def grid_node_rates(wl, stream):
     """Rates of ap_eval_nodes (the workload's pulse onto a 256^3 Yee grid,
     six float arrays, float-float phase) and ap_yee1d_run (float lines)."""
@@ -478,6 +510,8 @@ def run_ours(args):
                               "sample": "%d particles x %d steps, one call" % (nv, wl.n_steps)}
         for prec in variants:
             variants[prec]["fp32_speedup"] = (units_rank / kern) / variants[prec]["value"]
+        if args.workload == 4:
+            variants["closed_form"] = closed_form_rate(wl, stream, units_rank / kern)
 
     # grid-node form: analytic E1/B1 on the staggered nodes of a 256^3 Yee
     # grid (six float arrays), and independent 1-D vacuum Yee lines

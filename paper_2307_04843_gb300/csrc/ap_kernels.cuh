@@ -176,9 +176,7 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
 // step fused.  Dynamic shared memory: step tables, grid slots (float grid
 // kernels), then the histogram (hist_off bytes in).
 template <int KIND, int PREC, int GRID>
-__global__ void __launch_bounds__(256, GRID == kGridCells ? 3 : GRID == kGridCellsReg ? 2 : 1)
-    push_kernel(const __grid_constant__ Pulse<Real<PREC>> P, const __grid_constant__ PushArgs a,
-                unsigned hist_off) {
+__device__ __forceinline__ void push_body(const Pulse<Real<PREC>> &P, const PushArgs &a, unsigned hist_off) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ double s_red[32];
   StepFF *s_steps = reinterpret_cast<StepFF *>(s_dyn);
@@ -209,6 +207,31 @@ __global__ void __launch_bounds__(256, GRID == kGridCells ? 3 : GRID == kGridCel
     for (int b = threadIdx.x; b < a.diag.bins; b += blockDim.x)
       if (s_hist[b]) atomicAdd(&a.diag.hist[b], s_hist[b]);
   }
+}
+
+// Two entries for the same body.  The per-cell coefficient variants name a
+// residency target (3 blocks of 256 with the cell in shared memory, 2 with
+// it in registers); the others keep the compiler's own register choice (an
+// explicit minimum of one block lets it spend registers freely, which cost
+// the flying-focus kernel 7 % through lost occupancy).
+template <int KIND, int PREC, int GRID>
+__global__ void __launch_bounds__(256)
+    push_kernel(const __grid_constant__ Pulse<Real<PREC>> P, const __grid_constant__ PushArgs a,
+                unsigned hist_off) {
+  push_body<KIND, PREC, GRID>(P, a, hist_off);
+}
+
+template <int KIND, int PREC, int GRID>
+__global__ void __launch_bounds__(256, GRID == kGridCells ? 3 : 2)
+    push_kernel_cells(const __grid_constant__ Pulse<Real<PREC>> P, const __grid_constant__ PushArgs a,
+                      unsigned hist_off) {
+  push_body<KIND, PREC, GRID>(P, a, hist_off);
+}
+
+template <int KIND, int PREC, int GRID>
+constexpr auto push_entry() {
+  if constexpr (GRID == kGridCells || GRID == kGridCellsReg) return push_kernel_cells<KIND, PREC, GRID>;
+  else return push_kernel<KIND, PREC, GRID>;
 }
 
 // Batched persistent launch (row a12): blocks pop fixed-size tiles of
@@ -417,7 +440,7 @@ inline int set_smem(K kern, size_t smem) {
 
 template <int KIND, int PREC, int GRID>
 int launch_push_t(const Pulse<Real<PREC>> &P, const PushArgs &a, void *stream) {
-  auto kern = push_kernel<KIND, PREC, GRID>;
+  auto kern = push_entry<KIND, PREC, GRID>();
   const int block = a.shape.block;
   const size_t head = push_smem_head<PREC, GRID>(block);
   const size_t smem = head + (a.diag.hist ? (size_t)a.diag.bins * sizeof(uint32_t) : 0);
