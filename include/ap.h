@@ -5,9 +5,9 @@
  * electromagnetics" (arXiv:2307.04843).  The fields are split into an
  * analytic vacuum part E1/B1 and a grid part E2/B2 (Sec. 2, Eqs. E_1, E_2);
  * here each macroparticle evaluates E1/B1 in closed form at its own position
- * and time, adds the trilinearly gathered grid field (Sec. 2.1, Fig. 1: "the
- * total fields are then interpolated to the particle position"), and takes a
- * relativistic Boris step.
+ * and time, adds the trilinearly gathered grid field (Sec. 2.1, Fig. 1: the
+ * particle is pushed with the sum of the analytic and grid fields at its
+ * position), and takes a relativistic Boris step.
  *
  * Units are normalised: c = omega0 = k0 = 1 (lambda = 2 pi), fields in
  * m c omega0 / e so that the field amplitude is a0 (Sec. 2.2, definition of

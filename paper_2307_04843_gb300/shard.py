@@ -1,7 +1,7 @@
 """Host-side sharding of the push over ranks (one process per GPU).
 
-The analytic field needs no communication (Sec. 2.3 of the paper: evaluating
-the pulse "does not require communication between processes"), so the
+The analytic field needs no communication (Sec. 2.3: each process evaluates
+the pulse on its own, with no data from other processes), so the
 particles -- or whole pulse sets of a batched run -- are split across ranks
 and every rank pushes its shard independently.  The only exchange is one
 final reduction of the diagnostics: histogram counts and per-set sums of
