@@ -133,8 +133,8 @@ void or_set_gamma_sums(int n_sets, const int64_t *off, const double *ux, const d
                        const double *uz, double *sums);
 
 /* Yee-staggered samples of the analytic E1, B1 on a grid (Sec. 2.1 and
- * Fig. 1: the analytic fields are set on the grid nodes every step and added
- * to the internally advanced ones).  Node (i, j, k) sits at
+ * Fig. 1: the analytic fields are set on the grid nodes every step and summed
+ * with the fields the grid solver advances).  Node (i, j, k) sits at
  * lo + (i dx, j dy, k dz); inside the cell the six components sit at the
  * usual Yee offsets, in cells:
  *   Ex (1/2, 0, 0), Ey (0, 1/2, 0), Ez (0, 0, 1/2),
