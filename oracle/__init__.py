@@ -11,7 +11,10 @@ Functions: ``fields``, ``push``, ``boris``, ``grid_sample``, ``gamma_hist``,
 ``set_gamma_sums``, ``profile``, ``envelope``, ``state``,
 ``grad_fd`` (FP64 central finite differences with Richardson extrapolation of
 the per-set mean final gamma), ``yee_nodes`` (E1, B1 at Yee-staggered grid
-nodes) and ``yee1d`` (the 1-D vacuum Yee scheme of Sec. 2.1).
+nodes), ``yee1d`` (the 1-D vacuum Yee scheme of Sec. 2.1), and for Sec. 4
+``current`` (the analytic current J1), ``envelope_logd``, ``plasma1d`` (the
+line with a linear cold-plasma current) and ``apt1d`` (the same line in the
+split form with E1 and J1 analytic).
 """
 from .core import (  # noqa: F401
     build,
@@ -30,4 +33,8 @@ from .core import (  # noqa: F401
     grad_fd,
     yee_nodes,
     yee1d,
+    current,
+    envelope_logd,
+    plasma1d,
+    apt1d,
 )

@@ -30,7 +30,7 @@ class _Pulse(ctypes.Structure):
         ("env_len", ctypes.c_double), ("phase0", ctypes.c_double),
         ("beta_f", ctypes.c_double), ("bw_frac", ctypes.c_double),
         ("ff_length", ctypes.c_double), ("yee_dx", ctypes.c_double),
-        ("yee_dt", ctypes.c_double),
+        ("yee_dt", ctypes.c_double), ("omega_p", ctypes.c_double),
     ]
 
 
@@ -45,6 +45,7 @@ class _State(ctypes.Structure):
         ("n", ctypes.c_int),
         ("fw", _DA), ("fk", _DA), ("fz", _DA), ("ft", _DA), ("fphi", _DA), ("fzR", _DA),
         ("z_mid", ctypes.c_double), ("t_mid", ctypes.c_double),
+        ("zeta", ctypes.c_double), ("jamp", ctypes.c_double), ("fdc", ctypes.c_double),
     ]
 
 
@@ -97,6 +98,16 @@ def lib():
         L.or_yee_nodes.restype = None
         L.or_yee1d.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64]
         L.or_yee1d.restype = None
+        L.or_envelope_logd.argtypes = [ctypes.POINTER(_State), ctypes.c_double, dp, dp]
+        L.or_envelope_logd.restype = ctypes.c_int
+        L.or_current.argtypes = [ctypes.POINTER(_State)] + [ctypes.c_double] * 4 + [dp]
+        L.or_current.restype = None
+        L.or_plasma1d.argtypes = [ctypes.c_int64, dp, dp, dp, dp, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_int64]
+        L.or_plasma1d.restype = None
+        L.or_apt1d.argtypes = [ctypes.POINTER(_State), ctypes.c_int64, dp, dp, dp, dp] + \
+            [ctypes.c_double] * 4 + [ctypes.c_int64]
+        L.or_apt1d.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -114,7 +125,7 @@ def _pulse_struct(d):
     p.yee = 1 if d.get("yee", False) else 0
     p.one_d = 1 if d.get("one_d", False) else 0
     for name in ("a0", "omega", "w0", "z_focus", "t_focus", "env_len", "phase0", "beta_f",
-                 "bw_frac", "ff_length", "yee_dx", "yee_dt"):
+                 "bw_frac", "ff_length", "yee_dx", "yee_dt", "omega_p"):
         default = 1.0 if name == "omega" else 0.0
         setattr(p, name, float(d.get(name, default)))
     return p
@@ -133,7 +144,8 @@ def state(pulse):
     """Derived constants as a dict (k, vphi, vg, bratio, zR, amp and, for the
     flying focus, the component table)."""
     st = prepare(pulse)
-    out = {k: getattr(st, k) for k in ("k", "vphi", "vg", "bratio", "zR", "amp", "n", "z_mid", "t_mid")}
+    out = {k: getattr(st, k) for k in ("k", "vphi", "vg", "bratio", "zR", "amp", "n", "z_mid", "t_mid",
+                                       "zeta", "jamp", "fdc")}
     n = st.n
     for k in ("fw", "fk", "fz", "ft", "fphi", "fzR"):
         out[k] = np.array(getattr(st, k)[:n])
@@ -157,6 +169,34 @@ def fields(pulse, x, y, z, t):
         L.or_fields(ctypes.byref(st), x[i], y[i], z[i], t[i], _dp(buf))
         out[:, i] = buf
     return out.reshape((6,) + shape)
+
+
+def current(pulse, x, y, z, t):
+    """Analytic current J1 (Eq. j1) at points; returns [3, n] (Jx, Jy, Jz)."""
+    st = prepare(pulse)
+    x, y, z, t = np.broadcast_arrays(*[np.asarray(v, dtype=np.float64) for v in (x, y, z, t)])
+    shape = x.shape
+    x, y, z, t = [np.ascontiguousarray(v).ravel() for v in (x, y, z, t)]
+    out = np.empty((3, x.size))
+    buf = np.empty(3)
+    L = lib()
+    for i in range(x.size):
+        L.or_current(ctypes.byref(st), x[i], y[i], z[i], t[i], _dp(buf))
+        out[:, i] = buf
+    return out.reshape((3,) + shape)
+
+
+def envelope_logd(pulse, eta):
+    """(Gamma'/Gamma, Gamma''/Gamma) at each eta."""
+    st = prepare(pulse)
+    eta = np.atleast_1d(np.asarray(eta, dtype=np.float64))
+    l1, l2 = np.empty(eta.size), np.empty(eta.size)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    for i, e in enumerate(eta):
+        if lib().or_envelope_logd(ctypes.byref(st), float(e), ctypes.byref(a), ctypes.byref(b)) != 0:
+            raise ValueError("oracle: envelope without logarithmic derivatives")
+        l1[i], l2[i] = a.value, b.value
+    return l1, l2
 
 
 def profile(pulse, x, y, z, j=0, t=0.0):
@@ -300,3 +340,34 @@ def yee1d(E, B, dz, dt, n_steps):
         raise ValueError("E and B must be 1-D arrays of one length")
     lib().or_yee1d(E.size, _dp(E), _dp(B), float(dz), float(dt), int(n_steps))
     return E, B
+
+
+def _line_arrays(E, B, J, wp2):
+    E = np.array(E, dtype=np.float64)
+    B = np.array(B, dtype=np.float64)
+    J = np.array(J, dtype=np.float64)
+    wp2 = np.ascontiguousarray(np.broadcast_to(np.asarray(wp2, dtype=np.float64), E.shape))
+    if E.ndim != 1 or B.shape != E.shape or J.shape != E.shape:
+        raise ValueError("E, B and J must be 1-D arrays of one length")
+    return E, B, J, wp2
+
+
+def plasma1d(E, B, J, wp2, dz, dt, n_steps):
+    """n_steps of the 1-D Yee line with a linear cold-plasma current (E_x at
+    z_k, B_y at z_{k+1/2}, J_x at z_k; wp2 = omega_p^2 per node or scalar);
+    returns the new (E, B, J)."""
+    E, B, J, wp2 = _line_arrays(E, B, J, wp2)
+    lib().or_plasma1d(E.size, _dp(E), _dp(B), _dp(J), _dp(wp2), float(dz), float(dt), int(n_steps))
+    return E, B, J
+
+
+def apt1d(pulse, E2, B2, J, wp2, z0, dz, t0, dt, n_steps):
+    """n_steps of the line in the split form of Sec. 4 with the pulse's
+    analytic E1 and current J1; returns the new (E2, B2, J)."""
+    st = prepare(pulse)
+    E, B, J, wp2 = _line_arrays(E2, B2, J, wp2)
+    rc = lib().or_apt1d(ctypes.byref(st), E.size, _dp(E), _dp(B), _dp(J), _dp(wp2), float(z0),
+                        float(dz), float(t0), float(dt), int(n_steps))
+    if rc != 0:
+        raise ValueError("oracle: the line carries E_x: the pulse must be polarised along x")
+    return E, B, J

@@ -79,6 +79,47 @@ static void polarisation(int pol, double complex *px, double complex *py) {
 
 /* ------------------------------------------------------------------ setup */
 
+/* Plane wave in a linear cold plasma (Sec. 4).  With the second-order Yee
+ * scheme and the current advanced by the leapfrog dJ/dt = omega_p^2 E at the
+ * half steps, the current lags the continuum one by the factor
+ * zeta = (omega dt/2) / sin(omega dt/2); k then follows from Eq. dispersion_j,
+ *   sin^2(omega dt/2) - (omega_p^2/omega^2)(omega dt/2) sin(omega dt/2) zeta
+ *     = (c dt/dx)^2 sin^2(k dx/2),
+ * and B0/E0 from Eq. e_amp_j.  With this zeta the plasma term equals
+ * (omega_p dt/2)^2 whatever omega is, so v_g = d omega/dk is the ratio of the
+ * two sides' derivatives,
+ *   v_g = (c dt/dx)^2 sin(k dx/2) cos(k dx/2) dx / (sin(omega dt/2) cos(omega dt/2) dt).
+ * Without the Yee flag: the continuum, omega^2 = omega_p^2 + c^2 k^2,
+ * zeta = 1, v_g = c^2 k / omega, B0/E0 = c k / omega. */
+static int or_prepare_plasma(const or_pulse *p, or_state *s) {
+  const double w = p->omega, wp = p->omega_p;
+  if (!(wp > 0.0) || p->kind != OR_PLANE || p->env == OR_ENV_SIN2) return -1;
+  if (p->yee) {
+    const double h = 0.5 * w * p->yee_dt;
+    if (!(h < 0.5 * OR_PI)) return -1;
+    const double sw = sin(h), cw = cos(h);
+    const double r = p->yee_dt / p->yee_dx;
+    s->zeta = h / sw;
+    const double lhs = sw * sw - (wp * wp) / (w * w) * h * sw * s->zeta;
+    const double sk2 = lhs / (r * r);
+    if (!(sk2 > 0.0 && sk2 < 1.0)) return -1;
+    const double sk = sqrt(sk2), ck = sqrt(1.0 - sk2);
+    s->k = (2.0 / p->yee_dx) * asin(sk);
+    s->vg = r * r * sk * ck * p->yee_dx / (sw * cw * p->yee_dt);
+    s->bratio = cw * sqrt(1.0 - (wp * wp) / (w * w) * s->zeta * h / sw);
+  } else {
+    if (!(wp < w)) return -1;
+    s->zeta = 1.0;
+    s->k = sqrt(w * w - wp * wp);
+    s->vg = s->k / w;
+    s->bratio = s->k / w;
+  }
+  s->vphi = w / s->k;
+  s->jamp = wp * wp * s->zeta / w;
+  s->fdc = 1.0 - s->vphi / s->vg;
+  return 0;
+}
+
 int or_prepare(const or_pulse *p, or_state *s) {
   s->p = *p;
   if (!(p->omega > 0.0)) return -1;
@@ -88,6 +129,9 @@ int or_prepare(const or_pulse *p, or_state *s) {
   s->vphi = 1.0;
   s->vg = 1.0;
   s->bratio = 1.0;
+  s->zeta = 1.0;
+  s->jamp = 0.0;
+  s->fdc = 0.0;
   if (p->yee) {
     if (!(p->yee_dx > 0.0) || !(p->yee_dt > 0.0) || p->kind == OR_FLYING) return -1;
     double cr = p->yee_dt / p->yee_dx;
@@ -97,6 +141,7 @@ int or_prepare(const or_pulse *p, or_state *s) {
     s->bratio = 1.0 - (p->omega * p->yee_dt) * (p->omega * p->yee_dt) / 8.0;
   }
   s->k = p->omega / s->vphi;
+  if (p->omega_p != 0.0 && or_prepare_plasma(p, s) != 0) return -1;
   s->zR = 0.5 * s->k * p->w0 * p->w0;
   s->amp = p->a0;
   s->n = 0;
@@ -181,6 +226,35 @@ double or_envelope(const or_state *s, double eta) {
   }
 }
 
+/* Logarithmic derivatives of the envelope: ln Gamma is -2 ln2 eta^2 / T^2
+ * (Gaussian) or -(eta/tau)^(2g) (super-Gaussian), so
+ *   L1 = (ln Gamma)',  L2 = Gamma''/Gamma = L1^2 + (ln Gamma)''. */
+int or_envelope_logd(const or_state *s, double eta, double *L1, double *L2) {
+  const or_pulse *p = &s->p;
+  switch (p->env) {
+    case OR_ENV_GAUSS: {
+      double a = 2.0 * log(2.0) / (p->env_len * p->env_len);
+      *L1 = -2.0 * a * eta;
+      *L2 = (*L1) * (*L1) - 2.0 * a;
+      return 0;
+    }
+    case OR_ENV_SGAUSS: {
+      double g = (double)p->sg_order, tau = p->env_len, u = eta / tau;
+      *L1 = -2.0 * g * pow(u, 2.0 * g - 1.0) / tau;
+      *L2 = (*L1) * (*L1) - 2.0 * g * (2.0 * g - 1.0) * pow(u, 2.0 * g - 2.0) / (tau * tau);
+      return 0;
+    }
+    case OR_ENV_SIN2:
+      *L1 = 0.0;
+      *L2 = 0.0;
+      return -1;
+    default:
+      *L1 = 0.0;
+      *L2 = 0.0;
+      return 0;
+  }
+}
+
 /* ----------------------------------------------------------------- beams */
 
 /* Paraxial beam in the +z, e^{i(omega t - k z)} convention: Eq. paraxial with
@@ -245,6 +319,7 @@ void or_fields(const or_state *s, double x, double y, double z, double t, double
   double complex px, py;
   polarisation(p->pol, &px, &py);
   double complex U = 0.0, DX = 0.0, DY = 0.0; /* transverse phasor, longitudinal phasors */
+  double complex UB = 0.0;                     /* phasor of the transverse B */
   const int lon = p->longitudinal && p->kind != OR_PLANE;
   if (p->kind == OR_FLYING) {
     /* Linear superposition of the spectral components (Sec. 3.3); no
@@ -261,12 +336,26 @@ void or_fields(const or_state *s, double x, double y, double z, double t, double
         DY += (-I / s->fk[j]) * gy * ph;
       }
     }
+    UB = U;
   } else {
     double eta = (t - p->t_focus) - (z - p->z_focus) / s->vg;
     double G = or_envelope(s, eta);
     double psi = p->omega * (t - p->t_focus) - s->k * (z - p->z_focus) + p->phase0;
     double complex ph = G * cexp(I * psi);
     U = profile_c(s, 0, x, y, z, t) * ph;
+    UB = U;
+    if (p->omega_p != 0.0) {
+      /* Eq. b_corr_t with Phi = 0: the lowest finite-duration terms, weighted
+       * by 1 - v_phi/v_g, change B's amplitude by the factor
+       *   1 - c L2/omega^2 + (c L1/omega)^2 / 2
+       * and shift its phase by c L1/omega (c = 1 - v_phi/v_g, L1 and L2 the
+       * logarithmic derivatives of Gamma). */
+      double L1, L2;
+      or_envelope_logd(s, eta, &L1, &L2);
+      double th = s->fdc * L1 / p->omega;
+      double A = 1.0 - s->fdc * L2 / (p->omega * p->omega) + 0.5 * th * th;
+      UB = profile_c(s, 0, x, y, z, t) * A * G * cexp(I * (psi + th));
+    }
     if (lon) {
       double complex gx, gy;
       profile_grad(s, 0, x, y, z, t, &gx, &gy);
@@ -275,11 +364,11 @@ void or_fields(const or_state *s, double x, double y, double z, double t, double
     }
   }
   /* Transverse fields: E_perp = Re[U p], B_perp = (B0/E0) z x E_perp
-   * (Eqs. plane_func, plane_b). */
+   * (Eqs. plane_func, plane_b; Eq. b_corr_t in a plasma). */
   EB[0] = creal(px * U);
   EB[1] = creal(py * U);
-  EB[3] = s->bratio * creal(-py * U);
-  EB[4] = s->bratio * creal(px * U);
+  EB[3] = s->bratio * creal(-py * UB);
+  EB[4] = s->bratio * creal(px * UB);
   EB[2] = 0.0;
   EB[5] = 0.0;
   if (lon) {
@@ -294,6 +383,28 @@ void or_fields(const or_state *s, double x, double y, double z, double t, double
       EB[5] = s->bratio * creal((-I / p->omega) * (-py * DX + px * DY));
     }
   }
+}
+
+/* Eq. j1 with Phi = 0: the current of the linear plasma response,
+ *   J = Re[-i (omega_p^2 zeta / omega) A Gamma e^{i (psi + L1/omega)} p],
+ *   A = 1 - L2/omega^2 + (L1/omega)^2 / 2,
+ * the lowest finite-duration terms of the series in (i/omega)^n d^n/dt^n. */
+void or_current(const or_state *s, double x, double y, double z, double t, double J[3]) {
+  const or_pulse *p = &s->p;
+  J[0] = J[1] = J[2] = 0.0;
+  if (p->omega_p == 0.0) return;
+  double complex px, py;
+  polarisation(p->pol, &px, &py);
+  double eta = (t - p->t_focus) - (z - p->z_focus) / s->vg;
+  double G = or_envelope(s, eta);
+  double psi = p->omega * (t - p->t_focus) - s->k * (z - p->z_focus) + p->phase0;
+  double L1, L2;
+  or_envelope_logd(s, eta, &L1, &L2);
+  double th = L1 / p->omega;
+  double A = 1.0 - L2 / (p->omega * p->omega) + 0.5 * th * th;
+  double complex V = -I * s->jamp * profile_c(s, 0, x, y, z, t) * A * G * cexp(I * (psi + th));
+  J[0] = creal(px * V);
+  J[1] = creal(py * V);
 }
 
 /* ------------------------------------------------------------------ grid */
@@ -445,4 +556,36 @@ void or_yee1d(int64_t nz, double *E, double *B, double dz, double dt, int64_t n_
     for (int64_t k = 1; k < nz; ++k) E[k] -= r * (B[k] - B[k - 1]);
     for (int64_t k = 0; k + 1 < nz; ++k) B[k] -= 0.5 * r * (E[k + 1] - E[k]);
   }
+}
+
+void or_plasma1d(int64_t nz, double *E, double *B, double *J, const double *wp2, double dz,
+                 double dt, int64_t n_steps) {
+  const double r = dt / dz;
+  for (int64_t n = 0; n < n_steps; ++n) {
+    for (int64_t k = 0; k + 1 < nz; ++k) B[k] -= 0.5 * r * (E[k + 1] - E[k]);
+    for (int64_t k = 0; k < nz; ++k) J[k] += dt * wp2[k] * E[k];
+    for (int64_t k = 1; k < nz; ++k) E[k] = (E[k] - r * (B[k] - B[k - 1])) - dt * J[k];
+    for (int64_t k = 0; k + 1 < nz; ++k) B[k] -= 0.5 * r * (E[k + 1] - E[k]);
+  }
+}
+
+int or_apt1d(const or_state *s, int64_t nz, double *E2, double *B2, double *J, const double *wp2,
+             double z0, double dz, double t0, double dt, int64_t n_steps) {
+  if (s->p.pol != OR_LIN_X) return -1;
+  const double r = dt / dz;
+  double EB[6], J1[3];
+  for (int64_t n = 0; n < n_steps; ++n) {
+    const double t = t0 + (double)n * dt;
+    for (int64_t k = 0; k + 1 < nz; ++k) B2[k] -= 0.5 * r * (E2[k + 1] - E2[k]);
+    for (int64_t k = 0; k < nz; ++k) {
+      or_fields(s, 0.0, 0.0, z0 + (double)k * dz, t, EB);
+      J[k] += dt * wp2[k] * (EB[0] + E2[k]);
+    }
+    for (int64_t k = 1; k < nz; ++k) {
+      or_current(s, 0.0, 0.0, z0 + (double)k * dz, t + 0.5 * dt, J1);
+      E2[k] = (E2[k] - r * (B2[k] - B2[k - 1])) - dt * (J[k] - J1[0]);
+    }
+    for (int64_t k = 0; k + 1 < nz; ++k) B2[k] -= 0.5 * r * (E2[k + 1] - E2[k]);
+  }
+  return 0;
 }

@@ -18,7 +18,11 @@
  *     psi = omega (t - t_f) - k (z - z_f) + phase0  (Eq. plane_func),
  *     eta = (t - t_f) - (z - z_f) / v_g            (envelope argument);
  *   - B_perp = (B0/E0) z_hat x E_perp              (Eq. plane_b);
- *   - electron: q = -1, m = 1, du/dt = -(E + u x B / gamma), dx/dt = u/gamma.
+ *   - electron: q = -1, m = 1, du/dt = -(E + u x B / gamma), dx/dt = u/gamma;
+ *   - plasma (Sec. 4): Ampere's law dE/dt = curl B - J, the usual sign.  Eq.
+ *     E_1_j prints a plus sign, but with the current of Eq. j1 only the minus
+ *     sign gives the dispersion relation Eq. dispersion_j (omega^2 = omega_p^2
+ *     + c^2 k^2 in the continuum), so the plus is read as a misprint.
  *
  * Formulas are written in the textbook (w, R, atan Gouy) form with explicit
  * Laguerre sums; the longitudinal components come from 4th-order central
@@ -74,6 +78,9 @@ typedef struct {
   double bw_frac;           /* flying focus: half-width of the frequency spread / omega */
   double ff_length;         /* flying focus: length L of the focal range */
   double yee_dx, yee_dt;    /* cell size and time step entering Eqs. vphi, vg, e_amp */
+  double omega_p;           /* nonzero: plane wave in a linear cold plasma of plasma frequency
+                               omega_p, with the analytic current J1 of Sec. 4 (kind OR_PLANE,
+                               Gaussian, super-Gaussian or CW envelope) */
 } or_pulse;
 
 typedef struct {
@@ -85,6 +92,9 @@ typedef struct {
   double fw[OR_MAX_COMP], fk[OR_MAX_COMP], fz[OR_MAX_COMP], ft[OR_MAX_COMP];
   double fphi[OR_MAX_COMP], fzR[OR_MAX_COMP];
   double z_mid, t_mid;         /* flying focus: middle of the focal range and its time */
+  double zeta;                 /* plasma: current phase factor zeta (1 in the continuum) */
+  double jamp;                 /* plasma: omega_p^2 zeta / omega, J1 per unit field */
+  double fdc;                  /* plasma: 1 - v_phi / v_g, weight of B's finite-duration terms */
 } or_state;
 
 /* Derive all constants from the physical description.  Returns 0, or -1 for
@@ -94,6 +104,12 @@ int or_prepare(const or_pulse *p, or_state *s);
 /* Envelope Gamma(eta). */
 double or_envelope(const or_state *s, double eta);
 
+/* Logarithmic derivatives L1 = Gamma'/Gamma and L2 = Gamma''/Gamma of the
+ * envelope at eta (the finite-duration terms of Eqs. j1 and b_corr_t).
+ * Returns 0, or -1 for the sin^2 envelope (not twice differentiable at its
+ * ends). */
+int or_envelope_logd(const or_state *s, double eta, double *L1, double *L2);
+
 /* Complex transverse profile u of one beam (component j for the flying focus,
  * ignored otherwise) at (x, y, z) and time t (used by the closed-form flying
  * focus only), returned as re/im. */
@@ -102,6 +118,12 @@ void or_profile(const or_state *s, int j, double x, double y, double z, double t
 
 /* Analytic E1, B1 at (x, y, z, t): EB = {Ex, Ey, Ez, Bx, By, Bz}. */
 void or_fields(const or_state *s, double x, double y, double z, double t, double EB[6]);
+
+/* Analytic current J1 (Sec. 4, Eq. j1 with Phi = 0) at (x, y, z, t):
+ * J = {Jx, Jy, Jz}, zero unless omega_p > 0.  J stands for 4 pi J / c in the
+ * field units, so that Ampere's law reads dE/dt = curl B - J and the linear
+ * cold-plasma current obeys dJ/dt = omega_p^2 zeta E. */
+void or_current(const or_state *s, double x, double y, double z, double t, double J[3]);
 
 /* Trilinear gather of a static node-centred grid, layout [6][nz][ny][nx]
  * (x fastest), nodes at lo + i (hi - lo)/(n - 1); positions outside the box
@@ -153,6 +175,31 @@ void or_yee_nodes(const or_state *s, int nx, int ny, int nz, const double lo[3],
  *   B[k] -= (r/2) (E[k+1] - E[k]),  k = 0 .. nz-2
  * E[0] and B[nz-1] are never updated (fixed ends). */
 void or_yee1d(int64_t nz, double *E, double *B, double dz, double dt, int64_t n_steps);
+
+/* n_steps steps of the same line with a linear cold-plasma current J on the
+ * whole nodes (J[k] at z_k and half time levels), the traditional
+ * simulation that Sec. 4 compares against:
+ *   B half step as above;
+ *   J[k] += (dt wp2[k]) E[k],                  k = 0 .. nz-1  (J^{n+1/2})
+ *   E[k] = (E[k] - r (B[k] - B[k-1])) - dt J[k],  k = 1 .. nz-1
+ *   B half step with the new E.
+ * wp2[k] = omega_p^2 at z_k.  With wp2 = 0 this is or_yee1d. */
+void or_plasma1d(int64_t nz, double *E, double *B, double *J, const double *wp2, double dz,
+                 double dt, int64_t n_steps);
+
+/* n_steps steps of the line in the split form of Sec. 4 (Eqs. E_1_j, E_2_j):
+ * E2, B2 are the internally advanced fields, J the physical plasma current,
+ * driven by the total field E1 + E2; the E2 update takes the source
+ * J - J1 with the analytic E1 at (z_k, t_n) and J1 at (z_k, t_n + dt/2),
+ * t_n = t0 + n dt, z_k = z0 + k dz:
+ *   B2 half step;
+ *   J[k] += (dt wp2[k]) (E1 + E2[k]);
+ *   E2[k] = (E2[k] - r (B2[k] - B2[k-1])) - dt (J[k] - J1);
+ *   B2 half step.
+ * The line carries E_x and B_y: the pulse must be linearly polarised along
+ * x.  Returns 0, or -1 for another polarisation. */
+int or_apt1d(const or_state *s, int64_t nz, double *E2, double *B2, double *J, const double *wp2,
+             double z0, double dz, double t0, double dt, int64_t n_steps);
 
 #ifdef __cplusplus
 }

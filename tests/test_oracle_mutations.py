@@ -44,8 +44,9 @@ MUTATIONS = [
      "    for (int64_t k = 1; k < nz; ++k) E[k] -= r * (B[k] - B[k - 1]);",
      "    for (int64_t k = 1; k < nz; ++k) E[k] += r * (B[k] - B[k - 1]);", "yee1d_scheme"),
     ("Yee B half step taken as a full step",
-     "    for (int64_t k = 0; k + 1 < nz; ++k) B[k] -= 0.5 * r * (E[k + 1] - E[k]);\n  }",
-     "    for (int64_t k = 0; k + 1 < nz; ++k) B[k] -= r * (E[k + 1] - E[k]);\n  }", "yee1d_scheme"),
+     "E[k] -= r * (B[k] - B[k - 1]);\n    for (int64_t k = 0; k + 1 < nz; ++k) B[k] -= 0.5 * r * (E[k + 1] - E[k]);",
+     "E[k] -= r * (B[k] - B[k - 1]);\n    for (int64_t k = 0; k + 1 < nz; ++k) B[k] -= r * (E[k + 1] - E[k]);",
+     "yee1d_scheme"),
     ("Ex sampled on the cell node instead of the x edge", "    {0.5, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.0, 0.5},",
      "    {0.0, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.0, 0.5},", "staggering"),
     ("1D-3V push moves the transverse position",
@@ -55,9 +56,41 @@ MUTATIONS = [
      "    {0.5, 0.0, 0.5}, {0.5, 0.0, 0.5}, {0.5, 0.5, 0.0},", "staggering"),
 ]
 
+PLASMA = "tests/test_oracle_pins_plasma.py"
+MUTATIONS += [
+    ("current without the phase-velocity factor zeta", "  s->jamp = wp * wp * s->zeta / w;",
+     "  s->jamp = wp * wp / w;", "cw_is_carried", PLASMA),
+    ("current phase shift with the wrong sign", "  double th = L1 / p->omega;", "  double th = -L1 / p->omega;",
+     "finite_duration", PLASMA),
+    ("B finite-duration terms without the 1 - v_phi/v_g weight", "      double th = s->fdc * L1 / p->omega;",
+     "      double th = L1 / p->omega;", "finite_duration", PLASMA),
+    ("current amplitude second-derivative sign",
+     "  double A = 1.0 - L2 / (p->omega * p->omega) + 0.5 * th * th;",
+     "  double A = 1.0 + L2 / (p->omega * p->omega) + 0.5 * th * th;", "finite_duration", PLASMA),
+    ("plasma B0/E0 without the plasma factor",
+     "    s->bratio = cw * sqrt(1.0 - (wp * wp) / (w * w) * s->zeta * h / sw);", "    s->bratio = cw;",
+     "cw_is_carried", PLASMA),
+    ("fluid current driven by the updated E",
+     "    for (int64_t k = 0; k < nz; ++k) J[k] += dt * wp2[k] * E[k];\n"
+     "    for (int64_t k = 1; k < nz; ++k) E[k] = (E[k] - r * (B[k] - B[k - 1])) - dt * J[k];",
+     "    for (int64_t k = 1; k < nz; ++k) E[k] = (E[k] - r * (B[k] - B[k - 1])) - dt * J[k];\n"
+     "    for (int64_t k = 0; k < nz; ++k) J[k] += dt * wp2[k] * E[k];", "cw_is_carried", PLASMA),
+    ("Ampere current sign", "E[k] = (E[k] - r * (B[k] - B[k - 1])) - dt * J[k];",
+     "E[k] = (E[k] - r * (B[k] - B[k - 1])) + dt * J[k];", "cw_is_carried", PLASMA),
+    ("plasma group velocity without cos(omega dt/2)",
+     "    s->vg = r * r * sk * ck * p->yee_dx / (sw * cw * p->yee_dt);",
+     "    s->vg = r * r * sk * ck * p->yee_dx / (sw * p->yee_dt);", "domega_dk", PLASMA),
+    ("split line E2 source sign", "- dt * (J[k] - J1[0]);", "- dt * (J[k] + J1[0]);",
+     "split_line_keeps", PLASMA),
+    ("Gaussian L2 without the L1^2 term", "      *L2 = (*L1) * (*L1) - 2.0 * a;", "      *L2 = -2.0 * a;",
+     "log_derivatives", PLASMA),
+]
 
-@pytest.mark.parametrize("name,old,new,selector", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_planted_mistake_is_caught(tmp_path, name, old, new, selector):
+
+@pytest.mark.parametrize("mutation", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, mutation):
+    name, old, new, selector = mutation[:4]
+    pins = mutation[4] if len(mutation) > 4 else "tests/test_oracle_pins.py"
     work = tmp_path / "w"
     work.mkdir()
     shutil.copytree(os.path.join(ROOT, "oracle"), work / "oracle",
@@ -70,6 +103,6 @@ def test_planted_mistake_is_caught(tmp_path, name, old, new, selector):
     (work / "oracle" / "oracle.c").write_text(src.replace(old, new))
     env = dict(os.environ, PYTHONPATH=str(work))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        "tests/test_oracle_pins.py", "-k", selector],
+                        pins, "-k", selector],
                        cwd=str(work), env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1, "pins did not catch: %s\n%s" % (name, r.stdout[-2000:])
