@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define AP_ABI_VERSION 1
+#define AP_ABI_VERSION 2
 
 /* ------------------------------------------------------------ status codes */
 #define AP_OK 0
@@ -127,6 +127,15 @@ typedef struct {
   double bw_frac;     /* flying focus: frequencies span omega (1 +- bw_frac) */
   double ff_length;   /* flying focus: length L of the focal range */
   double yee_dx, yee_dt; /* AP_F_YEE_DISP: cell size and time step of the Yee solver */
+  double omega_p;     /* 0: vacuum.  > 0: plane wave in a linear cold plasma of plasma
+                         frequency omega_p carrying the analytic current J1 (Sec. 4);
+                         kind AP_PLANE only, envelope AP_ENV_GAUSS, AP_ENV_SGAUSS or
+                         AP_ENV_CW.  k follows from omega^2 = omega_p^2 + c^2 k^2, or with
+                         AP_F_YEE_DISP from the Yee relation with a leapfrog current
+                         (Eq. dispersion_j, zeta = (omega dt/2)/sin(omega dt/2)) and
+                         B0/E0 from Eq. e_amp_j; B carries the finite-duration terms of
+                         Eq. b_corr_t and J1 those of Eq. j1 (Phi = 0).  AP_ERR_ARG if
+                         omega is below the cut-off or the Yee relation has no real k. */
 } ap_pulse_desc;
 
 #define AP_MAX_COMP 128
@@ -217,6 +226,28 @@ typedef struct {
 } ap_yee1d;
 
 #define AP_YEE1D_MAX_NODES 12288  /* nodes per line: the line stays on chip (registers) */
+
+/* 1-D lines with a linear cold-plasma current (Sec. 4), device memory,
+ * caller-owned, [n_lines][nz] each, double for AP_FP64 and float for
+ * AP_FP32_PHASEFF, aligned to the element size:
+ *   E[l][k] = E_x at z_k, B[l][k] = B_y at z_{k+1/2}, both at whole time
+ *   levels; J[l][k] = J_x at z_k at half time levels (on entry t0 - dt/2);
+ *   wp2 (nullable) = omega_p^2 at z_k, [n_lines][nz]; NULL: omega_p^2 of
+ *   the field `omega_p` on every node.
+ * J stands for 4 pi J / c in the field units: Ampere's law reads
+ * dE/dt = curl B - J and the current obeys dJ/dt = omega_p^2 E.
+ * z_k = z0 + k dz places the nodes for the analytic fields (ap_apt1d_run). */
+typedef struct {
+  void *E, *B, *J;
+  const void *wp2;
+  int32_t nz, n_lines;
+  double dz, dt;
+  double omega_p;
+  double z0;
+} ap_line1d;
+
+#define AP_LINE1D_MAX_NODES_F32 12288 /* nodes per float line (the line sits in shared memory) */
+#define AP_LINE1D_MAX_NODES_F64 6144  /* nodes per double line */
 
 /* Launch shape, chosen by the autotuner (0 = library default). */
 typedef struct {
@@ -378,6 +409,16 @@ int ap_num_sets(ap_handle h);
 int ap_eval_nodes(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int32_t accumulate,
                   int32_t precision, void *stream);
 
+/* Analytic current J1 of plane-wave set `set` (Sec. 4, Eq. j1 with Phi = 0;
+ * zero for a vacuum pulse) at time t on the E nodes of `g`: f[0], f[1], f[2]
+ * receive J_x, J_y, J_z at the Ex, Ey, Ez offsets (J stands for 4 pi J / c,
+ * Ampere's law dE/dt = curl B - J); f[3..5] must be NULL.  The split form of
+ * Sec. 4 takes J1 at the half steps, t = t_n + dt/2.  accumulate and
+ * precision as for ap_eval_nodes.  Errors: those of ap_eval_nodes;
+ * AP_ERR_ARG also for a set that is not a plane wave or a non-NULL f[3..5]. */
+int ap_eval_current(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int32_t accumulate,
+                    int32_t precision, void *stream);
+
 /* n_steps steps of the second-order Yee scheme in vacuum on every line of
  * `y`, in the three-substep form of Sec. 2.1 with r = dt/dz:
  *   B[k] -= (r/2)(E[k+1] - E[k])   k = 0 .. nz-2
@@ -391,6 +432,41 @@ int ap_eval_nodes(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int3
  * AP_FP32_PHASEFF (float arrays).  Errors: AP_ERR_ARG (nz < 2 or above
  * AP_YEE1D_MAX_NODES, n_lines < 0, n_steps < 0), AP_ERR_ALIGN, AP_ERR_CUDA. */
 int ap_yee1d_run(const ap_yee1d *y, int64_t n_steps, int32_t precision, void *stream);
+
+/* n_steps steps of the Yee line with a linear cold-plasma current -- the
+ * traditional simulation that Sec. 4 compares the analytic current with --
+ * on every line of `y`, r = dt/dz, a_k = dt wp2[k]:
+ *   B[k] -= (r/2)(E[k+1] - E[k])                 k = 0 .. nz-2
+ *   J[k] += a_k E[k]                              k = 0 .. nz-1  (J^{n+1/2})
+ *   E[k] = (E[k] - r (B[k] - B[k-1])) - dt J[k]   k = 1 .. nz-1
+ *   B[k] -= (r/2)(E[k+1] - E[k])                 k = 0 .. nz-2
+ * E[0] and B[nz-1] are held fixed.  Each product, sum and difference is
+ * rounded separately in the stated order (no fused multiply-add); with
+ * wp2 = 0 the result is that of ap_yee1d_run bit for bit.  All steps run in
+ * one launch, one block per line with the line in shared memory.
+ * Errors: AP_ERR_ARG (nz < 2 or above AP_LINE1D_MAX_NODES_F32/_F64,
+ * n_lines < 0, n_steps < 0, NULL arrays, non-finite or non-positive dz, dt,
+ * negative or non-finite omega_p), AP_ERR_ALIGN, AP_ERR_CUDA. */
+int ap_plasma1d_run(const ap_line1d *y, int64_t n_steps, int32_t precision, void *stream);
+
+/* n_steps steps of the same lines in the split form of Sec. 4 (Eqs. E_1_j,
+ * E_2_j): E, B hold the internally advanced E2, B2 and J the physical plasma
+ * current, driven by the total field E1 + E2; the analytic E1 and current
+ * J1 are those of pulse set `set` at (x, y) = (0, 0), z_k = z0 + k dz:
+ *   B2[k] -= (r/2)(E2[k+1] - E2[k])
+ *   J[k] += a_k (E1(z_k, t_n) + E2[k])
+ *   E2[k] = (E2[k] - r (B2[k] - B2[k-1])) - dt (J[k] - J1(z_k, t_n + dt/2))
+ *   B2[k] -= (r/2)(E2[k+1] - E2[k])
+ * with t_n = t0 + n dt.  The total field is E1 + E2 (ap_eval_nodes on a
+ * 1-D grid with the same nodes gives E1, B1).  E1 and J1 are evaluated in
+ * every step in the kernel, in the precision's arithmetic (AP_FP32_PHASEFF:
+ * float with the float-float carrier phase), so E2 only carries the part of
+ * the field that the analytic pulse and current miss.  The pulse must be
+ * linearly polarised along x (the line carries E_x, B_y).
+ * Errors: those of ap_plasma1d_run; AP_ERR_ARG also for a bad set, a pulse
+ * not polarised along x, or 2 n_steps + 1 >= 2^24 with AP_FP32_PHASEFF. */
+int ap_apt1d_run(ap_handle h, int32_t set, const ap_line1d *y, double t0, int64_t n_steps,
+                 int32_t precision, void *stream);
 
 #ifdef __cplusplus
 }

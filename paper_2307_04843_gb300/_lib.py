@@ -39,6 +39,9 @@ AP_OBJ_MEAN_GAMMA = 0
 AP_MAX_COMP = 128
 AP_MAX_SETS = 4096
 AP_YEE1D_MAX_NODES = 12288
+AP_LINE1D_MAX_NODES_F32 = 12288
+AP_LINE1D_MAX_NODES_F64 = 6144
+AP_ABI_VERSION = 2
 
 
 class ApPulseDesc(ctypes.Structure):
@@ -50,6 +53,7 @@ class ApPulseDesc(ctypes.Structure):
         ("z_focus", ctypes.c_double), ("t_focus", ctypes.c_double), ("env_len", ctypes.c_double),
         ("phase0", ctypes.c_double), ("beta_f", ctypes.c_double), ("bw_frac", ctypes.c_double),
         ("ff_length", ctypes.c_double), ("yee_dx", ctypes.c_double), ("yee_dt", ctypes.c_double),
+        ("omega_p", ctypes.c_double),
     ]
 
 
@@ -89,6 +93,14 @@ class ApYee1d(ctypes.Structure):
     _fields_ = [
         ("E", ctypes.c_void_p), ("B", ctypes.c_void_p), ("nz", ctypes.c_int32),
         ("n_lines", ctypes.c_int32), ("dz", ctypes.c_double), ("dt", ctypes.c_double),
+    ]
+
+
+class ApLine1d(ctypes.Structure):
+    _fields_ = [
+        ("E", ctypes.c_void_p), ("B", ctypes.c_void_p), ("J", ctypes.c_void_p), ("wp2", ctypes.c_void_p),
+        ("nz", ctypes.c_int32), ("n_lines", ctypes.c_int32), ("dz", ctypes.c_double), ("dt", ctypes.c_double),
+        ("omega_p", ctypes.c_double), ("z0", ctypes.c_double),
     ]
 
 
@@ -133,7 +145,12 @@ SIGNATURES = {
     "ap_num_sets": (ctypes.c_int, [_vp]),
     "ap_eval_nodes": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ApYeeGrid), ctypes.c_double,
                                      ctypes.c_int32, ctypes.c_int32, _vp]),
+    "ap_eval_current": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ApYeeGrid), ctypes.c_double,
+                                       ctypes.c_int32, ctypes.c_int32, _vp]),
     "ap_yee1d_run": (ctypes.c_int, [ctypes.POINTER(ApYee1d), ctypes.c_int64, ctypes.c_int32, _vp]),
+    "ap_plasma1d_run": (ctypes.c_int, [ctypes.POINTER(ApLine1d), ctypes.c_int64, ctypes.c_int32, _vp]),
+    "ap_apt1d_run": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ApLine1d), ctypes.c_double,
+                                    ctypes.c_int64, ctypes.c_int32, _vp]),
 }
 
 _lib = None
@@ -162,6 +179,9 @@ def lib():
                     fn = getattr(L, name)
                     fn.restype = res
                     fn.argtypes = args
+                if L.ap_version() != AP_ABI_VERSION:
+                    raise RuntimeError("libapt.so has ABI version %d, the binding expects %d: rebuild it"
+                                       % (L.ap_version(), AP_ABI_VERSION))
                 _lib = L
     return _lib
 
@@ -188,7 +208,7 @@ def pulse_desc(d):
               (AP_F_YEE_DISP if d.get("yee", False) else 0) | \
               (AP_F_1D3V if d.get("one_d", False) else 0)
     for name in ("a0", "omega", "w0", "z_focus", "t_focus", "env_len", "phase0", "beta_f",
-                 "bw_frac", "ff_length", "yee_dx", "yee_dt"):
+                 "bw_frac", "ff_length", "yee_dx", "yee_dt", "omega_p"):
         setattr(p, name, float(d.get(name, 1.0 if name == "omega" else 0.0)))
     return p
 
@@ -453,6 +473,14 @@ def ap_eval_nodes(h, set_index, fields, lo, d, t, accumulate=False, precision="f
                                                _stream(stream)))
 
 
+def ap_eval_current(h, set_index, fields, lo, d, t, accumulate=False, precision="fp64", stream=None):
+    """J1 on the E nodes: fields = [Jx, Jy, Jz] tensors (or None)."""
+    gs = yee_grid_struct(list(fields) + [None, None, None], lo, d)
+    check("ap_eval_current", lib().ap_eval_current(h, set_index, ctypes.byref(gs), float(t),
+                                                   1 if accumulate else 0, precision_id(precision),
+                                                   _stream(stream)))
+
+
 def ap_yee1d_run(E, B, dz, dt, n_steps, stream=None):
     """n_steps of the 1-D vacuum Yee scheme on CUDA tensors E, B of shape
     (n_lines, nz) or (nz,), float64 (AP_FP64) or float32 (AP_FP32_PHASEFF)."""
@@ -470,6 +498,44 @@ def ap_yee1d_run(E, B, dz, dt, n_steps, stream=None):
     if prec is None:
         raise ValueError("E and B must be float32 or float64")
     check("ap_yee1d_run", lib().ap_yee1d_run(ctypes.byref(y), int(n_steps), prec, _stream(stream)))
+
+
+def line_struct(E, B, J, dz, dt, wp2=None, omega_p=0.0, z0=0.0):
+    """ap_line1d from CUDA tensors E, B, J (and optional wp2) of one shape
+    (n_lines, nz) or (nz,) and one dtype; returns (struct, precision id)."""
+    import torch
+    arrs = [E, B, J] + ([wp2] if wp2 is not None else [])
+    for a in arrs:
+        if a.shape != E.shape or a.dtype != E.dtype or not a.is_cuda or not a.is_contiguous():
+            raise ValueError("line arrays must be contiguous CUDA tensors of one shape and dtype")
+    if E.dim() not in (1, 2):
+        raise ValueError("line arrays must have shape (n_lines, nz) or (nz,)")
+    prec = {torch.float64: 0, torch.float32: 2}.get(E.dtype)
+    if prec is None:
+        raise ValueError("line arrays must be float32 or float64")
+    y = ApLine1d()
+    y.E, y.B, y.J = E.data_ptr(), B.data_ptr(), J.data_ptr()
+    y.wp2 = wp2.data_ptr() if wp2 is not None else None
+    y.nz = int(E.shape[-1])
+    y.n_lines = int(E.shape[0]) if E.dim() == 2 else 1
+    y.dz, y.dt, y.omega_p, y.z0 = float(dz), float(dt), float(omega_p), float(z0)
+    return y, prec
+
+
+def ap_plasma1d_run(E, B, J, dz, dt, n_steps, wp2=None, omega_p=0.0, stream=None):
+    """n_steps of the Yee line with a linear cold-plasma current (E_x at z_k,
+    B_y at z_{k+1/2}, J_x at z_k and half steps); float64 (AP_FP64) or
+    float32 (AP_FP32_PHASEFF) by the arrays' dtype."""
+    y, prec = line_struct(E, B, J, dz, dt, wp2, omega_p)
+    check("ap_plasma1d_run", lib().ap_plasma1d_run(ctypes.byref(y), int(n_steps), prec, _stream(stream)))
+
+
+def ap_apt1d_run(h, set_index, E2, B2, J, z0, dz, t0, dt, n_steps, wp2=None, omega_p=0.0, stream=None):
+    """n_steps of the split line of Sec. 4 with the analytic E1 and J1 of
+    set `set_index` (nodes at z0 + k dz, steps from t0)."""
+    y, prec = line_struct(E2, B2, J, dz, dt, wp2, omega_p, z0)
+    check("ap_apt1d_run", lib().ap_apt1d_run(h, int(set_index), ctypes.byref(y), float(t0), int(n_steps),
+                                             prec, _stream(stream)))
 
 
 # ------------------------------------------------------------ convenience
@@ -516,6 +582,14 @@ class Handle:
     def eval_nodes(self, fields, lo, d, t, accumulate=False, precision="fp64", set_index=0, stream=None):
         """Analytic E1/B1 on the Yee-staggered nodes (see ap_eval_nodes)."""
         ap_eval_nodes(self.h, set_index, fields, lo, d, t, accumulate, precision, stream)
+
+    def eval_current(self, fields, lo, d, t, accumulate=False, precision="fp64", set_index=0, stream=None):
+        """Analytic current J1 on the E nodes (see ap_eval_current)."""
+        ap_eval_current(self.h, set_index, fields, lo, d, t, accumulate, precision, stream)
+
+    def apt1d(self, E2, B2, J, z0, dz, t0, dt, n_steps, wp2=None, omega_p=0.0, set_index=0, stream=None):
+        """Split line with this handle's analytic E1 and J1 (see ap_apt1d_run)."""
+        ap_apt1d_run(self.h, set_index, E2, B2, J, z0, dz, t0, dt, n_steps, wp2, omega_p, stream)
 
     def status(self, stream=None):
         return ap_sync_status(self.h, stream)

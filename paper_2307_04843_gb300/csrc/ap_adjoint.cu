@@ -507,6 +507,7 @@ int ap_push_adjoint(ap_handle h, const ap_particles *p0, const ap_grid *g, doubl
   if (objective != AP_OBJ_MEAN_GAMMA) return AP_ERR_ARG;
   if (precision != AP_FP64 && precision != AP_FP32_PHASEFF) return AP_ERR_UNSUPPORTED;
   if (uk < 0 || uk == AP_FLYING_SUM) return AP_ERR_UNSUPPORTED;
+  if (apt::handle_any_plasma(h)) return AP_ERR_UNSUPPORTED;
   if (n_steps < 1 || ckpt_every < 1 || ckpt_every > apt::kAdjMaxK) return AP_ERR_ARG;
   if (p0->set_offsets ? p0->n_sets != ns : ns != 1) return AP_ERR_ARG;
   const size_t need = ap_adjoint_workspace_bytes(h, p0->n, n_steps, ckpt_every);

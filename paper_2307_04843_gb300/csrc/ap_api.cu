@@ -97,6 +97,41 @@ double lg_peak(int p, int a) {
   return v > fb ? v : fb;
 }
 
+// Plane wave in a linear cold plasma (Sec. 4): wavenumber k, group velocity,
+// B0/E0 and the current's phase factor zeta.  With AP_F_YEE_DISP the Yee
+// relation of Eq. dispersion_j for a current advanced by the leapfrog
+// dJ/dt = omega_p^2 E at half steps, whose zeta = h/sin h (h = omega dt/2)
+// turns the plasma term into q^2, q = omega_p dt/2:
+//   sin^2 h - q^2 = (dt/dx)^2 sin^2(k dx/2),
+// v_g = d omega/dk from the two sides' derivatives, and Eq. e_amp_j
+// B0/E0 = cos h sqrt(1 - q^2/sin^2 h).  Otherwise the continuum:
+// omega^2 = omega_p^2 + k^2, v_g = k/omega, B0/E0 = k/omega, zeta = 1.
+// False when no real k exists (below the cut-off, or beyond the grid's
+// largest wavenumber).
+bool plasma_dispersion(const ap_pulse_desc &d, double &k, double &vg, double &br, double &zeta) {
+  const double w = d.omega, wp = d.omega_p;
+  if (d.flags & AP_F_YEE_DISP) {
+    const double h = 0.5 * w * d.yee_dt;
+    if (!(h < 0.5 * kPi)) return false;
+    const double sh = std::sin(h), ch = std::cos(h), r = d.yee_dt / d.yee_dx;
+    const double q = 0.5 * wp * d.yee_dt;
+    const double s2 = (sh * sh - q * q) / (r * r);  // sin^2(k dx/2)
+    if (!(s2 > 0.0 && s2 < 1.0)) return false;
+    const double sk = std::sqrt(s2), ck = std::sqrt(1.0 - s2);
+    zeta = h / sh;
+    k = 2.0 * std::asin(sk) / d.yee_dx;
+    vg = r * r * sk * ck * d.yee_dx / (sh * ch * d.yee_dt);
+    br = ch * std::sqrt(1.0 - (q * q) / (sh * sh));
+  } else {
+    if (!(wp < w)) return false;
+    zeta = 1.0;
+    k = std::sqrt((w - wp) * (w + wp));
+    vg = k / w;
+    br = k / w;
+  }
+  return true;
+}
+
 int check_desc(const ap_pulse_desc &d) {
   if (d.kind < AP_PLANE || d.kind > AP_FLYING_CF) return AP_ERR_ARG;
   if (d.kind == AP_FLYING_CF && !(d.beta_f < 1.0 && std::isfinite(d.beta_f))) return AP_ERR_ARG;
@@ -123,6 +158,13 @@ int check_desc(const ap_pulse_desc &d) {
     if (!(d.yee_dx > 0.0) || !(d.yee_dt > 0.0) || !(d.yee_dt < d.yee_dx)) return AP_ERR_ARG;
   }
   if (d.flags & ~(AP_F_LONGITUDINAL | AP_F_YEE_DISP | AP_F_1D3V)) return AP_ERR_ARG;
+  if (!(d.omega_p >= 0.0) || !std::isfinite(d.omega_p)) return AP_ERR_ARG;
+  if (d.omega_p > 0.0) {
+    if (d.kind != AP_PLANE) return AP_ERR_ARG;
+    if (d.env != AP_ENV_GAUSS && d.env != AP_ENV_SGAUSS && d.env != AP_ENV_CW) return AP_ERR_ARG;
+    double k, vg, br, zeta;
+    if (!plasma_dispersion(d, k, vg, br, zeta)) return AP_ERR_ARG;
+  }
   return AP_OK;
 }
 
@@ -145,7 +187,23 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
     vg = 1.0 - (1.0 - cr * cr) * wdx * wdx / 8.0;
     br = 1.0 - wdt * wdt / 8.0;
   }
-  const double k = d.omega / vphi;
+  double k = d.omega / vphi, zeta = 1.0;
+  if (d.omega_p > 0.0) {
+    plasma_dispersion(d, k, vg, br, zeta);
+    vphi = d.omega / k;
+    P.plasma = 1;
+    P.fdc = 1.0 - vphi / vg;
+    P.jamp = d.omega_p * d.omega_p * zeta / d.omega;
+  }
+  P.inv_w = 1.0 / d.omega;
+  if (d.env == AP_ENV_GAUSS) {  // ln Gamma = -2 ln2 eta^2 / T^2
+    P.lg_c1 = 4.0 * std::log(2.0) / (d.env_len * d.env_len);
+    P.lg_c2 = P.lg_c1;
+  } else if (d.env == AP_ENV_SGAUSS) {  // ln Gamma = -(eta/tau)^(2g)
+    const double g2 = 2.0 * d.sg_order;
+    P.lg_c1 = g2 / d.env_len;
+    P.lg_c2 = g2 * (g2 - 1.0) / (d.env_len * d.env_len);
+  }
   P.omega = d.omega;
   P.k = k;
   P.t_f = d.t_focus;
@@ -263,7 +321,9 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
   std::memset(&F, 0, sizeof(F));
   F.kind = P.kind; F.pol = P.pol; F.env = P.env; F.lon = P.lon;
   F.lg_p = P.lg_p; F.lg_al = P.lg_al; F.lg_sgn = P.lg_sgn; F.n_comp = P.n_comp;
-  F.sg_order = P.sg_order; F.yee = P.yee;
+  F.sg_order = P.sg_order; F.yee = P.yee; F.plasma = P.plasma;
+  F.fdc = (float)P.fdc; F.jamp = (float)P.jamp; F.inv_w = (float)P.inv_w;
+  F.lg_c1 = (float)P.lg_c1; F.lg_c2 = (float)P.lg_c2;
   F.amp = (float)P.amp; F.inv_vg = (float)P.inv_vg; F.bratio = (float)P.bratio;
   F.lonE = (float)P.lonE; F.lonB = (float)P.lonB;
   F.inv_w0sq = (float)P.inv_w0sq; F.inv_zR = (float)P.inv_zR;
@@ -449,6 +509,13 @@ int handle_info(ap_handle h, int *device, int *sm_count, int *n_sets, int *unifo
   return AP_OK;
 }
 
+int handle_any_plasma(ap_handle h) {
+  if (!h) return 0;
+  for (const auto &d : h->descs)
+    if (d.omega_p > 0.0) return 1;
+  return 0;
+}
+
 int handle_push_args(ap_handle h, const ap_particles *p, const ap_grid *g, double t0, double dt,
                      int64_t n_steps, int32_t precision, PushArgs *a, void *stream) {
   return fill_push_args(h, p, g, t0, dt, n_steps, precision, nullptr, 1, *a, stream);
@@ -599,9 +666,13 @@ int ap_eval_fields(ap_handle h, int32_t set, const double *xyzt, int64_t n, doub
   return apt::launch_eval(h->descs[set].kind, precision, h->pd[set], h->pf[set], a, stream);
 }
 
-int ap_eval_nodes(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int32_t accumulate,
-                  int32_t precision, void *stream) {
+namespace {
+
+// Analytic E1/B1 (current = 0) or J1 (current = 1) on the staggered nodes.
+int eval_nodes_common(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int32_t accumulate,
+                      int32_t precision, void *stream, int current) {
   if (!h || !g || set < 0 || set >= h->n_sets) return AP_ERR_ARG;
+  if (current && (h->descs[set].kind != AP_PLANE || g->f[3] || g->f[4] || g->f[5])) return AP_ERR_ARG;
   if (precision < AP_FP64 || precision > AP_FP32_PHASEFF) return AP_ERR_ARG;
   if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !std::isfinite(t)) return AP_ERR_ARG;
   // node indices (and index + grid stride) are exact in float; the node
@@ -649,7 +720,20 @@ int ap_eval_nodes(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int3
   }
   a.t = t;
   a.sm_count = h->sm_count;
+  a.current = current;
   return apt::launch_nodes(h->descs[set].kind, precision, h->pd[set], h->pf[set], a, stream);
+}
+
+}  // namespace
+
+int ap_eval_nodes(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int32_t accumulate,
+                  int32_t precision, void *stream) {
+  return eval_nodes_common(h, set, g, t, accumulate, precision, stream, 0);
+}
+
+int ap_eval_current(ap_handle h, int32_t set, const ap_yee_grid *g, double t, int32_t accumulate,
+                    int32_t precision, void *stream) {
+  return eval_nodes_common(h, set, g, t, accumulate, precision, stream, 1);
 }
 
 int ap_gather_push(ap_handle h, const ap_particles *p, const ap_grid *g, double t0, double dt,
@@ -751,3 +835,66 @@ int ap_sync_status(ap_handle h, void *stream) {
 }
 
 }  // extern "C"
+
+namespace {
+
+// Validates a line description and fills the kernel arguments.
+int line_args(const ap_line1d *y, int64_t n_steps, int32_t precision, apt::LineArgs *a) {
+  if (!y || n_steps < 0 || y->n_lines < 0) return AP_ERR_ARG;
+  if (precision != AP_FP64 && precision != AP_FP32_PHASEFF) return AP_ERR_ARG;
+  const int max_nodes = precision == AP_FP64 ? AP_LINE1D_MAX_NODES_F64 : AP_LINE1D_MAX_NODES_F32;
+  if (y->nz < 2 || y->nz > max_nodes) return AP_ERR_ARG;
+  if (!(y->dz > 0.0) || !(y->dt > 0.0) || !(y->dz < 1e300) || !(y->dt < 1e300)) return AP_ERR_ARG;
+  if (!(y->omega_p >= 0.0) || !std::isfinite(y->omega_p) || !std::isfinite(y->z0)) return AP_ERR_ARG;
+  if (y->n_lines > 0 && (!y->E || !y->B || !y->J)) return AP_ERR_ARG;
+  const uintptr_t mask = precision == AP_FP64 ? 7u : 3u;
+  const uintptr_t bits = reinterpret_cast<uintptr_t>(y->E) | reinterpret_cast<uintptr_t>(y->B) |
+                         reinterpret_cast<uintptr_t>(y->J) | reinterpret_cast<uintptr_t>(y->wp2);
+  if ((bits & mask) != 0) return AP_ERR_ALIGN;
+  std::memset(a, 0, sizeof(*a));
+  a->E = y->E;
+  a->B = y->B;
+  a->J = y->J;
+  a->wp2 = y->wp2;
+  a->nz = y->nz;
+  a->n_lines = y->n_lines;
+  a->dz = y->dz;
+  a->dt = y->dt;
+  a->omega_p2 = y->omega_p * y->omega_p;
+  a->z0 = y->z0;
+  a->z0_hi = (float)y->z0;
+  a->z0_lo = (float)(y->z0 - (double)a->z0_hi);
+  a->dz_hi = (float)y->dz;
+  a->dz_lo = (float)(y->dz - (double)a->dz_hi);
+  a->n_steps = n_steps;
+  return AP_OK;
+}
+
+}  // namespace
+
+int ap_plasma1d_run(const ap_line1d *y, int64_t n_steps, int32_t precision, void *stream) {
+  apt::LineArgs a;
+  const int rc = line_args(y, n_steps, precision, &a);
+  if (rc != AP_OK) return rc;
+  if (y->n_lines == 0 || n_steps == 0) return AP_OK;
+  static const Pulse<double> unused_d{};
+  static const Pulse<float> unused_f{};
+  return apt::launch_line(false, precision, unused_d, unused_f, a, stream);
+}
+
+int ap_apt1d_run(ap_handle h, int32_t set, const ap_line1d *y, double t0, int64_t n_steps,
+                 int32_t precision, void *stream) {
+  if (!h || set < 0 || set >= h->n_sets || !std::isfinite(t0)) return AP_ERR_ARG;
+  const ap_pulse_desc &d = h->descs[set];
+  if (d.kind != AP_PLANE || d.pol != AP_LIN_X) return AP_ERR_ARG;
+  // float-float time levels: 2 n + 1 exact in float
+  if (precision == AP_FP32_PHASEFF && n_steps >= (1 << 23)) return AP_ERR_ARG;
+  apt::LineArgs a;
+  int rc = line_args(y, n_steps, precision, &a);
+  if (rc != AP_OK) return rc;
+  rc = current_device_matches(h);
+  if (rc != AP_OK) return rc;
+  if (y->n_lines == 0 || n_steps == 0) return AP_OK;
+  a.t0 = t0;
+  return apt::launch_line(true, precision, h->pd[set], h->pf[set], a, stream);
+}

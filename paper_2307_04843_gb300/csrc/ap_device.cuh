@@ -436,7 +436,45 @@ __device__ __forceinline__ R reduce_angle(R a) {
   return a;
 }
 
-// Plane wave (Eqs. plane_func, plane_b): U = A Gamma e^{i psi}.
+// Logarithmic derivatives L1 = Gamma'/Gamma and L2 = Gamma''/Gamma of the
+// envelope (the finite-duration terms of Sec. 4).  GAUSS: ln Gamma =
+// -2 ln2 eta^2/T^2, so L1 = -lg_c1 eta and L2 = L1^2 - lg_c2 with
+// lg_c1 = lg_c2 = 4 ln2/T^2.  SGAUSS: ln Gamma = -u^(2g), u = eta/tau, so with
+// q = u^(2g-2): L1 = -lg_c1 u q, L2 = L1^2 - lg_c2 q, lg_c1 = 2g/tau,
+// lg_c2 = 2g(2g-1)/tau^2.  CW: zero.
+template <class PT, typename R>
+__device__ __forceinline__ void envelope_logd(const PT &P, R eta, R &L1, R &L2) {
+  L1 = R(0);
+  L2 = R(0);
+  if (P.env == AP_ENV_GAUSS) {
+    L1 = -P.lg_c1 * eta;
+    L2 = L1 * L1 - P.lg_c2;
+  } else if (P.env == AP_ENV_SGAUSS) {
+    const R u = eta * P.env_a;
+    const R s = u * u;
+    R q = R(1);
+    for (int i = 1; i < P.sg_order; ++i) q *= s;
+    L1 = -P.lg_c1 * u * q;
+    L2 = L1 * L1 - P.lg_c2 * q;
+  }
+}
+
+// Amplitude factor and phase shift of the lowest finite-duration terms,
+// A = 1 - w L2/omega^2 + th^2/2, th = w L1/omega (Eqs. j1 and b_corr_t with
+// Phi = 0; w = 1 for J1, w = 1 - v_phi/v_g for B), applied to U as
+// A U e^{i th}.
+template <typename R>
+__device__ __forceinline__ Cx<R> finite_duration(Cx<R> U, R w, R L1, R L2, R inv_w) {
+  const R th = w * L1 * inv_w;
+  const R A = R(1) - w * L2 * inv_w * inv_w + R(0.5) * th * th;
+  R s, c;
+  sincos_r(th, &s, &c);
+  return {A * (U.re * c - U.im * s), A * (U.re * s + U.im * c)};
+}
+
+// Plane wave (Eqs. plane_func, plane_b): U = A Gamma e^{i psi}.  In a
+// plasma (Sec. 4) B is built from U with the finite-duration terms of
+// Eq. b_corr_t.
 template <class PT, typename R>
 __device__ __forceinline__ void fields_plane(const PT &P, const Local<R> &L, R E[3], R B[3]) {
   R mul, l2;
@@ -447,6 +485,34 @@ __device__ __forceinline__ void fields_plane(const PT &P, const Local<R> &L, R E
   sincos_r(L.psi, &s, &c);
   Cx<R> U{a * c, a * s};
   finish_beam(P, L.x, L.y, U, U, R(0), false, E, B);
+  if constexpr (std::is_same<PT, Pulse<R>>::value) {
+    if (P.plasma) {
+      R L1, L2, Et[3];
+      envelope_logd(P, L.eta, L1, L2);
+      const Cx<R> UB = finite_duration(U, P.fdc, L1, L2, P.inv_w);
+      finish_beam(P, L.x, L.y, UB, UB, R(0), false, Et, B);
+    }
+  }
+}
+
+// Analytic current J1 of a plane wave in a linear plasma (Sec. 4, Eq. j1
+// with Phi = 0): J = Re[-i (omega_p^2 zeta/omega) A U e^{i th} p],
+// th = L1/omega, A = 1 - L2/omega^2 + th^2/2.  J stands for 4 pi J / c.
+template <typename R>
+__device__ __forceinline__ void current_plane(const Pulse<R> &P, const Local<R> &L, R J[3]) {
+  R mul, l2;
+  envelope(P, L.eta, mul, l2);
+  R a = P.jamp * P.amp * mul;
+  if (l2 != R(0)) a *= exp2_r(l2);
+  R s, c;
+  sincos_r(L.psi, &s, &c);
+  R L1, L2;
+  envelope_logd(P, L.eta, L1, L2);
+  const Cx<R> V = finite_duration(Cx<R>{a * c, a * s}, R(1), L1, L2, P.inv_w);
+  // Re[p (-i V)] with -i V = (V.im, -V.re)
+  J[0] = P.px_re * V.im + P.px_im * V.re;
+  J[1] = P.py_re * V.im + P.py_im * V.re;
+  J[2] = R(0);
 }
 
 // Paraxial Gaussian beam (Eq. paraxial, D = 3, +z):

@@ -33,7 +33,7 @@ template <typename R>
 struct Pulse {
   int32_t kind, pol, env, lon;
   int32_t lg_p, lg_al, lg_sgn, n_comp;
-  int32_t sg_order, yee, pad0, pad1;
+  int32_t sg_order, yee, plasma, pad1;
   R amp;            // amplitude coefficient A of the profile
   R inv_vg;         // 1 / v_g
   R bratio;         // B0 / E0 (Eq. e_amp; 1 in vacuum)
@@ -51,6 +51,11 @@ struct Pulse {
   R a0, inv_w0, amp_unit;        // a0, 1/w0 and amp / a0 (adjoint: d/da0, d/dw0)
   R beta_f, inv_1mb;             // closed-form flying focus: v_f / c and 1 / (1 - beta_f)
   R adv_xy;                      // 1, or 0 for 1D-3V sets (transverse position held)
+  // plane wave in a linear plasma (Sec. 4): 1 - v_phi/v_g (weight of B's
+  // finite-duration terms, Eq. b_corr_t), J1 amplitude omega_p^2 zeta/omega
+  // (Eq. j1), 1/omega, and the constants of the envelope's logarithmic
+  // derivatives (see envelope_logd)
+  R fdc, jamp, inv_w, lg_c1, lg_c2;
   // carrier phase psi = omega (t - t_f) - k (z - z_f) + phase0 (double, host-exact)
   double omega, k, t_f, z_f, phase0;
   // float-float copies for AP_FP32_PHASEFF
@@ -131,7 +136,23 @@ struct NodeArgs {
   float lo_hi[3], lo_lo[3], d_hi[3], d_lo[3];
   double t;
   int sm_count;
+  int current;  // 1: the analytic current J1 into f[0..2] (plane waves)
 };
+
+// 1-D lines with a linear cold-plasma current (ap_line.cu): the traditional
+// line, or the split line with the analytic E1 and J1 of a plane-wave pulse.
+struct LineArgs {
+  void *E, *B, *J;
+  const void *wp2;       // [n_lines][nz] or null (uniform omega_p2)
+  int nz, n_lines;
+  double dz, dt, omega_p2, z0, t0;
+  float z0_hi, z0_lo, dz_hi, dz_lo;  // float-float node positions (AP_FP32_PHASEFF)
+  long long n_steps;
+};
+// Nonzero if any set of the handle is a plasma pulse (Sec. 4).
+int handle_any_plasma(ap_handle h);
+int launch_line(bool apt, int precision, const Pulse<double> &pd, const Pulse<float> &pf,
+                const LineArgs &a, void *stream);
 
 // One launcher per pulse kind; precision selects the template instance.
 // `pulse_d` / `pulse_f` are host copies; `dpulse_*` device copies (batched).

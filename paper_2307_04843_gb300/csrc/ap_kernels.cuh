@@ -350,6 +350,21 @@ __device__ __forceinline__ FF node_coord_ff(float f, float lo_hi, float lo_lo, f
   return {hi, __fsub_rn(s.lo, __fsub_rn(hi, s.hi))};
 }
 
+// What a node receives: the analytic E1, B1, or (plane waves, `current`)
+// the analytic current J1 in place of E with B zero.
+template <int KIND, int PREC>
+__device__ __forceinline__ void node_values(const Pulse<Real<PREC>> &P, const Local<Real<PREC>> &L,
+                                            int current, Real<PREC> E[3], Real<PREC> B[3]) {
+  if constexpr (KIND == AP_PLANE) {
+    if (current) {
+      current_plane(P, L, E);
+      B[0] = B[1] = B[2] = Real<PREC>(0);
+      return;
+    }
+  }
+  analytic_fields<KIND, PREC>(P, L, E, B);
+}
+
 template <int KIND, int PREC, typename T>
 __global__ void __launch_bounds__(256) nodes_kernel(const __grid_constant__ Pulse<Real<PREC>> P,
                                                     const __grid_constant__ NodeArgs a) {
@@ -396,7 +411,7 @@ __global__ void __launch_bounds__(256) nodes_kernel(const __grid_constant__ Puls
     }
     Local<R> L = local_coords<PREC>(P, st, pos);
     R E[3], B[3];
-    analytic_fields<KIND, PREC>(P, L, E, B);
+    node_values<KIND, PREC>(P, L, a.current, E, B);
     const R v = c == 0 ? E[0] : c == 1 ? E[1] : c == 2 ? E[2] : c == 3 ? B[0] : c == 4 ? B[1] : B[2];
     f[n] = a.accumulate ? (T)((W)f[n] + (W)v) : (T)v;
     // advance (i, j, k) by the stride (k only grows until the loop ends)
@@ -493,7 +508,7 @@ __global__ void __launch_bounds__(256) nodes_plane_kernel(const __grid_constant_
     }
     Local<R> L = local_coords<PREC>(P, st, pos);
     R E[3], B[3];
-    analytic_fields<AP_PLANE, PREC>(P, L, E, B);
+    node_values<AP_PLANE, PREC>(P, L, a.current, E, B);
     const R v = c == 0 ? E[0] : c == 1 ? E[1] : c == 2 ? E[2] : c == 3 ? B[0] : c == 4 ? B[1] : B[2];
     T *row = f + r * a.nx;
     for (int i = lane; i < a.nx; i += 32) row[i] = a.accumulate ? (T)((W)row[i] + (W)v) : (T)v;

@@ -1,0 +1,151 @@
+// ap_line.cu -- 1-D lines with a linear cold-plasma current (Sec. 4, the
+// analytic pulse technique with an analytic current J1).
+//
+// Two updates of one line carrying E_x on the whole nodes z_k, B_y on the
+// half nodes and the current J_x on the whole nodes at half time levels:
+//   traditional: the Yee scheme of Sec. 2.1 with the current advanced by the
+//     leapfrog dJ/dt = omega_p^2 E (the simulation Sec. 4 compares with);
+//   split (APT): E, B hold the internally advanced E2, B2; the physical
+//     current J is driven by E1 + E2, and E2 is sourced by J - J1, with the
+//     analytic E1 (at t_n) and J1 (at t_n + dt/2) of a plane-wave pulse
+//     evaluated in the kernel every step (Eqs. E_1_j, E_2_j, j1).
+//
+// One block per line; the line (E, B, J and a_k = dt omega_p^2(z_k)) stays
+// in shared memory for all n_steps and is written back once.  Per step: the
+// B half step; a barrier; the current and E update of each node (one pass:
+// both read only the node's own E and J and the neighbouring B); a barrier;
+// the second B half step.  The second B half step and the next step's first
+// one write only their own node and read only E, so no barrier separates
+// them.  Each product, sum and difference is rounded separately in the
+// stated order, so the double traditional line reproduces a plain double
+// loop of the same expressions bit for bit.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ap_kernels.cuh"
+
+namespace apt {
+namespace {
+
+constexpr int kLineBlock = 1024;
+
+__device__ __forceinline__ double l_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double l_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double l_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float l_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float l_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float l_mul(float a, float b) { return __fmul_rn(a, b); }
+
+// Local coordinates of node k (x = y = 0) at one time level.
+template <int PREC>
+__device__ __forceinline__ Local<Real<PREC>> node_local(const Pulse<Real<PREC>> &P, const LineArgs &a,
+                                                        const typename TimeBase<PREC>::Step &st, int k) {
+  Pos<PREC> pos;
+  if constexpr (PREC == AP_FP32_PHASEFF) {
+    pos.x = FF{0.0f, 0.0f};
+    pos.y = FF{0.0f, 0.0f};
+    pos.z = node_coord_ff((float)k, a.z0_hi, a.z0_lo, a.dz_hi, a.dz_lo);
+  } else {
+    pos.load(0.0, 0.0, __dadd_rn(a.z0, __dmul_rn((double)k, a.dz)));
+  }
+  return local_coords<PREC>(P, st, pos);
+}
+
+template <typename T, int PREC, bool APT>
+__global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant__ Pulse<Real<PREC>> P,
+                                                          const __grid_constant__ LineArgs a) {
+  using R = Real<PREC>;
+  extern __shared__ __align__(16) unsigned char line_smem[];
+  const int nz = a.nz;
+  T *e = reinterpret_cast<T *>(line_smem);
+  T *b = e + nz;
+  T *j = b + nz;
+  T *q = j + nz;  // a_k = dt omega_p^2(z_k)
+  const size_t off = (size_t)blockIdx.x * (size_t)nz;
+  T *Eg = static_cast<T *>(a.E) + off;
+  T *Bg = static_cast<T *>(a.B) + off;
+  T *Jg = static_cast<T *>(a.J) + off;
+  const T *W = a.wp2 ? static_cast<const T *>(a.wp2) + off : nullptr;
+  const T dt = (T)a.dt;
+  const T r = (T)(a.dt / a.dz);
+  const T hr = (T)(0.5 * (a.dt / a.dz));
+  const T wpu = (T)a.omega_p2;
+  const int t = threadIdx.x, bd = blockDim.x;
+  for (int k = t; k < nz; k += bd) {
+    e[k] = Eg[k];
+    b[k] = Bg[k];
+    j[k] = Jg[k];
+    q[k] = l_mul(dt, W ? W[k] : wpu);
+  }
+  TimeBase<PREC> tb;
+  if constexpr (APT) tb.init(P, a.t0, 0.5 * a.dt);  // level 2n: t_n, 2n + 1: t_n + dt/2
+  __syncthreads();
+  for (long long n = 0; n < a.n_steps; ++n) {
+    // B^{n+1/2} = B^n - (r/2)(E_{k+1}^n - E_k^n)
+    for (int k = t; k < nz - 1; k += bd) b[k] = l_sub(b[k], l_mul(hr, l_sub(e[k + 1], e[k])));
+    __syncthreads();
+    typename TimeBase<PREC>::Step st_e{}, st_j{};
+    if constexpr (APT) {
+      st_e = tb.at(2 * n);
+      st_j = tb.at(2 * n + 1);
+    }
+    // J^{n+1/2} = J^{n-1/2} + a_k (E1 + E2)^n;  E^{n+1} = (E^n - r dB) - dt (J - J1)^{n+1/2}
+    for (int k = t; k < nz; k += bd) {
+      const T ek = e[k];
+      T drive = ek;
+      if constexpr (APT) {
+        R E1[3], B1[3];
+        const Local<R> L = node_local<PREC>(P, a, st_e, k);
+        analytic_fields<AP_PLANE, PREC>(P, L, E1, B1);
+        drive = l_add((T)E1[0], ek);
+      }
+      const T jk = l_add(j[k], l_mul(q[k], drive));
+      j[k] = jk;
+      if (k >= 1) {
+        T src = jk;
+        if constexpr (APT) {
+          R J1[3];
+          const Local<R> L = node_local<PREC>(P, a, st_j, k);
+          current_plane(P, L, J1);
+          src = l_sub(jk, (T)J1[0]);
+        }
+        e[k] = l_sub(l_sub(ek, l_mul(r, l_sub(b[k], b[k - 1]))), l_mul(dt, src));
+      }
+    }
+    __syncthreads();
+    // B^{n+1} = B^{n+1/2} - (r/2)(E_{k+1}^{n+1} - E_k^{n+1})
+    for (int k = t; k < nz - 1; k += bd) b[k] = l_sub(b[k], l_mul(hr, l_sub(e[k + 1], e[k])));
+  }
+  // every node is written back by the thread that last wrote it
+  for (int k = t; k < nz; k += bd) {
+    Eg[k] = e[k];
+    Bg[k] = b[k];
+    Jg[k] = j[k];
+  }
+}
+
+template <typename T, int PREC, bool APT>
+int launch_line_t(const Pulse<Real<PREC>> &P, const LineArgs &a, void *stream) {
+  auto kern = line_kernel<T, PREC, APT>;
+  const size_t smem = 4u * sizeof(T) * (size_t)a.nz;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return AP_ERR_CUDA;
+  int block = (a.nz + 31) / 32 * 32;
+  if (block > kLineBlock) block = kLineBlock;
+  kern<<<(unsigned)a.n_lines, block, smem, static_cast<cudaStream_t>(stream)>>>(P, a);
+  return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+}
+
+}  // namespace
+
+int launch_line(bool apt_mode, int precision, const Pulse<double> &pd, const Pulse<float> &pf,
+                const LineArgs &a, void *stream) {
+  if (precision == AP_FP64)
+    return apt_mode ? launch_line_t<double, AP_FP64, true>(pd, a, stream)
+                    : launch_line_t<double, AP_FP64, false>(pd, a, stream);
+  return apt_mode ? launch_line_t<float, AP_FP32_PHASEFF, true>(pf, a, stream)
+                  : launch_line_t<float, AP_FP32_PHASEFF, false>(pf, a, stream);
+}
+
+}  // namespace apt

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_version_and_status_strings(L):
-    assert _lib.ap_version() == 1
+    assert _lib.ap_version() == _lib.AP_ABI_VERSION == 2
     for code in (0, -1, -2, -3, -4, -5, -6, -7):
         s = _lib.ap_status_string(code)
         assert s and s != "unknown status"
@@ -62,6 +62,12 @@ def _init_rc(L, d, n=1):
     dict(kind="flying", w0=1.0, n_comp=8, beta_f=0.0, ff_length=10.0),
     dict(kind="plane", yee=True, yee_dx=0.1, yee_dt=0.2),       # Courant number > 1
     dict(kind="plane", a0=float("nan")),
+    dict(kind="plane", env="cw", omega_p=1.5),                  # plasma: omega below the cut-off
+    dict(kind="plane", env="cw", omega_p=-0.1),
+    dict(kind="plane", env="cw", omega_p=float("nan")),
+    dict(kind="gauss", w0=5.0, env="cw", omega_p=0.1),           # J1 only for plane waves
+    dict(kind="plane", env="sin2", env_len=4.0, omega_p=0.1),    # envelope without Gamma''
+    dict(kind="plane", env="cw", omega_p=0.05, yee=True, yee_dx=3.1, yee_dt=3.05),  # k beyond the grid
 ])
 def test_invalid_descriptions_rejected_on_host(L, bad):
     rc, h = _init_rc(L, bad)
@@ -117,3 +123,34 @@ def test_node_and_yee_arguments_rejected_on_host(L):
 def test_build_is_up_to_date_after_build(L):
     assert build.up_to_date()
     assert os.path.exists(build.LIB)
+
+
+def _line(nz=16, n_lines=1, E=16, B=16, J=16, wp2=None, dz=0.1, dt=0.05, omega_p=0.1, z0=0.0):
+    y = _lib.ApLine1d()
+    y.E, y.B, y.J, y.wp2 = E, B, J, wp2
+    y.nz, y.n_lines, y.dz, y.dt, y.omega_p, y.z0 = nz, n_lines, dz, dt, omega_p, z0
+    return y
+
+
+@pytest.mark.parametrize("prec,max_nodes", [(0, 6144), (2, 12288)])
+def test_plasma_line_arguments_checked_on_host(L, prec, max_nodes):
+    """Validation before any launch: nothing is dereferenced (the pointers
+    here are fake addresses) and no-work calls return before CUDA."""
+    run = lambda y, n=1, p=prec: L.ap_plasma1d_run(ctypes.byref(y), n, p, None)  # noqa: E731
+    assert L.ap_plasma1d_run(None, 1, prec, None) == _lib.AP_ERR_ARG
+    assert run(_line(nz=1)) == _lib.AP_ERR_ARG
+    assert run(_line(nz=max_nodes + 1)) == _lib.AP_ERR_ARG
+    assert run(_line(dz=0.0)) == _lib.AP_ERR_ARG
+    assert run(_line(dt=float("inf"))) == _lib.AP_ERR_ARG
+    assert run(_line(omega_p=-1.0)) == _lib.AP_ERR_ARG
+    assert run(_line(z0=float("nan"))) == _lib.AP_ERR_ARG
+    assert run(_line(E=None)) == _lib.AP_ERR_ARG
+    assert run(_line(), n=-1) == _lib.AP_ERR_ARG
+    assert run(_line(), p=1) == _lib.AP_ERR_ARG        # AP_FP32_PHASE64: no line variant
+    assert run(_line(J=18)) == _lib.AP_ERR_ALIGN
+    assert run(_line(wp2=20 if prec == 0 else 22)) == _lib.AP_ERR_ALIGN
+    assert run(_line(n_lines=0, nz=max_nodes)) == _lib.AP_OK  # no work, no launch
+    assert run(_line(), n=0) == _lib.AP_OK
+    y = _line()
+    assert L.ap_apt1d_run(None, 0, ctypes.byref(y), 0.0, 1, prec, None) == _lib.AP_ERR_ARG
+
