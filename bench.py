@@ -24,6 +24,7 @@ CUDA graph plus the adjoint).
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -88,6 +89,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="wall seconds of oracle work on all host cores (cpu_baseline)")
+    ap.add_argument("--lines-only", action="store_true",
+                    help="run only the Sec. 4 lines, one split-line and one traditional-line call "
+                         "(a small case for profiling); prints their rates")
+    ap.add_argument("--split-steps", type=int, default=200)
+    ap.add_argument("--plasma-steps", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -314,6 +320,11 @@ NODE_OPS_PER_EVAL = 90  # FP32 operations of one Gaussian field evaluation with
                         # longitudinal terms (phase unit 30, envelope 2,
                         # profile + longitudinal + assembly 58), no push
 YEE_LINES, YEE_NZ, YEE_STEPS = 152, 8192, 2000
+# 1-D lines with a cold-plasma current (Sec. 4): n_e = 1e-3 n_c, a g = 4
+# super-Gaussian of tau = 30 at 20 cells per wavelength, c dt/dz = 0.9
+LINE_LINES, LINE_NZ, SPLIT_STEPS, PLASMA_STEPS = 304, 4096, 2000, 20000
+MUFU_PER_CLK = 16         # special-function operations per clock per SM (4 per sub-partition)
+SPLIT_MUFU_PER_NODE_STEP = 8  # E1: ex2, sin, cos; J1: ex2, sin, cos and the sin, cos of its phase shift
 
 
 def closed_form_rate(wl, stream, sum_rate):
@@ -391,6 +402,8 @@ def grid_node_rates(wl, stream):
     B = torch.zeros_like(E)
     E[:, YEE_NZ // 2] = 1.0
     ysec = timed(lambda: _lib.ap_yee1d_run(E, B, 0.05, 0.0475, YEE_STEPS), 2)
+    del E, B
+    lines = line_rates(SPLIT_STEPS, PLASMA_STEPS, timed)
     return {
         "eval_nodes": {"value": nodes / sec, "unit": "nodes/s", "ms": sec * 1e3,
                        "grid": "%d^3, 6 staggered components, float arrays, float-float phase" % n,
@@ -404,6 +417,51 @@ def grid_node_rates(wl, stream):
         "yee1d": {"value": YEE_LINES * YEE_NZ * YEE_STEPS / ysec, "unit": "node-steps/s",
                   "ms": ysec * 1e3, "lines": YEE_LINES, "nz": YEE_NZ, "steps": YEE_STEPS,
                   "dtype": "f32"},
+        **lines,
+    }
+
+
+def line_rates(split_steps, plasma_steps, timed=None):
+    """Rates of the Sec. 4 lines: the split line with E1, J1 evaluated in the
+    kernel every step (ap_apt1d_run) and the traditional Yee + current line
+    (ap_plasma1d_run), float, LINE_LINES x LINE_NZ.  timed(fn, reps) times
+    repetitions after a warm-up call; without it each runs once."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+
+    def once(fn, reps):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    timed = timed or once
+    wp = math.sqrt(1e-3)
+    dzl = 2.0 * math.pi / 20.0
+    dtl = 0.9 * dzl
+    sp = dict(kind="plane", pol="x", env="sgauss", sg_order=4, env_len=30.0, a0=1.0, omega_p=wp,
+              yee=True, yee_dx=dzl, yee_dt=dtl)
+    E = torch.zeros((LINE_LINES, LINE_NZ), dtype=torch.float32, device="cuda")
+    B, J = torch.zeros_like(E), torch.zeros_like(E)
+    z0 = -0.5 * LINE_NZ * dzl
+    with _lib.Handle(sp) as hs:
+        ssec = timed(lambda: hs.apt1d(E, B, J, z0, dzl, 0.0, dtl, split_steps, omega_p=wp), 2)
+        if hs.status() != 0:
+            raise RuntimeError("device status after the split line")
+    tsec = timed(lambda: _lib.ap_plasma1d_run(E, B, J, dzl, dtl, plasma_steps, omega_p=wp), 2)
+    split_rate = LINE_LINES * LINE_NZ * split_steps / ssec
+    mufu_peak = SM_COUNT * MUFU_PER_CLK * SM_MAX_MHZ * 1e6
+    return {
+        "apt1d_split": {"value": split_rate, "unit": "node-steps/s", "ms": ssec * 1e3,
+                        "lines": LINE_LINES, "nz": LINE_NZ, "steps": split_steps, "dtype": "f32",
+                        "mufu_frac": split_rate * SPLIT_MUFU_PER_NODE_STEP / mufu_peak,
+                        "mufu_per_node_step": SPLIT_MUFU_PER_NODE_STEP},
+        "plasma1d": {"value": LINE_LINES * LINE_NZ * plasma_steps / tsec, "unit": "node-steps/s",
+                     "ms": tsec * 1e3, "lines": LINE_LINES, "nz": LINE_NZ, "steps": plasma_steps,
+                     "dtype": "f32"},
     }
 
 def run_ours(args):
@@ -642,6 +700,11 @@ def main():
         from paper_2307_04843_gb300 import build
         if not build.up_to_date():
             build.build()
+        if args.lines_only:
+            import torch
+            torch.cuda.set_device(0)
+            print(json.dumps(line_rates(args.split_steps, args.plasma_steps)))
+            return
         run_ours(args)
 
 

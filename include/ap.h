@@ -248,6 +248,8 @@ typedef struct {
 
 #define AP_LINE1D_MAX_NODES_F32 12288 /* nodes per float line (the line sits in shared memory) */
 #define AP_LINE1D_MAX_NODES_F64 6144  /* nodes per double line */
+#define AP_APT1D_MAX_NODES_F32 8192   /* nodes per float line of ap_apt1d_run (it also keeps
+                                         three per-node phase constants in shared memory) */
 
 /* Launch shape, chosen by the autotuner (0 = library default). */
 typedef struct {
@@ -464,7 +466,8 @@ int ap_plasma1d_run(const ap_line1d *y, int64_t n_steps, int32_t precision, void
  * the field that the analytic pulse and current miss.  The pulse must be
  * linearly polarised along x (the line carries E_x, B_y).
  * Errors: those of ap_plasma1d_run; AP_ERR_ARG also for a bad set, a pulse
- * not polarised along x, or 2 n_steps + 1 >= 2^24 with AP_FP32_PHASEFF. */
+ * not polarised along x, and with AP_FP32_PHASEFF for 2 n_steps + 1 >= 2^24
+ * or nz above AP_APT1D_MAX_NODES_F32. */
 int ap_apt1d_run(ap_handle h, int32_t set, const ap_line1d *y, double t0, int64_t n_steps,
                  int32_t precision, void *stream);
 

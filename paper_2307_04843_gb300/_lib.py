@@ -41,6 +41,7 @@ AP_MAX_SETS = 4096
 AP_YEE1D_MAX_NODES = 12288
 AP_LINE1D_MAX_NODES_F32 = 12288
 AP_LINE1D_MAX_NODES_F64 = 6144
+AP_APT1D_MAX_NODES_F32 = 8192
 AP_ABI_VERSION = 2
 
 

@@ -889,6 +889,7 @@ int ap_apt1d_run(ap_handle h, int32_t set, const ap_line1d *y, double t0, int64_
   if (d.kind != AP_PLANE || d.pol != AP_LIN_X) return AP_ERR_ARG;
   // float-float time levels: 2 n + 1 exact in float
   if (precision == AP_FP32_PHASEFF && n_steps >= (1 << 23)) return AP_ERR_ARG;
+  if (precision == AP_FP32_PHASEFF && y && y->nz > AP_APT1D_MAX_NODES_F32) return AP_ERR_ARG;
   apt::LineArgs a;
   int rc = line_args(y, n_steps, precision, &a);
   if (rc != AP_OK) return rc;

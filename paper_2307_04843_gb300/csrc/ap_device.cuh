@@ -264,8 +264,10 @@ struct TimeBase<AP_FP32_PHASEFF> {
     T0 = split_double(t0 - pp.t_f);
     DT = split_double(dt);
   }
-  __device__ StepFF at(long long n) const {
-    const float nf = (float)n;  // exact for n < 2^24
+  __device__ StepFF at(long long n) const { return at_f((float)n); }  // exact for n < 2^24
+  // the same with the level given as a float holding an integer below 2^24
+  // (callers that count in float avoid the int-to-float conversion)
+  __device__ StepFF at_f(float nf) const {
     FF nd = two_prod(nf, del.hi);
     FF c = two_sum(om0.hi, nd.hi);
     float clo = __fadd_rn(__fadd_rn(c.lo, nd.lo), __fmaf_rn(nf, del.lo, om0.lo));

@@ -37,7 +37,40 @@ __device__ __forceinline__ float l_sub(float a, float b) { return __fsub_rn(a, b
 __device__ __forceinline__ float l_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float l_mul(float a, float b) { return __fmul_rn(a, b); }
 
-// Local coordinates of node k (x = y = 0) at one time level.
+// Float-float split line: the node-dependent part of the carrier phase,
+// k (z_k - z_f) as float-float, and z_k - z_f, computed once per launch with
+// the operations of local_coords (so the phase and envelope argument of every
+// evaluation are those of the generic path bit for bit).
+struct NodeFF {
+  float kd_hi, kd_lo, dz;
+};
+
+__device__ __forceinline__ NodeFF node_ff(const Pulse<float> &P, const LineArgs &a, float fk) {
+  const FF z = node_coord_ff(fk, a.z0_hi, a.z0_lo, a.dz_hi, a.dz_lo);
+  FF dz = two_sum(z.hi, -P.zf_hi);
+  dz.lo = __fadd_rn(dz.lo, __fsub_rn(z.lo, P.zf_lo));
+  FF kd = two_prod(P.k_hi, dz.hi);
+  kd.lo = __fadd_rn(kd.lo, __fmaf_rn(P.k_hi, dz.lo, __fmul_rn(P.k_lo, dz.hi)));
+  return {kd.hi, kd.lo, __fadd_rn(dz.hi, dz.lo)};
+}
+
+__device__ __forceinline__ Local<float> node_local_ff(const Pulse<float> &P, const StepFF &st, float kd_hi,
+                                                      float kd_lo, float dz) {
+  Local<float> L;
+  const FF ps = two_sum(st.C, -kd_hi);
+  L.psi = reduce_ff(ps.hi, __fsub_rn(ps.lo, kd_lo));
+  L.x = 0.0f;
+  L.y = 0.0f;
+  L.dz = dz;
+  const float Tf = __fadd_rn(st.Th, st.Tl);
+  L.eta = fmaf(-dz, P.inv_vg, Tf);
+  L.T = Tf;
+  L.phi_hi = 0.0f;
+  L.phi_lo = 0.0f;
+  return L;
+}
+
+// Local coordinates of node k (x = y = 0) at one time level (double).
 template <int PREC>
 __device__ __forceinline__ Local<Real<PREC>> node_local(const Pulse<Real<PREC>> &P, const LineArgs &a,
                                                         const typename TimeBase<PREC>::Step &st, int k) {
@@ -62,6 +95,11 @@ __global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant_
   T *b = e + nz;
   T *j = b + nz;
   T *q = j + nz;  // a_k = dt omega_p^2(z_k)
+  // float split line only: per-node phase constants (see NodeFF)
+  constexpr bool kFF = APT && PREC == AP_FP32_PHASEFF;
+  float *kdh = reinterpret_cast<float *>(q + nz);
+  float *kdl = kdh + nz;
+  float *dzn = kdl + nz;
   const size_t off = (size_t)blockIdx.x * (size_t)nz;
   T *Eg = static_cast<T *>(a.E) + off;
   T *Bg = static_cast<T *>(a.B) + off;
@@ -77,16 +115,27 @@ __global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant_
     b[k] = Bg[k];
     j[k] = Jg[k];
     q[k] = l_mul(dt, W ? W[k] : wpu);
+    if constexpr (kFF) {
+      const NodeFF c = node_ff(P, a, (float)k);
+      kdh[k] = c.kd_hi;
+      kdl[k] = c.kd_lo;
+      dzn[k] = c.dz;
+    }
   }
   TimeBase<PREC> tb;
   if constexpr (APT) tb.init(P, a.t0, 0.5 * a.dt);  // level 2n: t_n, 2n + 1: t_n + dt/2
+  float lev = 0.0f;  // 2n in float (exact: 2 n_steps + 1 < 2^24 is checked on the host)
   __syncthreads();
   for (long long n = 0; n < a.n_steps; ++n) {
     // B^{n+1/2} = B^n - (r/2)(E_{k+1}^n - E_k^n)
     for (int k = t; k < nz - 1; k += bd) b[k] = l_sub(b[k], l_mul(hr, l_sub(e[k + 1], e[k])));
     __syncthreads();
     typename TimeBase<PREC>::Step st_e{}, st_j{};
-    if constexpr (APT) {
+    if constexpr (kFF) {
+      st_e = tb.at_f(lev);
+      st_j = tb.at_f(lev + 1.0f);
+      lev += 2.0f;
+    } else if constexpr (APT) {
       st_e = tb.at(2 * n);
       st_j = tb.at(2 * n + 1);
     }
@@ -94,9 +143,17 @@ __global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant_
     for (int k = t; k < nz; k += bd) {
       const T ek = e[k];
       T drive = ek;
+      float c_kdh = 0.0f, c_kdl = 0.0f, c_dz = 0.0f;
+      if constexpr (kFF) {
+        c_kdh = kdh[k];
+        c_kdl = kdl[k];
+        c_dz = dzn[k];
+      }
       if constexpr (APT) {
         R E1[3], B1[3];
-        const Local<R> L = node_local<PREC>(P, a, st_e, k);
+        Local<R> L;
+        if constexpr (kFF) L = node_local_ff(P, st_e, c_kdh, c_kdl, c_dz);
+        else L = node_local<PREC>(P, a, st_e, k);
         analytic_fields<AP_PLANE, PREC>(P, L, E1, B1);
         drive = l_add((T)E1[0], ek);
       }
@@ -106,7 +163,9 @@ __global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant_
         T src = jk;
         if constexpr (APT) {
           R J1[3];
-          const Local<R> L = node_local<PREC>(P, a, st_j, k);
+          Local<R> L;
+          if constexpr (kFF) L = node_local_ff(P, st_j, c_kdh, c_kdl, c_dz);
+          else L = node_local<PREC>(P, a, st_j, k);
           current_plane(P, L, J1);
           src = l_sub(jk, (T)J1[0]);
         }
@@ -128,7 +187,8 @@ __global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant_
 template <typename T, int PREC, bool APT>
 int launch_line_t(const Pulse<Real<PREC>> &P, const LineArgs &a, void *stream) {
   auto kern = line_kernel<T, PREC, APT>;
-  const size_t smem = 4u * sizeof(T) * (size_t)a.nz;
+  const size_t per_node = 4u * sizeof(T) + ((APT && PREC == AP_FP32_PHASEFF) ? 3u * sizeof(float) : 0u);
+  const size_t smem = per_node * (size_t)a.nz;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return AP_ERR_CUDA;
   int block = (a.nz + 31) / 32 * 32;
