@@ -323,7 +323,6 @@ YEE_LINES, YEE_NZ, YEE_STEPS = 152, 8192, 2000
 # 1-D lines with a cold-plasma current (Sec. 4): n_e = 1e-3 n_c, a g = 4
 # super-Gaussian of tau = 30 at 20 cells per wavelength, c dt/dz = 0.9
 LINE_LINES, LINE_NZ, SPLIT_STEPS, PLASMA_STEPS = 304, 4096, 2000, 20000
-MUFU_PER_CLK = 16         # special-function operations per clock per SM (4 per sub-partition)
 SPLIT_MUFU_PER_NODE_STEP = 8  # E1: ex2, sin, cos; J1: ex2, sin, cos and the sin, cos of its phase shift
 
 
@@ -453,7 +452,7 @@ def line_rates(split_steps, plasma_steps, timed=None):
             raise RuntimeError("device status after the split line")
     tsec = timed(lambda: _lib.ap_plasma1d_run(E, B, J, dzl, dtl, plasma_steps, omega_p=wp), 2)
     split_rate = LINE_LINES * LINE_NZ * split_steps / ssec
-    mufu_peak = SM_COUNT * MUFU_PER_CLK * SM_MAX_MHZ * 1e6
+    mufu_peak = SM_COUNT * MUFU_LANES * SM_MAX_MHZ * 1e6
     return {
         "apt1d_split": {"value": split_rate, "unit": "node-steps/s", "ms": ssec * 1e3,
                         "lines": LINE_LINES, "nz": LINE_NZ, "steps": split_steps, "dtype": "f32",

@@ -313,3 +313,62 @@ def test_split_vs_traditional_on_gpu_matches_oracle():
         # near the peak the split form agrees with the traditional line to
         # well below the field (a0 = 1); E2 stays small everywhere
         assert gpu[0] < 50 * wp2 * 1e-2 and gpu[1] < 2 * wp2
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,nz", [("fp32", 8192), ("fp64", 6144)])
+def test_split_line_at_maximum_length(precision, nz):
+    """The longest split lines (float: 28 B of shared memory per node, 229 KB;
+    double: 32 B per node) against the oracle; one node more is refused."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    wp = 0.2
+    pulse = _pulse(wp, env_len=40.0, phase0=0.5)
+    dz, dt = pulse["yee_dx"], pulse["yee_dt"]
+    z0, n = -0.5 * nz * dz, 12
+    ref = _oracle_split(pulse, nz, z0, n, wp * wp)
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    with _lib.Handle(pulse) as h:
+        _, _, J = _gpu_initial(h, nz, z0, dz, dt, dtype)
+        E2 = torch.zeros(nz, dtype=dtype, device="cuda")
+        B2 = torch.zeros_like(E2)
+        h.apt1d(E2, B2, J, z0, dz, 0.0, dt, n, omega_p=wp)
+        assert h.status() == 0
+        big = torch.zeros(nz + 1, dtype=dtype, device="cuda")
+        with pytest.raises(_lib.APError) as e:
+            h.apt1d(big, big.clone(), big.clone(), z0, dz, 0.0, dt, 1, omega_p=wp)
+        assert e.value.status == _lib.AP_ERR_ARG
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    for got, want in zip((E2, B2, J), ref):
+        assert np.max(np.abs(_host(got) - want)) <= tol
+    assert np.max(np.abs(ref[2])) > 0.01
+
+
+@pytest.mark.gpu
+def test_split_line_bench_configuration_sampled():
+    """The bench's split-line call (304 float lines x 4096 nodes x 2000
+    steps, E2 = B2 = J = 0 on entry, uniform plasma): every line is the same
+    problem, so all lines come out bit-identical, and one line matches the
+    oracle's run of the same call."""
+    import torch
+    import bench
+    from paper_2307_04843_gb300 import _lib
+    wp = math.sqrt(1e-3)
+    dzl = 2.0 * math.pi / 20.0
+    dtl = 0.9 * dzl
+    sp = dict(kind="plane", pol="x", env="sgauss", sg_order=4, env_len=30.0, a0=1.0, omega_p=wp,
+              yee=True, yee_dx=dzl, yee_dt=dtl)
+    nl, nz, n = bench.LINE_LINES, bench.LINE_NZ, bench.SPLIT_STEPS
+    z0 = -0.5 * nz * dzl
+    E = torch.zeros((nl, nz), dtype=torch.float32, device="cuda")
+    B, J = torch.zeros_like(E), torch.zeros_like(E)
+    with _lib.Handle(sp) as h:
+        h.apt1d(E, B, J, z0, dzl, 0.0, dtl, n, omega_p=wp)
+        assert h.status() == 0
+    for t in (E, B, J):
+        assert torch.equal(t, t[0:1].expand_as(t))
+    ref = oracle.apt1d(sp, np.zeros(nz), np.zeros(nz), np.zeros(nz), wp * wp, z0, dzl, 0.0, dtl, n)
+    scale = np.max(np.abs(ref[0]))
+    assert scale > 1e-4
+    for got, want in zip((E[0], B[0], J[0]), ref):
+        assert np.max(np.abs(_host(got) - want)) <= 1e-5 + 1e-3 * np.max(np.abs(want))
