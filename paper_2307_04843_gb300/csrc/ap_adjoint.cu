@@ -45,8 +45,10 @@ constexpr int kNp = 4;   // parameters: a0, w0, z_f, beta_f
 // for the closed-form flying focus, the beta_f-dependent ones (slot 4).
 template <typename R, int NT>
 struct PulseAD {
-  int32_t kind, pol, env, lon, lg_p, lg_al, lg_sgn, sg_order;
+  static constexpr bool kHasPlasma = true;
+  int32_t kind, pol, env, lon, lg_p, lg_al, lg_sgn, sg_order, plasma;
   R amp, bratio, lonE, lonB, env_a, env_b, px_re, px_im, py_re, py_im;
+  R fdc, inv_w, lg_c1, lg_c2;  // plane wave in a plasma (Sec. 4, Eq. b_corr_t)
   R lg_r[6][kLgMaxP];
   Dual<R, NT> inv_w0sq, inv_zR, lg_pref, beta_f;
 };
@@ -57,6 +59,7 @@ __device__ __forceinline__ PulseAD<R, NT> make_ad(const Pulse<R> &P) {
   PulseAD<R, NT> A;
   A.kind = P.kind; A.pol = P.pol; A.env = P.env; A.lon = P.lon;
   A.lg_p = P.lg_p; A.lg_al = P.lg_al; A.lg_sgn = P.lg_sgn; A.sg_order = P.sg_order;
+  A.plasma = P.plasma; A.fdc = P.fdc; A.inv_w = P.inv_w; A.lg_c1 = P.lg_c1; A.lg_c2 = P.lg_c2;
   A.amp = P.amp_unit;  // unit a0: the physical field is a0 times this one
   A.bratio = P.bratio; A.lonE = P.lonE; A.lonB = P.lonB;
   A.env_a = P.env_a; A.env_b = P.env_b;
@@ -507,7 +510,6 @@ int ap_push_adjoint(ap_handle h, const ap_particles *p0, const ap_grid *g, doubl
   if (objective != AP_OBJ_MEAN_GAMMA) return AP_ERR_ARG;
   if (precision != AP_FP64 && precision != AP_FP32_PHASEFF) return AP_ERR_UNSUPPORTED;
   if (uk < 0 || uk == AP_FLYING_SUM) return AP_ERR_UNSUPPORTED;
-  if (apt::handle_any_plasma(h)) return AP_ERR_UNSUPPORTED;
   if (n_steps < 1 || ckpt_every < 1 || ckpt_every > apt::kAdjMaxK) return AP_ERR_ARG;
   if (p0->set_offsets ? p0->n_sets != ns : ns != 1) return AP_ERR_ARG;
   const size_t need = ap_adjoint_workspace_bytes(h, p0->n, n_steps, ckpt_every);

@@ -509,13 +509,6 @@ int handle_info(ap_handle h, int *device, int *sm_count, int *n_sets, int *unifo
   return AP_OK;
 }
 
-int handle_any_plasma(ap_handle h) {
-  if (!h) return 0;
-  for (const auto &d : h->descs)
-    if (d.omega_p > 0.0) return 1;
-  return 0;
-}
-
 int handle_push_args(ap_handle h, const ap_particles *p, const ap_grid *g, double t0, double dt,
                      int64_t n_steps, int32_t precision, PushArgs *a, void *stream) {
   return fill_push_args(h, p, g, t0, dt, n_steps, precision, nullptr, 1, *a, stream);

@@ -465,8 +465,8 @@ __device__ __forceinline__ void envelope_logd(const PT &P, R eta, R &L1, R &L2) 
 // A = 1 - w L2/omega^2 + th^2/2, th = w L1/omega (Eqs. j1 and b_corr_t with
 // Phi = 0; w = 1 for J1, w = 1 - v_phi/v_g for B), applied to U as
 // A U e^{i th}.
-template <typename R>
-__device__ __forceinline__ Cx<R> finite_duration(Cx<R> U, R w, R L1, R L2, R inv_w) {
+template <typename R, typename S>
+__device__ __forceinline__ Cx<R> finite_duration(Cx<R> U, S w, R L1, R L2, S inv_w) {
   const R th = w * L1 * inv_w;
   const R A = R(1) - w * L2 * inv_w * inv_w + R(0.5) * th * th;
   R s, c;
@@ -487,7 +487,7 @@ __device__ __forceinline__ void fields_plane(const PT &P, const Local<R> &L, R E
   sincos_r(L.psi, &s, &c);
   Cx<R> U{a * c, a * s};
   finish_beam(P, L.x, L.y, U, U, R(0), false, E, B);
-  if constexpr (std::is_same<PT, Pulse<R>>::value) {
+  if constexpr (PT::kHasPlasma) {
     if (P.plasma) {
       R L1, L2, Et[3];
       envelope_logd(P, L.eta, L1, L2);
@@ -510,7 +510,7 @@ __device__ __forceinline__ void current_plane(const Pulse<R> &P, const Local<R> 
   sincos_r(L.psi, &s, &c);
   R L1, L2;
   envelope_logd(P, L.eta, L1, L2);
-  const Cx<R> V = finite_duration(Cx<R>{a * c, a * s}, R(1), L1, L2, P.inv_w);
+  const Cx<R> V = finite_duration(Cx<R>{a * c, a * s}, R(1), L1, L2, R(P.inv_w));
   // Re[p (-i V)] with -i V = (V.im, -V.re)
   J[0] = P.px_re * V.im + P.px_im * V.re;
   J[1] = P.py_re * V.im + P.py_im * V.re;

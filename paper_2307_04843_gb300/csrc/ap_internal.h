@@ -31,6 +31,7 @@ struct Comp {
 // and rounded once to the arithmetic type R of the push.
 template <typename R>
 struct Pulse {
+  static constexpr bool kHasPlasma = true;  // carries the Sec. 4 plasma constants
   int32_t kind, pol, env, lon;
   int32_t lg_p, lg_al, lg_sgn, n_comp;
   int32_t sg_order, yee, plasma, pad1;
@@ -149,8 +150,6 @@ struct LineArgs {
   float z0_hi, z0_lo, dz_hi, dz_lo;  // float-float node positions (AP_FP32_PHASEFF)
   long long n_steps;
 };
-// Nonzero if any set of the handle is a plasma pulse (Sec. 4).
-int handle_any_plasma(ap_handle h);
 int launch_line(bool apt, int precision, const Pulse<double> &pd, const Pulse<float> &pf,
                 const LineArgs &a, void *stream);
 

@@ -144,6 +144,15 @@ def test_eval_current_and_corrected_b_on_nodes_match_oracle():
                 for c in range(3):
                     want = np.broadcast_to(Jref[c][:, None, None], shape)
                     assert np.max(np.abs(_host(J[c]) - want)) <= tol * pulse["a0"], (prec, c)
+                # accumulate: added to what the arrays hold (J - J1 with a sign flip
+                # is how a caller forms the source of E2)
+                prior = np.random.default_rng(5).standard_normal((3,) + shape)
+                J = [_cuda(prior[c], dtype) for c in range(3)]
+                h.eval_current(J, lo, d, t, accumulate=True, precision=prec)
+                held = prior.astype(np.float32 if prec == "fp32" else np.float64).astype(np.float64)
+                for c in range(3):
+                    want = held[c] + np.broadcast_to(Jref[c][:, None, None], shape)
+                    assert np.max(np.abs(_host(J[c]) - want)) <= tol * pulse["a0"] + 1e-6, (prec, c)
                 assert h.status() == 0
         assert np.max(np.abs(Jref)) > 0.02
     # J1 of a vacuum pulse is zero; J1 only for plane waves
@@ -253,14 +262,34 @@ def test_push_in_plasma_pulse_matches_oracle(precision):
     else:
         assert np.median(e) <= 1e-4 and np.max(e) <= 1e-3
     assert np.max(np.abs(ref["ux"])) > 0.3
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adjoint_in_plasma_pulse_vs_oracle_fd(precision):
+    """Gradients of the mean final gamma with respect to a0 and z_f for a
+    plasma pulse (the corrected B of Eq. b_corr_t enters through the dual
+    field evaluation), against the oracle's finite differences."""
     import torch
-    dev = _lib.to_device({k: v[:32] for k, v in parts.items()}, "fp32")
-    with _lib.Handle(pulse) as h:  # the adjoint does not cover plasma pulses
-        dJ = torch.zeros((1, 4), dtype=torch.float64, device="cuda")
-        ws = torch.zeros(1 << 20, dtype=torch.float32, device="cuda")
-        with pytest.raises(_lib.APError) as e:
-            _lib.ap_push_adjoint(h.h, dev, None, None, 0.0, 0.02, 10, 5, "fp32", dJ, None, ws)
-        assert e.value.status == _lib.AP_ERR_UNSUPPORTED
+    from paper_2307_04843_gb300.autograd import adjoint
+    from paper_2307_04843_gb300 import _lib
+    pulse = dict(kind="plane", pol="x", env="sgauss", sg_order=2, env_len=12.0, a0=1.5, omega_p=0.4,
+                 z_focus=1.0, t_focus=10.0)
+    rng = np.random.default_rng(23)
+    n = 24
+    parts = dict(x=rng.uniform(-1, 1, n), y=rng.uniform(-1, 1, n), z=rng.uniform(-1, 1, n) * L,
+                 ux=np.zeros(n), uy=np.zeros(n), uz=np.zeros(n))
+    t0, dt, n_steps, K = 0.0, 0.02, 1200, 128
+    dev = _lib.to_device(parts, precision)
+    d_off = torch.as_tensor(np.array([0, n], dtype=np.int64)).cuda()
+    J, dJ = adjoint([pulse], dev, d_off, t0, dt, n_steps, ckpt_every=K, precision=precision)
+    dJ = dJ.cpu().numpy()
+    g = oracle.grad_fd(pulse, parts, t0, dt, n_steps, names=("a0", "z_focus"), rel_h=1e-4,
+                       scale=dict(z_focus=L))
+    for k, name in ((0, "a0"), (2, "z_focus")):
+        assert abs(dJ[0, k] - g[name]) <= 1e-3 * max(abs(g[name]), 1e-8), (precision, name, dJ[0, k], g[name])
+    assert dJ[0, 1] == 0.0 and dJ[0, 3] == 0.0  # no w0, no beta_f in a plane wave
+    assert abs(g["a0"]) > 1e-3
 
 
 def split_vs_traditional(ppl, wp2, tau=30.0, g=4, dist=20.0, cr=0.95, gpu=True):
