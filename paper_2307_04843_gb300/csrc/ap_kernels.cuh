@@ -478,18 +478,62 @@ int launch_eval_t(const Pulse<Real<PREC>> &P, const EvalArgs &a, void *stream) {
   return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }
 
-// Plane waves (Eqs. plane_func, plane_b) depend on z and t only: one field
-// evaluation per row of nx nodes (every lane of the row's warp computes the
-// same value), then the warp streams it along the row, so for nx >= 32 the
-// kernel is bound by the stores, not the arithmetic.
+// One warp writes the value v along a row of n elements (store, or add to
+// what the row holds, rounding once to T): a scalar head up to the first
+// 16-byte boundary, then 16-byte vector stores, then a scalar tail.  The row
+// is aligned to sizeof(T) (checked on the host), so the head is at most
+// 16 / sizeof(T) - 1 elements.
+template <typename T, typename W>
+__device__ __forceinline__ void row_put(T *__restrict__ row, int n, W v, bool acc, int lane) {
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int kVe = 16 / (int)sizeof(T);
+  int head = (int)(((16u - ((unsigned)reinterpret_cast<uintptr_t>(row) & 15u)) & 15u) / sizeof(T));
+  if (head > n) head = n;
+  const int nv = (n - head) / kVe;
+  const int tail = head + nv * kVe;
+  V *rv = reinterpret_cast<V *>(row + head);
+  // two separate loops: the store path must not read the row
+  if (acc) {
+    if (lane < head) row[lane] = (T)((W)row[lane] + v);
+    for (int i = lane; i < nv; i += 32) {
+      V x = rv[i];
+      if constexpr (sizeof(T) == 4) {
+        x.x = (T)((W)x.x + v); x.y = (T)((W)x.y + v); x.z = (T)((W)x.z + v); x.w = (T)((W)x.w + v);
+      } else {
+        x.x = (T)((W)x.x + v); x.y = (T)((W)x.y + v);
+      }
+      rv[i] = x;
+    }
+    for (int i = tail + lane; i < n; i += 32) row[i] = (T)((W)row[i] + v);
+  } else {
+    const T vt = (T)v;
+    V x;
+    if constexpr (sizeof(T) == 4) x = make_float4(vt, vt, vt, vt);
+    else x = make_double2(vt, vt);
+    if (lane < head) row[lane] = vt;
+    for (int i = lane; i < nv; i += 32) rv[i] = x;
+    for (int i = tail + lane; i < n; i += 32) row[i] = vt;
+  }
+}
+
+// Plane waves (Eqs. plane_func, plane_b) depend on z and t only.  A row of
+// nx nodes (fixed y, z) holds two z positions: the whole node z_k (Ex, Ey,
+// Bz) and the half node z_k + dz/2 (Ez, Bx, By).  One warp per row
+// evaluates the field once at each position it needs (every lane computes
+// the same value), then streams each requested component along its row with
+// 16-byte stores, so for nx >= 32 the kernel is bound by the stores, not the
+// arithmetic.
 template <int PREC, typename T>
 __global__ void __launch_bounds__(256) nodes_plane_kernel(const __grid_constant__ Pulse<Real<PREC>> P,
                                                           const __grid_constant__ NodeArgs a) {
   using R = Real<PREC>;
   using W = typename std::conditional<(sizeof(T) > sizeof(R)), T, R>::type;
-  const int c = a.comp[blockIdx.y];
-  T *__restrict__ f = static_cast<T *>(a.f[c]);
-  const float oz = (c == 2 || c == 3 || c == 4) ? 0.5f : 0.0f;
+  bool need[2] = {false, false};  // whole, half
+  for (int i = 0; i < a.n_comp; ++i) {
+    const int c = a.comp[i];
+    if (c == 2 || c == 3 || c == 4) need[1] = true;
+    else need[0] = true;
+  }
   const long long rows = (long long)a.ny * a.nz;
   const int lane = threadIdx.x & 31;
   const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -498,20 +542,37 @@ __global__ void __launch_bounds__(256) nodes_plane_kernel(const __grid_constant_
   const typename TimeBase<PREC>::Step st = tb.at(0);
   for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
     const int k = (int)(r / a.ny);
-    Pos<PREC> pos;
-    if constexpr (PREC == AP_FP32_PHASEFF) {
-      pos.x = FF{0.0f, 0.0f};
-      pos.y = FF{0.0f, 0.0f};
-      pos.z = node_coord_ff((float)k + oz, a.lo_hi[2], a.lo_lo[2], a.d_hi[2], a.d_lo[2]);
-    } else {
-      pos.load(0.0, 0.0, fma((double)k + oz, a.d[2], a.lo[2]));
+    R v[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!need[h]) continue;
+      const float oz = h ? 0.5f : 0.0f;
+      Pos<PREC> pos;
+      if constexpr (PREC == AP_FP32_PHASEFF) {
+        pos.x = FF{0.0f, 0.0f};
+        pos.y = FF{0.0f, 0.0f};
+        pos.z = node_coord_ff((float)k + oz, a.lo_hi[2], a.lo_lo[2], a.d_hi[2], a.d_lo[2]);
+      } else {
+        pos.load(0.0, 0.0, fma((double)k + oz, a.d[2], a.lo[2]));
+      }
+      Local<R> L = local_coords<PREC>(P, st, pos);
+      R E[3], B[3];
+      node_values<AP_PLANE, PREC>(P, L, a.current, E, B);
+      if (h == 0) {
+        v[0] = E[0];
+        v[1] = E[1];
+        v[5] = B[2];
+      } else {
+        v[2] = E[2];
+        v[3] = B[0];
+        v[4] = B[1];
+      }
     }
-    Local<R> L = local_coords<PREC>(P, st, pos);
-    R E[3], B[3];
-    node_values<AP_PLANE, PREC>(P, L, a.current, E, B);
-    const R v = c == 0 ? E[0] : c == 1 ? E[1] : c == 2 ? E[2] : c == 3 ? B[0] : c == 4 ? B[1] : B[2];
-    T *row = f + r * a.nx;
-    for (int i = lane; i < a.nx; i += 32) row[i] = a.accumulate ? (T)((W)row[i] + (W)v) : (T)v;
+    for (int i = 0; i < a.n_comp; ++i) {
+      const int c = a.comp[i];
+      const R val = c == 0 ? v[0] : c == 1 ? v[1] : c == 2 ? v[2] : c == 3 ? v[3] : c == 4 ? v[4] : v[5];
+      row_put<T, W>(static_cast<T *>(a.f[c]) + r * a.nx, a.nx, (W)val, a.accumulate != 0, lane);
+    }
   }
 }
 
@@ -522,11 +583,11 @@ int launch_nodes_t(const Pulse<Real<PREC>> &P, const NodeArgs &a, void *stream) 
   if constexpr (KIND == AP_PLANE) {
     if (a.nx >= 32) {
       const long long rows = (long long)a.ny * a.nz;
-      long long gx = (rows + 7) / 8;  // 8 warps (rows) per block
-      long long cap = ((long long)a.sm_count * 8 + a.n_comp - 1) / a.n_comp;
+      long long gx = (rows + 7) / 8;  // 8 warps (rows) per block, every component of a row
+      const long long cap = (long long)a.sm_count * 8;
       if (gx > cap) gx = cap;
       if (gx < 1) gx = 1;
-      const dim3 grid((unsigned)gx, (unsigned)a.n_comp);
+      const dim3 grid((unsigned)gx, 1u);
       cudaStream_t s = static_cast<cudaStream_t>(stream);
       if (a.f64) nodes_plane_kernel<PREC, double><<<grid, block, 0, s>>>(P, a);
       else nodes_plane_kernel<PREC, float><<<grid, block, 0, s>>>(P, a);
