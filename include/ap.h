@@ -445,7 +445,9 @@ int ap_yee1d_run(const ap_yee1d *y, int64_t n_steps, int32_t precision, void *st
  * E[0] and B[nz-1] are held fixed.  Each product, sum and difference is
  * rounded separately in the stated order (no fused multiply-add); with
  * wp2 = 0 the result is that of ap_yee1d_run bit for bit.  All steps run in
- * one launch, one block per line with the line in shared memory.
+ * one launch, one block per line with the line on chip: float lines of up
+ * to 6144 nodes in registers (a few consecutive nodes per thread), longer
+ * float lines and double lines in shared memory.
  * Errors: AP_ERR_ARG (nz < 2 or above AP_LINE1D_MAX_NODES_F32/_F64,
  * n_lines < 0, n_steps < 0, NULL arrays, non-finite or non-positive dz, dt,
  * negative or non-finite omega_p), AP_ERR_ALIGN, AP_ERR_CUDA. */

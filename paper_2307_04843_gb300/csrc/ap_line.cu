@@ -184,6 +184,91 @@ __global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant_
   }
 }
 
+// Traditional line with the line in registers: thread t owns the C
+// consecutive nodes [t C, t C + C) of E, B, J and a_k; per step only the
+// values at thread boundaries move through shared memory, with two
+// barriers: (1) B half step (needs E at the next thread's first node, `en`),
+// publish the last B; barrier; (2) current and E update (needs B at the
+// previous thread's last node), publish the first E; barrier; (3) B half
+// step with the fresh `en`.  Each shared slot is written and read in
+// alternate barrier intervals.  The arithmetic per node is that of
+// line_kernel, so the result does not depend on C or the block size.
+template <typename T, int C, int MAXT>
+__global__ void __launch_bounds__(MAXT) plasma_line_reg_kernel(const __grid_constant__ LineArgs a) {
+  __shared__ T s_b[kLineBlock], s_e[kLineBlock];
+  const int nz = a.nz;
+  const size_t off = (size_t)blockIdx.x * (size_t)nz;
+  T *Eg = static_cast<T *>(a.E) + off;
+  T *Bg = static_cast<T *>(a.B) + off;
+  T *Jg = static_cast<T *>(a.J) + off;
+  const T *W = a.wp2 ? static_cast<const T *>(a.wp2) + off : nullptr;
+  const T dt = (T)a.dt;
+  const T r = (T)(a.dt / a.dz);
+  const T hr = (T)(0.5 * (a.dt / a.dz));
+  const T wpu = (T)a.omega_p2;
+  const int t = threadIdx.x;
+  const int base = t * C;
+  T e[C], b[C], j[C], q[C];
+#pragma unroll
+  for (int i = 0; i < C; ++i) {
+    const int k = base + i;
+    const bool in = k < nz;
+    e[i] = in ? Eg[k] : T(0);
+    b[i] = in ? Bg[k] : T(0);
+    j[i] = in ? Jg[k] : T(0);
+    q[i] = in ? l_mul(dt, W ? W[k] : wpu) : T(0);
+  }
+  s_e[t] = e[0];
+  __syncthreads();
+  T en = t + 1 < (int)blockDim.x ? s_e[t + 1] : T(0);
+  for (long long n = 0; n < a.n_steps; ++n) {
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+      const T enx = i + 1 < C ? e[i + 1] : en;
+      if (base + i < nz - 1) b[i] = l_sub(b[i], l_mul(hr, l_sub(enx, e[i])));
+    }
+    s_b[t] = b[C - 1];
+    __syncthreads();
+    const T bp = t > 0 ? s_b[t - 1] : T(0);
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+      const int k = base + i;
+      if (k < nz) {
+        j[i] = l_add(j[i], l_mul(q[i], e[i]));
+        if (k >= 1) {
+          const T bpv = i > 0 ? b[i - 1] : bp;
+          e[i] = l_sub(l_sub(e[i], l_mul(r, l_sub(b[i], bpv))), l_mul(dt, j[i]));
+        }
+      }
+    }
+    s_e[t] = e[0];
+    __syncthreads();
+    en = t + 1 < (int)blockDim.x ? s_e[t + 1] : T(0);
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+      const T enx = i + 1 < C ? e[i + 1] : en;
+      if (base + i < nz - 1) b[i] = l_sub(b[i], l_mul(hr, l_sub(enx, e[i])));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < C; ++i) {
+    const int k = base + i;
+    if (k < nz) {
+      Eg[k] = e[i];
+      Bg[k] = b[i];
+      Jg[k] = j[i];
+    }
+  }
+}
+
+template <typename T, int C, int MAXT>
+int launch_plasma_reg(const LineArgs &a, void *stream) {
+  const int block = ((a.nz + C - 1) / C + 31) / 32 * 32;
+  if (block > MAXT) return AP_ERR_ARG;
+  plasma_line_reg_kernel<T, C, MAXT><<<(unsigned)a.n_lines, block, 0, static_cast<cudaStream_t>(stream)>>>(a);
+  return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+}
+
 template <typename T, int PREC, bool APT>
 int launch_line_t(const Pulse<Real<PREC>> &P, const LineArgs &a, void *stream) {
   auto kern = line_kernel<T, PREC, APT>;
@@ -201,6 +286,13 @@ int launch_line_t(const Pulse<Real<PREC>> &P, const LineArgs &a, void *stream) {
 
 int launch_line(bool apt_mode, int precision, const Pulse<double> &pd, const Pulse<float> &pf,
                 const LineArgs &a, void *stream) {
+  // traditional float lines up to 8 x 768 nodes: the line in registers
+  if (!apt_mode && precision != AP_FP64) {
+    if (a.nz <= kLineBlock) return launch_plasma_reg<float, 1, kLineBlock>(a, stream);
+    if (a.nz <= 2 * kLineBlock) return launch_plasma_reg<float, 2, kLineBlock>(a, stream);
+    if (a.nz <= 4 * kLineBlock) return launch_plasma_reg<float, 4, kLineBlock>(a, stream);
+    if (a.nz <= 8 * 768) return launch_plasma_reg<float, 8, 768>(a, stream);
+  }
   if (precision == AP_FP64)
     return apt_mode ? launch_line_t<double, AP_FP64, true>(pd, a, stream)
                     : launch_line_t<double, AP_FP64, false>(pd, a, stream);

@@ -401,3 +401,22 @@ def test_split_line_bench_configuration_sampled():
     assert scale > 1e-4
     for got, want in zip((E[0], B[0], J[0]), ref):
         assert np.max(np.abs(_host(got) - want)) <= 1e-5 + 1e-3 * np.max(np.abs(want))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("nz", [999, 2000, 4000, 6144, 6145, 9001])
+def test_plasma_line_fp32_every_blocking(nz):
+    """Float lines take the register-blocked kernel with 1, 2, 4 or 8 nodes
+    per thread up to 6144 nodes and the shared-memory kernel beyond: every
+    one equals the float32 replica bit for bit, with per-node plasma."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    rng = np.random.default_rng(nz)
+    E, B, J = (rng.standard_normal((2, nz)).astype(np.float32) for _ in range(3))
+    wp2 = rng.uniform(0.0, 0.2, (2, nz)).astype(np.float32)
+    e, b, j, w = (_cuda(a, torch.float32) for a in (E, B, J, wp2))
+    _lib.ap_plasma1d_run(e, b, j, 0.05, 0.045, 60, wp2=w)
+    for l in range(2):
+        Er, Br, Jr = _float32_line(E[l], B[l], J[l], wp2[l], 0.05, 0.045, 60)
+        assert np.array_equal(e[l].cpu().numpy(), Er) and np.array_equal(b[l].cpu().numpy(), Br)
+        assert np.array_equal(j[l].cpu().numpy(), Jr)
