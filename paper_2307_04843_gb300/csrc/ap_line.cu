@@ -11,7 +11,9 @@
 //     evaluated in the kernel every step (Eqs. E_1_j, E_2_j, j1).
 //
 // One block per line; the line (E, B, J and a_k = dt omega_p^2(z_k)) stays
-// in shared memory for all n_steps and is written back once.  Per step: the
+// on chip for all n_steps and is written back once: in registers for the
+// traditional float line up to 6144 nodes (plasma_line_reg_kernel), in
+// shared memory otherwise (line_kernel).  Per step of line_kernel: the
 // B half step; a barrier; the current and E update of each node (one pass:
 // both read only the node's own E and J and the neighbouring B); a barrier;
 // the second B half step.  The second B half step and the next step's first
