@@ -49,6 +49,7 @@ struct PulseAD {
   int32_t kind, pol, env, lon, lg_p, lg_al, lg_sgn, sg_order, plasma;
   R amp, bratio, lonE, lonB, env_a, env_b, px_re, px_im, py_re, py_im;
   R fdc, inv_w, lg_c1, lg_c2;  // plane wave in a plasma (Sec. 4, Eq. b_corr_t)
+  R lg_alf;                    // |l| as a number
   R lg_r[6][kLgMaxP];
   Dual<R, NT> inv_w0sq, inv_zR, lg_pref, beta_f;
 };
@@ -60,6 +61,7 @@ __device__ __forceinline__ PulseAD<R, NT> make_ad(const Pulse<R> &P) {
   A.kind = P.kind; A.pol = P.pol; A.env = P.env; A.lon = P.lon;
   A.lg_p = P.lg_p; A.lg_al = P.lg_al; A.lg_sgn = P.lg_sgn; A.sg_order = P.sg_order;
   A.plasma = P.plasma; A.fdc = P.fdc; A.inv_w = P.inv_w; A.lg_c1 = P.lg_c1; A.lg_c2 = P.lg_c2;
+  A.lg_alf = P.lg_alf;
   A.amp = P.amp_unit;  // unit a0: the physical field is a0 times this one
   A.bratio = P.bratio; A.lonE = P.lonE; A.lonB = P.lonB;
   A.env_a = P.env_a; A.env_b = P.env_b;

@@ -254,6 +254,7 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
     const int a = d.lg_l < 0 ? -d.lg_l : d.lg_l;
     P.lg_p = d.lg_p;
     P.lg_al = a;
+    P.lg_alf = (double)a;
     P.lg_sgn = d.lg_l < 0 ? -1 : 1;
     for (int k = 0; k < apt::kLgMaxP; ++k) {
       const double k1 = (double)(k + 1);
@@ -333,6 +334,7 @@ void derive(const ap_pulse_desc &d, Pulse<double> &P, Pulse<float> &F) {
   for (int r = 0; r < 6; ++r)
     for (int k = 0; k < apt::kLgMaxP; ++k) F.lg_r[r][k] = (float)P.lg_r[r][k];
   F.lg_pref = (float)P.lg_pref;
+  F.lg_alf = (float)P.lg_alf;
   F.beta_f = (float)P.beta_f;
   F.adv_xy = (float)P.adv_xy;
   F.inv_1mb = (float)P.inv_1mb;

@@ -554,36 +554,36 @@ __device__ __forceinline__ void fields_lg(const PT &P, const Local<R> &L, R E[3]
   Cx<R> q{inv, zeta * inv};
   R a = (L.x * L.x + L.y * L.y) * P.inv_w0sq;
   R s = R(2) * a * q.re;
-  // L_p^{|l|}(s) and dL/ds = -L_{p-1}^{|l|+1}(s) by the three-term recurrence,
-  // which stays accurate where the monomial sum cancels (large s, large p)
-  R Lp = R(1), Lm = R(0);
+  // Two loops with run-time trip counts instead of five (each iteration of a
+  // loop costs a branch and its bookkeeping every step):
+  // over k < p: L_p^{|l|}(s) and dL/ds = -L_{p-1}^{|l|+1}(s) by the
+  // three-term recurrence (accurate where the monomial sum cancels: large s,
+  // large p), and g^p with g = q/q*;
+  // over i < |l|: (x + i sgn y)^{|l|}, its (|l| - 1)th power, and q^{|l|+1}.
+  Cx<R> g{(R(1) - zeta * zeta) * inv, R(2) * zeta * inv};
+  R Lp = R(1), Lm = R(0), Dp = R(1), Dm = R(0);
+  Cx<R> gp{R(1), R(0)};
   for (int k = 0; k < P.lg_p; ++k) {
-    R Ln = fma(fma(-P.lg_r[1][k], s, P.lg_r[0][k]), Lp, -P.lg_r[2][k] * Lm);
+    const R Ln = fma(fma(-P.lg_r[1][k], s, P.lg_r[0][k]), Lp, -P.lg_r[2][k] * Lm);
     Lm = Lp;
     Lp = Ln;
-  }
-  R dL = R(0);
-  if (P.lon && P.lg_p > 0) {
-    R Dp = R(1), Dm = R(0);
-    for (int k = 0; k + 1 < P.lg_p; ++k) {
-      R Dn = fma(fma(-P.lg_r[4][k], s, P.lg_r[3][k]), Dp, -P.lg_r[5][k] * Dm);
+    if (k + 1 < P.lg_p) {
+      const R Dn = fma(fma(-P.lg_r[4][k], s, P.lg_r[3][k]), Dp, -P.lg_r[5][k] * Dm);
       Dm = Dp;
       Dp = Dn;
     }
-    dL = -Dp;
+    gp = cmul(gp, g);
   }
-  // (x + i sgn y)^{|l|} and its (|l| - 1)th power
+  const R dL = P.lg_p > 0 ? -Dp : R(0);
   Cx<R> xi{L.x, P.lg_sgn >= 0 ? L.y : -L.y};
-  Cx<R> pw{R(1), R(0)}, pwm{R(1), R(0)};
+  Cx<R> pw{R(1), R(0)}, pwm{R(1), R(0)}, qp = q;
   for (int i = 0; i < P.lg_al; ++i) {
     pwm = pw;
     pw = cmul(pw, xi);
+    qp = cmul(qp, q);
   }
   // K = A pref q^{|l|+1} (q/q*)^p
-  Cx<R> K{P.amp * P.lg_pref, R(0)};
-  for (int i = 0; i <= P.lg_al; ++i) K = cmul(K, q);
-  Cx<R> g{(R(1) - zeta * zeta) * inv, R(2) * zeta * inv};
-  for (int i = 0; i < P.lg_p; ++i) K = cmul(K, g);
+  const Cx<R> K = cscale(cmul(qp, gp), P.amp * P.lg_pref);
   R mag = mul * exp2_r(fma(-a * q.re, R(kLog2e), l2));
   R ang = reduce_angle<R>(L.psi - a * q.im);
   R sn, cs;
@@ -593,7 +593,7 @@ __device__ __forceinline__ void fields_lg(const PT &P, const Local<R> &L, R E[3]
   Cx<R> DE{R(0), R(0)}, DB{R(0), R(0)};
   if (P.lon) {
     // dU/dx = base (T1 + x T2), dU/dy = base (i sgn T1 + y T2)
-    Cx<R> T1 = cscale(pwm, R(P.lg_al) * Lp);
+    Cx<R> T1 = cscale(pwm, P.lg_alf * Lp);
     Cx<R> T2 = cmul(pw, Cx<R>{R(4) * q.re * P.inv_w0sq * dL - R(2) * P.inv_w0sq * Lp * q.re,
                               -R(2) * P.inv_w0sq * Lp * q.im});
     R sg = P.lg_sgn >= 0 ? R(1) : R(-1);

@@ -49,6 +49,7 @@ struct Pulse {
   // dL_p^a/ds = -L_{p-1}^{a+1})
   R lg_r[6][kLgMaxP];
   R lg_pref;                     // (sqrt(2) / w0)^{|l|}
+  R lg_alf;                      // |l| as a number
   R a0, inv_w0, amp_unit;        // a0, 1/w0 and amp / a0 (adjoint: d/da0, d/dw0)
   R beta_f, inv_1mb;             // closed-form flying focus: v_f / c and 1 / (1 - beta_f)
   R adv_xy;                      // 1, or 0 for 1D-3V sets (transverse position held)
