@@ -32,6 +32,11 @@ CASES = {
                         longitudinal=True, t_focus=30.0),
     "lg2m1-x-lon": dict(kind="lg", pol="x", env="cw", a0=1.0, w0=3 * L, lg_p=2, lg_l=-1, longitudinal=True),
     "lg03-y": dict(kind="lg", pol="y", env="gauss", env_len=40.0, a0=1.0, w0=3 * L, lg_p=0, lg_l=3),
+    # |l| = 0 with p > 0 (no azimuthal power, the radial recurrence only) and LG_00
+    "lg20-cm-lon": dict(kind="lg", pol="cm", env="cw", a0=1.5, w0=2.5 * L, lg_p=2, lg_l=0, longitudinal=True,
+                        z_focus=-3.0),
+    "lg00-x-lon": dict(kind="lg", pol="x", env="gauss", env_len=30.0, a0=3.0, w0=3 * L, lg_p=0, lg_l=0,
+                       longitudinal=True),
     "flying-8-lon": dict(kind="flying", pol="x", a0=2.0, w0=2 * L, n_comp=8, bw_frac=0.05, beta_f=0.9,
                          ff_length=40 * L, longitudinal=True),
     # closed-form flying focus: counter-propagating (beta_f = -1) and subluminal focus
@@ -173,3 +178,22 @@ def test_maximum_table_sizes(precision):
             got = h.eval_fields(x, y, z, t, precision=precision).cpu().numpy()
         assert np.max(np.abs(got - ref)) <= tol * pulse["a0"], (pulse["kind"], np.max(np.abs(got - ref)))
         assert np.max(np.abs(ref)) > 0.05
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_lg00_equals_gaussian_through_both_device_paths(precision):
+    """LG_00 is the Gaussian (Sec. 3.1): the device's LG evaluation (Laguerre
+    recurrence, azimuthal and q powers) and its Gaussian evaluation give the
+    same fields, longitudinal terms included."""
+    from paper_2307_04843_gb300 import _lib
+    common = dict(pol="cp", env="gauss", env_len=30.0, a0=3.0, w0=2.5 * L, z_focus=4.0, t_focus=1.0,
+                  longitudinal=True)
+    x, y, z, t = _points(dict(kind="gauss", **common), 300, seed=17)
+    with _lib.Handle(dict(kind="lg", lg_p=0, lg_l=0, **common)) as h:
+        lg = h.eval_fields(x, y, z, t, precision=precision).cpu().numpy()
+    with _lib.Handle(dict(kind="gauss", **common)) as h:
+        ga = h.eval_fields(x, y, z, t, precision=precision).cpu().numpy()
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    assert np.max(np.abs(lg - ga)) <= tol * common["a0"]
+    assert np.max(np.abs(ga)) > 0.5
