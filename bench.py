@@ -323,7 +323,8 @@ YEE_LINES, YEE_NZ, YEE_STEPS = 152, 8192, 2000
 # 1-D lines with a cold-plasma current (Sec. 4): n_e = 1e-3 n_c, a g = 4
 # super-Gaussian of tau = 30 at 20 cells per wavelength, c dt/dz = 0.9
 LINE_LINES, LINE_NZ, SPLIT_STEPS, PLASMA_STEPS = 304, 4096, 2000, 20000
-SPLIT_MUFU_PER_NODE_STEP = 8  # E1: ex2, sin, cos; J1: ex2, sin, cos and the sin, cos of its phase shift
+SPLIT_MUFU_PER_NODE_STEP = 6  # E1: ex2, sin, cos; J1: ex2 and the sin, cos of its phase shift (its
+                              # carrier is E1's rotated by omega dt/2)
 
 
 def closed_form_rate(wl, stream, sum_rate):

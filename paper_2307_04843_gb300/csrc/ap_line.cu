@@ -72,6 +72,33 @@ __device__ __forceinline__ Local<float> node_local_ff(const Pulse<float> &P, con
   return L;
 }
 
+// E1 at t_n and J1 at t_n + dt/2 at one node of the float split line, for a
+// plane wave polarised along x (Eqs. plane_func, j1): the J1 carrier phase is
+// the E1 phase advanced by omega dt/2, applied as a fixed rotation
+// (sin, cos of omega dt/2 in sdl, cdl); the envelope and its log-derivatives
+// are evaluated at eta and eta + dt/2.
+__device__ __forceinline__ void line_sources_ff(const Pulse<float> &P, const StepFF &st, float kd_hi,
+                                                float kd_lo, float dz, float sdl, float cdl, float hdt,
+                                                float &E1, float &J1) {
+  const Local<float> L = node_local_ff(P, st, kd_hi, kd_lo, dz);
+  float mul, l2;
+  envelope(P, L.eta, mul, l2);
+  float a = P.amp * mul;
+  if (l2 != 0.0f) a *= exp2_r(l2);
+  float s, c;
+  sincos_r(L.psi, &s, &c);
+  E1 = a * c;
+  const float eta = L.eta + hdt;
+  envelope(P, eta, mul, l2);
+  float aj = P.jamp * P.amp * mul;
+  if (l2 != 0.0f) aj *= exp2_r(l2);
+  const float sj = fmaf(s, cdl, c * sdl), cj = fmaf(c, cdl, -(s * sdl));
+  float L1, L2;
+  envelope_logd(P, eta, L1, L2);
+  const Cx<float> V = finite_duration(Cx<float>{aj * cj, aj * sj}, 1.0f, L1, L2, P.inv_w);
+  J1 = V.im;  // Re[p (-i V)] with p = (1, 0)
+}
+
 // Local coordinates of node k (x = y = 0) at one time level (double).
 template <int PREC>
 __device__ __forceinline__ Local<Real<PREC>> node_local(const Pulse<Real<PREC>> &P, const LineArgs &a,
@@ -127,6 +154,14 @@ __global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant_
   TimeBase<PREC> tb;
   if constexpr (APT) tb.init(P, a.t0, 0.5 * a.dt);  // level 2n: t_n, 2n + 1: t_n + dt/2
   float lev = 0.0f;  // 2n in float (exact: 2 n_steps + 1 < 2^24 is checked on the host)
+  float sdl = 0.0f, cdl = 1.0f;  // sin, cos of omega dt/2 (float split line)
+  if constexpr (kFF) {
+    double sd, cd;
+    sincos(0.5 * P.omega * a.dt, &sd, &cd);
+    sdl = (float)sd;
+    cdl = (float)cd;
+  }
+  const float hdt = (float)(0.5 * a.dt);
   __syncthreads();
   for (long long n = 0; n < a.n_steps; ++n) {
     // B^{n+1/2} = B^n - (r/2)(E_{k+1}^n - E_k^n)
@@ -135,7 +170,6 @@ __global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant_
     typename TimeBase<PREC>::Step st_e{}, st_j{};
     if constexpr (kFF) {
       st_e = tb.at_f(lev);
-      st_j = tb.at_f(lev + 1.0f);
       lev += 2.0f;
     } else if constexpr (APT) {
       st_e = tb.at(2 * n);
@@ -145,17 +179,14 @@ __global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant_
     for (int k = t; k < nz; k += bd) {
       const T ek = e[k];
       T drive = ek;
-      float c_kdh = 0.0f, c_kdl = 0.0f, c_dz = 0.0f;
+      R j1 = R(0);
       if constexpr (kFF) {
-        c_kdh = kdh[k];
-        c_kdl = kdl[k];
-        c_dz = dzn[k];
-      }
-      if constexpr (APT) {
+        float e1;
+        line_sources_ff(P, st_e, kdh[k], kdl[k], dzn[k], sdl, cdl, hdt, e1, j1);
+        drive = l_add(e1, ek);
+      } else if constexpr (APT) {
         R E1[3], B1[3];
-        Local<R> L;
-        if constexpr (kFF) L = node_local_ff(P, st_e, c_kdh, c_kdl, c_dz);
-        else L = node_local<PREC>(P, a, st_e, k);
+        const Local<R> L = node_local<PREC>(P, a, st_e, k);
         analytic_fields<AP_PLANE, PREC>(P, L, E1, B1);
         drive = l_add((T)E1[0], ek);
       }
@@ -163,11 +194,11 @@ __global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant_
       j[k] = jk;
       if (k >= 1) {
         T src = jk;
-        if constexpr (APT) {
+        if constexpr (kFF) {
+          src = l_sub(jk, (T)j1);
+        } else if constexpr (APT) {
           R J1[3];
-          Local<R> L;
-          if constexpr (kFF) L = node_local_ff(P, st_j, c_kdh, c_kdl, c_dz);
-          else L = node_local<PREC>(P, a, st_j, k);
+          const Local<R> L = node_local<PREC>(P, a, st_j, k);
           current_plane(P, L, J1);
           src = l_sub(jk, (T)J1[0]);
         }
