@@ -84,6 +84,11 @@ MUTATIONS += [
      "split_line_keeps", PLASMA),
     ("Gaussian L2 without the L1^2 term", "      *L2 = (*L1) * (*L1) - 2.0 * a;", "      *L2 = -2.0 * a;",
      "log_derivatives", PLASMA),
+    ("split line current driven by E2 only", "      J[k] += dt * wp2[k] * (EB[0] + E2[k]);",
+     "      J[k] += dt * wp2[k] * E2[k];", "split_line_keeps", PLASMA),
+    ("split line J1 at t_n instead of t_n + dt/2",
+     "      or_current(s, 0.0, 0.0, z0 + (double)k * dz, t + 0.5 * dt, J1);",
+     "      or_current(s, 0.0, 0.0, z0 + (double)k * dz, t, J1);", "split_line_keeps", PLASMA),
 ]
 
 
