@@ -604,6 +604,11 @@ def run_ours(args):
                                     threads, grid=g_np)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "first %d particles of the workload x %d steps (%.1f s wall)" % (m, wl.n_steps, wall)}
+        # the same oracle on one core (a smaller sample, about a quarter of the time)
+        r1, m1, w1 = oracle_rate(wl.pulses[0], wl.parts, wl.t0, wl.dt, wl.n_steps, args.cpu_seconds / 4, 1,
+                                 grid=g_np)
+        cpu["single_thread"] = {"value": r1, "unit": UNIT, "cores": 1,
+                                "sample": "first %d particles x %d steps (%.1f s wall)" % (m1, wl.n_steps, w1)}
 
     # roofline of the push kernel
     al = ALGO[args.workload]
