@@ -265,8 +265,8 @@ def test_push_in_plasma_pulse_matches_oracle(precision):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_adjoint_in_plasma_pulse_vs_oracle_fd(precision):
+@pytest.mark.parametrize("precision,yee", [("fp64", False), ("fp32", False), ("fp64", True)])
+def test_adjoint_in_plasma_pulse_vs_oracle_fd(precision, yee):
     """Gradients of the mean final gamma with respect to a0 and z_f for a
     plasma pulse (the corrected B of Eq. b_corr_t enters through the dual
     field evaluation), against the oracle's finite differences."""
@@ -275,6 +275,8 @@ def test_adjoint_in_plasma_pulse_vs_oracle_fd(precision):
     from paper_2307_04843_gb300 import _lib
     pulse = dict(kind="plane", pol="x", env="sgauss", sg_order=2, env_len=12.0, a0=1.5, omega_p=0.4,
                  z_focus=1.0, t_focus=10.0)
+    if yee:  # the Yee-matched k, v_g, B0/E0 of Eqs. dispersion_j, e_amp_j
+        pulse.update(yee=True, yee_dx=L / 16, yee_dt=0.8 * L / 16)
     rng = np.random.default_rng(23)
     n = 24
     parts = dict(x=rng.uniform(-1, 1, n), y=rng.uniform(-1, 1, n), z=rng.uniform(-1, 1, n) * L,
