@@ -478,6 +478,92 @@ int launch_eval_t(const Pulse<Real<PREC>> &P, const EvalArgs &a, void *stream) {
   return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }
 
+// All requested components of every node in one thread.  The six staggered
+// positions of a node share two z levels -- the whole node (Ex, Ey, Bz) and
+// the half node (Ez, Bx, By) -- so the z- and t-only part of the evaluation
+// (local coordinates and carrier phase, envelope, and for beams the complex
+// q = 1/(1 - i zeta)) is computed once per level: the six evaluations are
+// straight-line code with identical z-only inputs, which the compiler
+// computes once.  Used when three or more components are requested.
+template <int KIND, int PREC, typename T>
+__global__ void __launch_bounds__(256) nodes_all_kernel(const __grid_constant__ Pulse<Real<PREC>> P,
+                                                        const __grid_constant__ NodeArgs a) {
+  using R = Real<PREC>;
+  using W = typename std::conditional<(sizeof(T) > sizeof(R)), T, R>::type;
+  bool want[6] = {false, false, false, false, false, false};
+  for (int q = 0; q < a.n_comp; ++q) want[a.comp[q]] = true;
+  const long long nxy = (long long)a.nx * a.ny;
+  const long long total = nxy * a.nz;
+  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= total) return;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  // node (i, j, k) of n and of the stride, advanced as in nodes_kernel (float
+  // copies of the indices: no int-to-float conversion per node)
+  int k = (int)(n / nxy);
+  int j = (int)((n - (long long)k * nxy) / a.nx);
+  int i = (int)(n - (long long)k * nxy - (long long)j * a.nx);
+  const long long sk64 = stride / nxy;
+  const int sj = (int)((stride - sk64 * nxy) / a.nx);
+  const int si = (int)(stride - sk64 * nxy - (long long)sj * a.nx);
+  const int sk = (int)(sk64 < (1 << 30) ? sk64 : (1 << 30));
+  float fi = (float)i, fj = (float)j, fk = (float)k;
+  const float fsi = (float)si, fsj = (float)sj, fsk = (float)sk;
+  const float fnx = (float)a.nx, fny = (float)a.ny;
+  TimeBase<PREC> tb;
+  tb.init(P, a.t, 0.0);
+  const typename TimeBase<PREC>::Step st = tb.at(0);
+  for (; n < total; n += stride) {
+    Local<R> Lz[2];
+    R xs[2], ys[2];  // transverse coordinates at the whole and the half node
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float o = h ? 0.5f : 0.0f;
+      Pos<PREC> pos;
+      if constexpr (PREC == AP_FP32_PHASEFF) {
+        pos.x = FF{0.0f, 0.0f};
+        pos.y = FF{0.0f, 0.0f};
+        pos.z = node_coord_ff(fk + o, a.lo_hi[2], a.lo_lo[2], a.d_hi[2], a.d_lo[2]);
+        xs[h] = fmaf(fi + o, a.d_hi[0], a.lo_hi[0]);
+        ys[h] = fmaf(fj + o, a.d_hi[1], a.lo_hi[1]);
+      } else {
+        pos.load(0.0, 0.0, fma((double)k + o, a.d[2], a.lo[2]));
+        xs[h] = (R)fma((double)i + o, a.d[0], a.lo[0]);
+        ys[h] = (R)fma((double)j + o, a.d[1], a.lo[1]);
+      }
+      Lz[h] = local_coords<PREC>(P, st, pos);
+    }
+    // component c at (x, y, z) offsets (Ex (1/2,0,0), Ey (0,1/2,0), Ez (0,0,1/2),
+    // Bx (0,1/2,1/2), By (1/2,0,1/2), Bz (1/2,1/2,0))
+    constexpr int kOx[6] = {1, 0, 0, 0, 1, 1}, kOy[6] = {0, 1, 0, 1, 0, 1}, kOz[6] = {0, 0, 1, 1, 1, 0};
+    R v[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      Local<R> L = Lz[kOz[c]];
+      L.x = xs[kOx[c]];
+      L.y = ys[kOy[c]];
+      R E[3], B[3];
+      node_values<KIND, PREC>(P, L, a.current, E, B);
+      v[c] = c < 3 ? E[c] : B[c - 3];
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      if (!want[c]) continue;
+      T *f = static_cast<T *>(a.f[c]);
+      f[n] = a.accumulate ? (T)((W)f[n] + (W)v[c]) : (T)v[c];
+    }
+    i += si;
+    fi += fsi;
+    int cj = 0;
+    if (i >= a.nx) { i -= a.nx; fi -= fnx; cj = 1; }
+    j += sj + cj;
+    fj += fsj + (cj ? 1.0f : 0.0f);
+    int ck = 0;
+    if (j >= a.ny) { j -= a.ny; fj -= fny; ck = 1; }
+    k = min(k + sk + ck, 1 << 30);
+    fk += fsk + (ck ? 1.0f : 0.0f);
+  }
+}
+
 // One warp writes the value v along a row of n elements (store, or add to
 // what the row holds, rounding once to T): a scalar head up to the first
 // 16-byte boundary, then 16-byte vector stores, then a scalar tail.  The row
@@ -593,6 +679,16 @@ int launch_nodes_t(const Pulse<Real<PREC>> &P, const NodeArgs &a, void *stream) 
       else nodes_plane_kernel<PREC, float><<<grid, block, 0, s>>>(P, a);
       return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
     }
+  }
+  if (a.n_comp >= 3) {
+    long long gx = (total + block - 1) / block;
+    const long long cap = (long long)a.sm_count * 8;
+    if (gx > cap) gx = cap;
+    if (gx < 1) gx = 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (a.f64) nodes_all_kernel<KIND, PREC, double><<<(unsigned)gx, block, 0, s>>>(P, a);
+    else nodes_all_kernel<KIND, PREC, float><<<(unsigned)gx, block, 0, s>>>(P, a);
+    return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
   }
   long long gx = (total + block - 1) / block;
   // enough resident threads per component to fill the GPU, then grid-stride
