@@ -490,8 +490,8 @@ __global__ void __launch_bounds__(256) nodes_all_kernel(const __grid_constant__ 
                                                         const __grid_constant__ NodeArgs a) {
   using R = Real<PREC>;
   using W = typename std::conditional<(sizeof(T) > sizeof(R)), T, R>::type;
-  bool want[6] = {false, false, false, false, false, false};
-  for (int q = 0; q < a.n_comp; ++q) want[a.comp[q]] = true;
+  unsigned want = 0u;  // bit c: component c requested (a register, not an indexed array)
+  for (int q = 0; q < a.n_comp; ++q) want |= 1u << a.comp[q];
   const long long nxy = (long long)a.nx * a.ny;
   const long long total = nxy * a.nz;
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(256) nodes_all_kernel(const __grid_constant__ 
     }
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      if (!want[c]) continue;
+      if (!((want >> c) & 1u)) continue;
       T *f = static_cast<T *>(a.f[c]);
       f[n] = a.accumulate ? (T)((W)f[n] + (W)v[c]) : (T)v[c];
     }
