@@ -316,12 +316,14 @@ def describe(wl, args):
 # ---------------------------------------------------------------- our arm
 
 NODE_N = 256           # staggered grid edge for the node-evaluation rate
-# FP32 operations per node of the Gaussian (longitudinal terms on) on the six
-# staggered positions: the z/t part once per z level (two levels: float-float
-# carrier phase and envelope argument 32, envelope 2, q = 1/(1 - i zeta) 3)
-# and the position part once per component (transverse exponent, angle and
-# its reduction, complex assembly, the one component written: 21)
-NODE_OPS_PER_NODE = 2 * 37 + 6 * 21
+# FP32 operations of the Gaussian (longitudinal terms on) on the six
+# staggered positions of the nodes: the position part once per component of a
+# node (transverse exponent, angle and its reduction, complex assembly, the one
+# component written: 21), and the z/t part once per (y, z) row for each of its
+# two z levels (float-float carrier phase and envelope argument 32, envelope
+# 2, q = 1/(1 - i zeta) 3), since every node of a row shares them
+NODE_OPS_PER_NODE = 6 * 21
+NODE_OPS_PER_ROW = 2 * 37
 YEE_LINES, YEE_NZ, YEE_STEPS = 152, 8192, 2000
 # 1-D lines with a cold-plasma current (Sec. 4): n_e = 1e-3 n_c, a g = 4
 # super-Gaussian of tau = 30 at 20 cells per wavelength, c dt/dz = 0.9
@@ -387,7 +389,7 @@ def grid_node_rates(wl, stream):
     sec = timed(lambda: wl.h.eval_nodes(f, lo, d, 0.0, precision="fp32"), 3)
     nodes = float(n) ** 3
     bytes_ = 24.0 * nodes
-    ops = NODE_OPS_PER_NODE * nodes
+    ops = NODE_OPS_PER_NODE * nodes + NODE_OPS_PER_ROW * float(n) ** 2
     peak_ops = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6
     hbm = None
     try:
@@ -412,7 +414,7 @@ def grid_node_rates(wl, stream):
                        "grid": "%d^3, 6 staggered components, float arrays, float-float phase" % n,
                        "alu_frac": ops / sec / peak_ops,
                        "hbm_frac": (bytes_ / sec / 1e9 / hbm) if hbm else None,
-                       "ops_per_node": NODE_OPS_PER_NODE, "bytes_per_node": 24},
+                       "ops_per_node": NODE_OPS_PER_NODE + NODE_OPS_PER_ROW / n, "bytes_per_node": 24},
         "eval_nodes_plane": {"value": nodes / psec, "unit": "nodes/s", "ms": psec * 1e3,
                              "grid": "%d^3, 6 staggered components, float arrays, plane wave" % n,
                              "hbm_frac": (bytes_ / psec / 1e9 / hbm) if hbm else None,

@@ -564,6 +564,78 @@ __global__ void __launch_bounds__(256) nodes_all_kernel(const __grid_constant__ 
   }
 }
 
+// Rows of nx >= 32 nodes, three or more components: one warp per (y, z)
+// row, lane l taking the nodes x = l, l + 32, ... (coalesced stores).  The
+// z/t part of the six staggered evaluations (local coordinates and carrier
+// phase, envelope, q) depends only on the row's two z levels: each lane
+// computes it once per row and reuses it for all its nodes, so per node only
+// the position part of the six evaluations remains (straight-line code, as
+// in nodes_all_kernel).
+template <int KIND, int PREC, typename T>
+__global__ void __launch_bounds__(256) nodes_row_kernel(const __grid_constant__ Pulse<Real<PREC>> P,
+                                                        const __grid_constant__ NodeArgs a) {
+  using R = Real<PREC>;
+  using W = typename std::conditional<(sizeof(T) > sizeof(R)), T, R>::type;
+  unsigned want = 0u;
+  for (int q = 0; q < a.n_comp; ++q) want |= 1u << a.comp[q];
+  const long long rows = (long long)a.ny * a.nz;
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  const float flane = (float)lane;
+  TimeBase<PREC> tb;
+  tb.init(P, a.t, 0.0);
+  const typename TimeBase<PREC>::Step st = tb.at(0);
+  constexpr int kOx[6] = {1, 0, 0, 0, 1, 1}, kOy[6] = {0, 1, 0, 1, 0, 1}, kOz[6] = {0, 0, 1, 1, 1, 0};
+  for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+    const int k = (int)(r / a.ny);
+    const int j = (int)(r - (long long)k * a.ny);
+    Local<R> Lz[2];
+    R ys[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float o = h ? 0.5f : 0.0f;
+      Pos<PREC> pos;
+      if constexpr (PREC == AP_FP32_PHASEFF) {
+        pos.x = FF{0.0f, 0.0f};
+        pos.y = FF{0.0f, 0.0f};
+        pos.z = node_coord_ff((float)k + o, a.lo_hi[2], a.lo_lo[2], a.d_hi[2], a.d_lo[2]);
+        ys[h] = fmaf((float)j + o, a.d_hi[1], a.lo_hi[1]);
+      } else {
+        pos.load(0.0, 0.0, fma((double)k + o, a.d[2], a.lo[2]));
+        ys[h] = (R)fma((double)j + o, a.d[1], a.lo[1]);
+      }
+      Lz[h] = local_coords<PREC>(P, st, pos);
+    }
+    const long long base = r * a.nx;
+    float fi = flane;
+    for (int i = lane; i < a.nx; i += 32, fi += 32.0f) {
+      R xs[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float o = h ? 0.5f : 0.0f;
+        if constexpr (PREC == AP_FP32_PHASEFF) xs[h] = fmaf(fi + o, a.d_hi[0], a.lo_hi[0]);
+        else xs[h] = (R)fma((double)i + o, a.d[0], a.lo[0]);
+      }
+      R v[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        Local<R> L = Lz[kOz[c]];
+        L.x = xs[kOx[c]];
+        L.y = ys[kOy[c]];
+        R E[3], B[3];
+        node_values<KIND, PREC>(P, L, a.current, E, B);
+        v[c] = c < 3 ? E[c] : B[c - 3];
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        if (!((want >> c) & 1u)) continue;
+        T *f = static_cast<T *>(a.f[c]) + base;
+        f[i] = a.accumulate ? (T)((W)f[i] + (W)v[c]) : (T)v[c];
+      }
+    }
+  }
+}
+
 // One warp writes the value v along a row of n elements (store, or add to
 // what the row holds, rounding once to T): a scalar head up to the first
 // 16-byte boundary, then 16-byte vector stores, then a scalar tail.  The row
@@ -679,6 +751,17 @@ int launch_nodes_t(const Pulse<Real<PREC>> &P, const NodeArgs &a, void *stream) 
       else nodes_plane_kernel<PREC, float><<<grid, block, 0, s>>>(P, a);
       return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
     }
+  }
+  if (a.n_comp >= 3 && a.nx >= 32) {
+    const long long rows = (long long)a.ny * a.nz;
+    long long gx = (rows + 7) / 8;  // 8 warps (rows) per block
+    const long long cap = (long long)a.sm_count * 8;
+    if (gx > cap) gx = cap;
+    if (gx < 1) gx = 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (a.f64) nodes_row_kernel<KIND, PREC, double><<<(unsigned)gx, block, 0, s>>>(P, a);
+    else nodes_row_kernel<KIND, PREC, float><<<(unsigned)gx, block, 0, s>>>(P, a);
+    return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
   }
   if (a.n_comp >= 3) {
     long long gx = (total + block - 1) / block;

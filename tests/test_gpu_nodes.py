@@ -44,13 +44,16 @@ def _grid(shape, dtype, fill=None):
 @pytest.mark.parametrize("name", sorted(NODE_CASES))
 @pytest.mark.parametrize("precision,f64", [("fp64", True), ("fp64", False), ("fp32", False),
                                            ("fp32_phase64", False)])
-def test_nodes_match_oracle(name, precision, f64):
+@pytest.mark.parametrize("shape", [(11, 6, 7), (4, 3, 70)], ids=["short-rows", "long-rows"])
+def test_nodes_match_oracle(name, precision, f64, shape):
+    """Every kind and precision on short rows (one thread per node) and on
+    rows of 70 nodes (one warp per row, two full warps of nodes and a ragged
+    third per lane group), ragged in every axis."""
     import torch
     from paper_2307_04843_gb300 import _lib
     pulse = NODE_CASES[name]
-    shape = (11, 6, 7)  # ragged in every axis, several blocks of threads
-    d = (0.37 * L, 0.29 * L, 0.11 * L)
-    lo = (-1.1 * L, -0.8 * L, -0.6 * L)
+    d = (0.37 * L, 0.29 * L, 0.11 * L) if shape[2] < 32 else (0.05 * L, 0.29 * L, 0.11 * L)
+    lo = (-1.1 * L, -0.8 * L, -0.6 * L) if shape[2] < 32 else (-1.75 * L, -0.8 * L, -0.6 * L)
     t = 0.9
     ref = oracle.yee_nodes(pulse, shape, lo, d, t)
     dtype = torch.float64 if f64 else torch.float32
