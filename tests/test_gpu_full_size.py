@@ -7,6 +7,8 @@ to the sums of the returned states, held transverse positions).
 
 Tolerances as in test_gpu_push: FP32 median relative |du| <= 1e-4, max
 <= 1e-3 (|du| / max(|u_ref|, 1))."""
+import math
+
 import numpy as np
 import pytest
 
@@ -158,3 +160,45 @@ def test_workload6_full_size_sweep(tmp_path):
     idx = _sample(int(off[-1]), 40, 6)
     ref = oracle.push(sets[0], subset(parts, idx), cfg["t0"], cfg["dt"], cfg["n_steps"], threads=THREADS)
     _check(subset(out, idx), ref)
+
+
+@pytest.mark.gpu
+def test_workload5_adjoint_full_size():
+    """The bench's adjoint call at full size (256 Gaussian sets, ~1.6e7
+    electrons, 2000 steps, checkpoints every 100, FP32): the objective equals
+    the forward push's per-set mean final gamma, and for three sampled sets
+    the gradient with respect to (a0, w0, z_f) matches FP64 central
+    differences of the GPU forward push over the whole set (the mean over the
+    set is the objective) to the gradient bound, 1e-3 relative."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    from paper_2307_04843_gb300.autograd import adjoint
+    cfg = workloads.config(5)
+    sets, counts = workloads.batch_sets(cfg)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    parts = workloads.particles_uniform(cfg["box"], int(off[-1]), workloads.seed_for(5))
+    dev = _lib.to_device(parts, "fp32")
+    d_off = torch.as_tensor(off).cuda()
+    J, dJ = adjoint(sets, dev, d_off, cfg["t0"], cfg["dt"], cfg["n_steps"], ckpt_every=cfg["ckpt_every"],
+                    precision="fp32")
+    J, dJ = J.cpu().numpy(), dJ.cpu().numpy()
+    _, sums = _batched_full(cfg, sets, parts, off, None)
+    np.testing.assert_allclose(J, sums / counts, rtol=1e-5)  # FP32 forward in both
+
+    def mean_gamma64(pulse, sub):
+        with _lib.Handle(pulse) as h:
+            d = _lib.to_device(sub, "fp64")
+            ss = torch.zeros(1, dtype=torch.float64, device="cuda")
+            h.push(d, cfg["t0"], cfg["dt"], cfg["n_steps"], precision="fp64", diag=dict(set_sum=ss))
+            assert h.status() == 0
+            return float(ss.item()) / sub["x"].size
+
+    rng = np.random.default_rng(55)
+    for s in rng.choice(len(sets), 3, replace=False):
+        sub = {k: v[off[s]:off[s + 1]] for k, v in parts.items()}
+        for col, name in enumerate(("a0", "w0", "z_focus")):
+            p = sets[s]
+            h = 1e-4 * (abs(p[name]) if name != "z_focus" else 2 * math.pi)
+            fd = (mean_gamma64(dict(p, **{name: p[name] + h}), sub) -
+                  mean_gamma64(dict(p, **{name: p[name] - h}), sub)) / (2 * h)
+            assert abs(dJ[s, col] - fd) <= 1e-3 * max(abs(fd), 1e-6), (s, name, dJ[s, col], fd)
