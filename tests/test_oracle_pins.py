@@ -402,6 +402,47 @@ def test_flying_focus_peak_moves_at_focal_velocity():
     assert abs(v - 0.99) < 0.01, v
 
 
+def test_flying_focus_sum_and_closed_form_fields_at_the_moving_focus():
+    """Field comparison of the two flying-focus constructions (Sec. 3.3) with
+    the same w0, a0 and v_f = 0.99: both reach a0 on axis at the moving focus;
+    the closed form's transverse intensity there is the waist Gaussian
+    exp(-2 r^2/w0^2) and its on-axis focal region is (1 - beta_f) z_R long;
+    the 64-component sum, whose components near the focus are at different
+    distances from their own waists and whose 10 % bandwidth sets its
+    duration, has a wider spot (at r = w0 above 0.3 of the axis value, the
+    Gaussian's 0.135) and an on-axis focal region tens of z units long."""
+    p = _ff_pulse()
+    st = oracle.state(p)
+    t = st["t_mid"]
+
+    def inten(pp, x, z):
+        if pp["kind"] == "flying_cf":  # the envelope |u|^2 (its focus moves ~1 unit per quarter period)
+            return abs(oracle.profile(pp, x, 0.0, z, t=t)) ** 2
+        # the sum: cycle average from two quadrature times (its focal region is long)
+        return oracle.fields(pp, x, 0.0, z, t)[0] ** 2 + oracle.fields(pp, x, 0.0, z, t + math.pi / 2)[0] ** 2
+
+    zs = np.arange(st["z_mid"] - 120, st["z_mid"] + 60, 1.0)
+    on = np.array([inten(p, 0.0, z) for z in zs])
+    k = int(np.argmax(on))
+    assert 0 < k < len(zs) - 1
+    zpk = zs[k]
+    cf = dict(kind="flying_cf", pol=p["pol"], env="cw", a0=p["a0"], w0=p["w0"], beta_f=p["beta_f"],
+              z_focus=zpk, t_focus=t)
+    assert math.sqrt(on[k]) == pytest.approx(p["a0"], rel=0.02)
+    assert math.sqrt(inten(cf, 0.0, zpk)) == pytest.approx(p["a0"], rel=1e-6)
+    rs = np.linspace(0.0, 1.5 * p["w0"], 16)
+    gauss = np.exp(-2.0 * rs ** 2 / p["w0"] ** 2)
+    i_cf = np.array([inten(cf, r, zpk) for r in rs])
+    i_sum = np.array([inten(p, r, zpk) for r in rs])
+    assert np.max(np.abs(i_cf / i_cf[0] - gauss)) < 0.02
+    at_w0 = np.argmin(np.abs(rs - p["w0"]))
+    assert i_sum[at_w0] / i_sum[0] > 0.3
+    # on-axis half-intensity lengths at this instant
+    zR1 = (1.0 - p["beta_f"]) * 0.5 * p["w0"] ** 2
+    assert inten(cf, 0.0, zpk + zR1) / inten(cf, 0.0, zpk) == pytest.approx(0.5, rel=1e-6)
+    assert inten(p, 0.0, zpk + 10.0) / on[k] > 0.5 and inten(p, 0.0, zpk - 10.0) / on[k] > 0.5
+
+
 def test_flying_focus_table_group_delay():
     """Component table: equally spaced frequencies over omega (1 +- 5%), foci
     equally spaced over [z_a, z_a + L], arrival times t_j = t_a + (z_j - z_a)/v_f,
