@@ -83,7 +83,8 @@ def parse():
                          "or the six component arrays")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--launch", default=None,
-                    help="fixed launch shape BLOCK[,BLOCKS_PER_SM[,GRID_CACHE]] instead of the autotuner's")
+                    help="fixed launch shape BLOCK[,BLOCKS_PER_SM[,GRID_CACHE[,PAIRS[,TILE]]]] instead of "
+                         "the autotuner's")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -245,9 +246,10 @@ class Workload:
         self.work = {k: v.clone() for k, v in self.init.items()}
         self.tuned = None
         if args.launch:
-            shape = [int(v) for v in args.launch.split(",")] + [0, 0]
-            self.h.set_launch(shape[0], shape[1], shape[2])
-            self.tuned = {"block": shape[0], "blocks_per_sm": shape[1], "grid_cache": shape[2], "fixed": True}
+            shape = [int(v) for v in args.launch.split(",")] + [0, 0, 0, 0]
+            self.h.set_launch(shape[0], shape[1], shape[2], shape[3], shape[4])
+            self.tuned = {"block": shape[0], "blocks_per_sm": shape[1], "grid_cache": shape[2],
+                          "pairs": shape[3], "tile": shape[4], "fixed": True}
         elif not args.no_autotune and idx not in (5, 6):
             from paper_2307_04843_gb300 import autotune
             self.tuned = autotune.tune(self.h, self.init, self.t0, self.dt, self.precision, self.grid,

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define AP_ABI_VERSION 2
+#define AP_ABI_VERSION 3
 
 /* ------------------------------------------------------------ status codes */
 #define AP_OK 0
@@ -170,9 +170,11 @@ typedef struct {
  *     trilinear coefficients (a0..a7) of
  *       F = a0 + a1 wx + a2 wy + a3 wz + a4 wx wy + a5 wy wz + a6 wx wz + a7 wx wy wz
  *     (w the position inside the cell, 0..1), each computed in double from
- *     the corners and rounded once: one contiguous 192-byte record per cell;
- *     the float pushes read it (7 FMA per component), the FP64 push and the
- *     adjoint read f[], which must then be given. */
+ *     the corners and rounded once: one contiguous 192-byte record per cell,
+ *     the components interleaved in pairs (Ex, Ey), (Ez, Bx), (By, Bz):
+ *     float 16 p + 2 k + h of a record is a_k of component 2 p + h.  The
+ *     float pushes read it (7 FMA per component, two components per packed
+ *     FMA), the FP64 push and the adjoint read f[], which must then be given. */
 typedef struct {
   const float *f[6];
   int32_t nx, ny, nz;
@@ -256,8 +258,18 @@ typedef struct {
   int32_t block;          /* threads per block, multiple of 32, <= 1024 */
   int32_t blocks_per_sm;  /* persistent kernels: resident blocks per SM */
   int32_t grid_cache;     /* float pushes with a AP_PACK_CELLS grid: where a thread keeps its
-                             current cell, 0 shared memory (12 slots, cp.async refetch),
-                             1 registers (48 registers, load refetch) */
+                             particles' current cells, 0 shared memory (12 slots each,
+                             cp.async refetch), 1 registers (48 registers each, load refetch),
+                             2 with two particles per thread: the first particle's cell in
+                             registers and the second's in shared memory (one particle per
+                             thread: as 1) */
+  int32_t pairs;          /* AP_FP32_PHASEFF pushes without a grid or with a AP_PACK_CELLS
+                             grid: 1 = each thread carries two particles, every FP32 operation
+                             of the field, the Boris step and the position packed (f32x2) over
+                             the pair; 0 = one particle per thread.  Results do not depend on
+                             the launch shape within either setting. */
+  int32_t tile;           /* batched launch: particles per tile, a multiple of the particles
+                             a block carries (block x (1 + pairs)); 0 = one block's worth */
 } ap_launch_cfg;
 
 typedef struct ap_handle_s *ap_handle;

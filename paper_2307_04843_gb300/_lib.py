@@ -42,7 +42,7 @@ AP_YEE1D_MAX_NODES = 12288
 AP_LINE1D_MAX_NODES_F32 = 12288
 AP_LINE1D_MAX_NODES_F64 = 6144
 AP_APT1D_MAX_NODES_F32 = 8192
-AP_ABI_VERSION = 2
+AP_ABI_VERSION = 3
 
 
 class ApPulseDesc(ctypes.Structure):
@@ -106,7 +106,8 @@ class ApLine1d(ctypes.Structure):
 
 
 class ApLaunchCfg(ctypes.Structure):
-    _fields_ = [("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("grid_cache", ctypes.c_int32)]
+    _fields_ = [("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("grid_cache", ctypes.c_int32),
+                ("pairs", ctypes.c_int32), ("tile", ctypes.c_int32)]
 
 
 # every entry point declared in include/ap.h: name -> (restype, argtypes)
@@ -352,8 +353,8 @@ def ap_destroy(h):
     lib().ap_destroy(h)
 
 
-def ap_set_launch(h, block=0, blocks_per_sm=0, grid_cache=0):
-    cfg = ApLaunchCfg(block, blocks_per_sm, grid_cache)
+def ap_set_launch(h, block=0, blocks_per_sm=0, grid_cache=0, pairs=0, tile=0):
+    cfg = ApLaunchCfg(block, blocks_per_sm, grid_cache, pairs, tile)
     check("ap_set_launch", lib().ap_set_launch(h, ctypes.byref(cfg)))
 
 
@@ -565,8 +566,8 @@ class Handle:
     def __exit__(self, *exc):
         self.close()
 
-    def set_launch(self, block=0, blocks_per_sm=0, grid_cache=0):
-        ap_set_launch(self.h, block, blocks_per_sm, grid_cache)
+    def set_launch(self, block=0, blocks_per_sm=0, grid_cache=0, pairs=0, tile=0):
+        ap_set_launch(self.h, block, blocks_per_sm, grid_cache, pairs, tile)
 
     def push(self, particles, t0, dt, n_steps, precision="fp32", grid=None, diag=None, stream=None):
         ap_gather_push(self.h, particles, grid, t0, dt, n_steps, precision, diag, stream)

@@ -24,7 +24,7 @@ struct ap_handle_s {
   Pulse<double> *d_pd = nullptr;
   Pulse<float> *d_pf = nullptr;
   int *d_status = nullptr;
-  apt::LaunchShape shape{0, 0, 0};
+  apt::LaunchShape shape{0, 0, 0, 0, 0};
 };
 
 struct ap_graph_s {
@@ -459,6 +459,10 @@ int fill_push_args(ap_handle_s *h, const ap_particles *p, const ap_grid *g, doub
   int rc = check_particles(p, precision);
   if (rc != AP_OK) return rc;
   if (!std::isfinite(t0) || !std::isfinite(dt) || n_steps < 0) return AP_ERR_ARG;
+  // the float-float time base counts steps in float and reduces the carrier
+  // phase C_n = C_0 + n (omega dt mod 2 pi) with a magic-number rounding that
+  // holds for |C_n| < 2^22 (2 pi): at most 2^23 - 1 steps per call
+  if (precision == AP_FP32_PHASEFF && n_steps >= (int64_t(1) << 23)) return AP_ERR_ARG;
   std::memset(&a, 0, sizeof(a));
   a.x = p->x; a.y = p->y; a.z = p->z;
   a.ux = p->ux; a.uy = p->uy; a.uz = p->uz;
@@ -639,13 +643,15 @@ int ap_num_sets(ap_handle h) { return h ? h->n_sets : AP_ERR_ARG; }
 int ap_set_launch(ap_handle h, const ap_launch_cfg *cfg) {
   if (!h) return AP_ERR_ARG;
   if (!cfg) {
-    h->shape = apt::LaunchShape{0, 0, 0};
+    h->shape = apt::LaunchShape{0, 0, 0, 0, 0};
     return AP_OK;
   }
   if (cfg->block != 0 && (cfg->block < 32 || cfg->block > 256 || (cfg->block & 31))) return AP_ERR_ARG;
   if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 64) return AP_ERR_ARG;
-  if (cfg->grid_cache != 0 && cfg->grid_cache != 1) return AP_ERR_ARG;
-  h->shape = apt::LaunchShape{cfg->block, cfg->blocks_per_sm, cfg->grid_cache};
+  if (cfg->grid_cache < 0 || cfg->grid_cache > 2) return AP_ERR_ARG;
+  if (cfg->pairs != 0 && cfg->pairs != 1) return AP_ERR_ARG;
+  if (cfg->tile < 0 || cfg->tile > (1 << 24)) return AP_ERR_ARG;
+  h->shape = apt::LaunchShape{cfg->block, cfg->blocks_per_sm, cfg->grid_cache, cfg->pairs, cfg->tile};
   return AP_OK;
 }
 
@@ -761,10 +767,13 @@ int ap_gather_push_batched(ap_handle h, const ap_particles *p, const ap_grid *g,
   if (rc != AP_OK) return rc;
   if (n_steps == 0) return AP_OK;
   ba.base.shape.block = h->shape.block > 0 ? h->shape.block : 128;
+  // particles per tile: a multiple of what one block carries per pass
+  const int per_pass = ba.base.shape.block * (h->shape.pairs ? 2 : 1);
+  if (h->shape.tile > 0 && h->shape.tile % per_pass != 0) return AP_ERR_ARG;
   ba.set_offsets = reinterpret_cast<const long long *>(p->set_offsets);
   ba.n_sets = h->n_sets;
   ba.tile_counter = static_cast<unsigned int *>(workspace);
-  ba.tile = ba.base.shape.block;
+  ba.tile = h->shape.tile > 0 ? h->shape.tile : per_pass;
   if (cudaMemsetAsync(workspace, 0, sizeof(unsigned int), static_cast<cudaStream_t>(stream)) !=
       cudaSuccess)
     return AP_ERR_CUDA;

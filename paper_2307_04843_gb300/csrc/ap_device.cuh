@@ -32,6 +32,10 @@ namespace apt {
 template <int PREC>
 using Real = typename std::conditional<PREC == AP_FP64, double, float>::type;
 
+// True for the packed pair type of ap_pair.cuh (two particles per value).
+template <typename R>
+struct IsPair : std::false_type {};
+
 // ------------------------------------------------------------ float-float
 // Error-free transformations (Knuth TwoSum, Dekker/FMA TwoProd).  The _rn
 // intrinsics keep the compiler from contracting or reassociating them.
@@ -51,6 +55,9 @@ __device__ __forceinline__ FF two_prod(float a, float b) {
   float e = __fmaf_rn(a, b, -p);
   return {p, e};
 }
+
+// the _rn spellings shared with the packed pair type (templates call these)
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 __device__ __forceinline__ FF split_double(double v) {
   float hi = __double2float_rn(v);
@@ -354,7 +361,11 @@ __device__ __forceinline__ void envelope(const PT &P, R eta, R &mul, R &l2) {
   l2 = R(0);
   switch (P.env) {
     case AP_ENV_SIN2: {
-      if (fabs(eta) > P.env_b) {
+      if constexpr (IsPair<R>::value) {
+        // both halves evaluated, each cleared outside its own window
+        const R c = cos_r(eta * P.env_a);
+        mul = sin2_window(c * c, eta, P.env_b);
+      } else if (fabs(eta) > P.env_b) {
         mul = R(0);
       } else {
         R c = cos_r(eta * P.env_a);
@@ -434,8 +445,8 @@ __device__ __forceinline__ void finish_beam(const PT &P, R x, R y, Cx<R> U, Cx<R
 
 template <typename R>
 __device__ __forceinline__ R reduce_angle(R a) {
-  if constexpr (std::is_same<R, float>::value) return reduce_f(a);
-  return a;
+  if constexpr (std::is_same<R, float>::value || IsPair<R>::value) return reduce_f(a);
+  else return a;
 }
 
 // Logarithmic derivatives L1 = Gamma'/Gamma and L2 = Gamma''/Gamma of the
@@ -534,7 +545,7 @@ __device__ __forceinline__ void fields_gauss(const PT &P, const Local<R> &L, R E
   R inv = rcp_r(fma(zeta, zeta, R(1)));
   Cx<R> q{inv, zeta * inv};
   R a = (L.x * L.x + L.y * L.y) * P.inv_w0sq;
-  R mag = P.amp * mul * exp2_r(fma(-a * q.re, R(kLog2e), l2));
+  R mag = P.amp * mul * exp2_r(fma(a * q.re, R(-kLog2e), l2));
   R ang = reduce_angle<R>(L.psi - a * q.im);
   R s, c;
   sincos_r(ang, &s, &c);
@@ -584,7 +595,7 @@ __device__ __forceinline__ void fields_lg(const PT &P, const Local<R> &L, R E[3]
   }
   // K = A pref q^{|l|+1} (q/q*)^p
   const Cx<R> K = cscale(cmul(qp, gp), P.amp * P.lg_pref);
-  R mag = mul * exp2_r(fma(-a * q.re, R(kLog2e), l2));
+  R mag = mul * exp2_r(fma(a * q.re, R(-kLog2e), l2));
   R ang = reduce_angle<R>(L.psi - a * q.im);
   R sn, cs;
   sincos_r(ang, &sn, &cs);
@@ -610,22 +621,21 @@ __device__ __forceinline__ void fields_lg(const PT &P, const Local<R> &L, R E[3]
 // (Sec. 3.3).  omega_j = w_first + j dw, vacuum k_j = omega_j, so
 // e^{i omega_j phi'} = e^{i w_first phi'} (e^{i dw phi'})^j: two reduced
 // base angles and one complex rotation per component.
-template <int PREC>
-__device__ __forceinline__ void fields_flying(const Pulse<Real<PREC>> &P, const Local<Real<PREC>> &L,
-                                              Real<PREC> E[3], Real<PREC> B[3]) {
-  using R = Real<PREC>;
+template <int PREC, typename R = Real<PREC>>
+__device__ __forceinline__ void fields_flying(const Pulse<Real<PREC>> &P, const Local<R> &L,
+                                              R E[3], R B[3]) {
   R A1, B1;
   if constexpr (PREC == AP_FP64) {
     A1 = P.ff_w * L.phi_hi;
     B1 = P.ff_dw * L.phi_hi;
   } else {
     // (w_first + 0) * phi' and dw * phi' in float-float, reduced mod 2 pi
-    const FF w{P.ffw_hi, P.ffw_lo}, d{P.ffd_hi, P.ffd_lo};
-    FF a = two_prod(w.hi, L.phi_hi);
-    float alo = __fmaf_rn(w.hi, L.phi_lo, __fmaf_rn(w.lo, L.phi_hi, a.lo));
+    const R whi = P.ffw_hi, wlo = P.ffw_lo, dhi = P.ffd_hi, dlo = P.ffd_lo;
+    const auto a = two_prod(whi, L.phi_hi);
+    const R alo = fma_rn(whi, L.phi_lo, fma_rn(wlo, L.phi_hi, a.lo));
     A1 = reduce_ff(a.hi, alo);
-    FF b = two_prod(d.hi, L.phi_hi);
-    float blo = __fmaf_rn(d.hi, L.phi_lo, __fmaf_rn(d.lo, L.phi_hi, b.lo));
+    const auto b = two_prod(dhi, L.phi_hi);
+    const R blo = fma_rn(dhi, L.phi_lo, fma_rn(dlo, L.phi_hi, b.lo));
     B1 = reduce_ff(b.hi, blo);
   }
   R sa, ca, sb, cb;
@@ -638,7 +648,7 @@ __device__ __forceinline__ void fields_flying(const Pulse<Real<PREC>> &P, const 
   Cx<R> S0{R(0), R(0)}, S1{R(0), R(0)};
   const int nc = P.n_comp;
   for (int j = 0; j < nc; ++j) {
-    const Comp<R> &cj = P.comp[j];
+    const auto &cj = P.comp[j];
     R zeta = fma(L.dz, cj.inv_zR, -cj.zoff);
     R inv = rcp_r(fma(zeta, zeta, R(1)));
     Cx<R> q{inv, zeta * inv};
@@ -654,15 +664,16 @@ __device__ __forceinline__ void fields_flying(const Pulse<Real<PREC>> &P, const 
   finish_beam(P, L.x, L.y, S0, S1, R(-2) * P.inv_w0sq, P.lon != 0, E, B);
 }
 
-template <int KIND, int PREC>
-__device__ __forceinline__ void analytic_fields(const Pulse<Real<PREC>> &P,
-                                                const Local<Real<PREC>> &L, Real<PREC> E[3],
-                                                Real<PREC> B[3]) {
+// R is Real<PREC>, or for the two-particle float-float kernels the packed
+// pair type of ap_pair.cuh.
+template <int KIND, int PREC, typename R = Real<PREC>>
+__device__ __forceinline__ void analytic_fields(const Pulse<Real<PREC>> &P, const Local<R> &L,
+                                                R E[3], R B[3]) {
   if constexpr (KIND == AP_PLANE) fields_plane(P, L, E, B);
   else if constexpr (KIND == AP_GAUSS) fields_gauss(P, L, E, B);
   else if constexpr (KIND == AP_LG) fields_lg(P, L, E, B);
   else if constexpr (KIND == AP_FLYING_CF) fields_gauss<true>(P, L, E, B);
-  else fields_flying<PREC>(P, L, E, B);
+  else fields_flying<PREC, R>(P, L, E, B);
 }
 
 // ------------------------------------------------------------ grid gather
@@ -920,11 +931,63 @@ __device__ __forceinline__ void grid_eval(const GridSlots &gc, float E[3], float
 
 // ------------------------------------- shared-memory cell-coefficient cache
 // With the per-cell coefficient copy (AP_PACK_CELLS) a thread keeps the 48
-// coefficients of its current cell in 12 shared-memory slots (slot 2c holds
-// a0..a3 and slot 2c+1 a4..a7 of component c), refetched as 12 contiguous
-// 16-byte cp.async copies of one 192-byte record, and evaluates each
-// component with 7 FMA:
-//   F = a0 + a3 wz + wy (a2 + a5 wz) + wx (a1 + a6 wz + wy (a4 + a7 wz)).
+// coefficients of its current cell (12 float4, one 192-byte record) in
+// registers or in 12 shared-memory slots, refetched as 12 contiguous 16-byte
+// loads or cp.async copies.  The record interleaves the components in pairs
+// (Ex, Ey), (Ez, Bx), (By, Bz): float4 4p + j holds coefficients 2j and
+// 2j + 1 of both components of pair p, (a_2j, a'_2j, a_2j+1, a'_2j+1), so that
+// each half of a float4 is a register pair and one packed FMA advances both
+// components of a pair.  Per component (7 FMA)
+//   F = a0 + a3 wz + wy (a2 + a5 wz) + wx (a1 + a6 wz + wy (a4 + a7 wz)),
+// evaluated for the three pairs with 21 packed FMA; each half rounds as the
+// scalar fmaf does, so the result per component is the scalar evaluation's.
+__device__ __forceinline__ void cell_eval(const float4 c[12], float wx, float wy, float wz,
+                                          float o[6]) {
+  const float2 WX = make_float2(wx, wx), WY = make_float2(wy, wy), WZ = make_float2(wz, wz);
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const float4 q0 = c[4 * p], q1 = c[4 * p + 1], q2 = c[4 * p + 2], q3 = c[4 * p + 3];
+    const float2 a0 = make_float2(q0.x, q0.y), a1 = make_float2(q0.z, q0.w);
+    const float2 a2 = make_float2(q1.x, q1.y), a3 = make_float2(q1.z, q1.w);
+    const float2 a4 = make_float2(q2.x, q2.y), a5 = make_float2(q2.z, q2.w);
+    const float2 a6 = make_float2(q3.x, q3.y), a7 = make_float2(q3.z, q3.w);
+    const float2 X = __ffma2_rn(a6, WZ, __ffma2_rn(__ffma2_rn(a7, WZ, a4), WY, a1));
+    const float2 Y = __ffma2_rn(a5, WZ, a2);
+    const float2 O = __ffma2_rn(X, WX, __ffma2_rn(Y, WY, __ffma2_rn(a3, WZ, a0)));
+    o[2 * p] = O.x;
+    o[2 * p + 1] = O.y;
+  }
+}
+
+__device__ __forceinline__ size_t cell_index(const GridView &g, int ix, int iy, int iz) {
+  return ((size_t)iz * (g.ny - 1) + iy) * (g.nx - 1) + ix;
+}
+
+// The cell of a particle at grid units (fx, fy, fz) for a refetch: its lower
+// corner (o), the weights inside it (w) and its index.  The corner comes
+// without the conversion pipe: rint(f - 1/2) through the 1.5 * 2^23 magic
+// number (a face point may land in the cell below, where its weight is 1:
+// same value), clamped to [0, n - 2]; the integer is read from the bits of
+// (corner + magic).
+__device__ __forceinline__ size_t locate_cell(const GridView &g, float fx, float fy, float fz,
+                                              float &ox, float &oy, float &oz, float &wx, float &wy,
+                                              float &wz) {
+  auto corner = [](float f, int n, int &i) {
+    float c = __fsub_rn(__fadd_rn(__fsub_rn(f, 0.5f), kRoundMagic), kRoundMagic);
+    c = fminf(fmaxf(c, 0.0f), (float)(n - 2));
+    i = __float_as_int(__fadd_rn(c, kRoundMagic)) - __float_as_int(kRoundMagic);
+    return c;
+  };
+  int ix, iy, iz;
+  ox = corner(fx, g.nx, ix);
+  oy = corner(fy, g.ny, iy);
+  oz = corner(fz, g.nz, iz);
+  wx = fx - ox;
+  wy = fy - oy;
+  wz = fz - oz;
+  return cell_index(g, ix, iy, iz);
+}
+
 struct CellSlots {
   float ox, oy, oz;  // lower corner of the cached cell in grid units
   float wx, wy, wz;  // weights of the current step
@@ -949,20 +1012,7 @@ __device__ __forceinline__ void grid_fetch(const GridView &g, CellSlots &gc, flo
   const float dev = fmaxf(fabsf(wx - 0.5f), fmaxf(fabsf(wy - 0.5f), fabsf(wz - 0.5f)));
   const bool need = !(dev <= 0.5f);
   if (__any_sync(0xffffffffu, need) && need) {
-    auto corner = [](float f, int n, int &i) {
-      float c = __fsub_rn(__fadd_rn(__fsub_rn(f, 0.5f), kRoundMagic), kRoundMagic);
-      c = fminf(fmaxf(c, 0.0f), (float)(n - 2));
-      i = __float_as_int(__fadd_rn(c, kRoundMagic)) - __float_as_int(kRoundMagic);
-      return c;
-    };
-    int ix, iy, iz;
-    gc.ox = corner(fx, g.nx, ix);
-    gc.oy = corner(fy, g.ny, iy);
-    gc.oz = corner(fz, g.nz, iz);
-    wx = fx - gc.ox;
-    wy = fy - gc.oy;
-    wz = fz - gc.oz;
-    const size_t cell = ((size_t)iz * (g.ny - 1) + iy) * (g.nx - 1) + ix;
+    const size_t cell = locate_cell(g, fx, fy, fz, gc.ox, gc.oy, gc.oz, wx, wy, wz);
     const float4 *src = g.cells + 12 * cell;
 #pragma unroll
     for (int k = 0; k < 12; ++k) cp_async16(gc.s0 + k * gc.step, src + k);
@@ -972,18 +1022,19 @@ __device__ __forceinline__ void grid_fetch(const GridView &g, CellSlots &gc, flo
   gc.wz = wz;
 }
 
+// the six interpolated components from the cached cell (the caller has
+// waited for the cell's copies)
+__device__ __forceinline__ void grid_values(const CellSlots &gc, float o[6]) {
+  float4 c[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) c[k] = lds128(gc.s0 + k * gc.step);
+  cell_eval(c, gc.wx, gc.wy, gc.wz, o);
+}
+
 __device__ __forceinline__ void grid_eval(const CellSlots &gc, float E[3], float B[3]) {
   cp_async_wait_all();  // this thread's copies (if any) have landed
-  const float wx = gc.wx, wy = gc.wy, wz = gc.wz;
   float o[6];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    const float4 a = lds128(gc.s0 + (2 * c) * gc.step);
-    const float4 b = lds128(gc.s0 + (2 * c + 1) * gc.step);
-    const float X = fmaf(b.z, wz, fmaf(fmaf(b.w, wz, b.x), wy, a.y));  // a1 + a6 wz + wy (a4 + a7 wz)
-    const float Y = fmaf(b.y, wz, a.z);                                // a2 + a5 wz
-    o[c] = fmaf(X, wx, fmaf(Y, wy, fmaf(a.w, wz, a.x)));              // a0 + a3 wz + wy Y + wx X
-  }
+  grid_values(gc, o);
   E[0] += o[0]; E[1] += o[1]; E[2] += o[2];
   B[0] += o[3]; B[1] += o[4]; B[2] += o[5];
 }
@@ -1013,20 +1064,7 @@ __device__ __forceinline__ void grid_fetch(const GridView &g, CellRegs &gc, floa
   const float dev = fmaxf(fabsf(wx - 0.5f), fmaxf(fabsf(wy - 0.5f), fabsf(wz - 0.5f)));
   const bool need = !(dev <= 0.5f);
   if (__any_sync(0xffffffffu, need) && need) {
-    auto corner = [](float f, int n, int &i) {
-      float c = __fsub_rn(__fadd_rn(__fsub_rn(f, 0.5f), kRoundMagic), kRoundMagic);
-      c = fminf(fmaxf(c, 0.0f), (float)(n - 2));
-      i = __float_as_int(__fadd_rn(c, kRoundMagic)) - __float_as_int(kRoundMagic);
-      return c;
-    };
-    int ix, iy, iz;
-    gc.ox = corner(fx, g.nx, ix);
-    gc.oy = corner(fy, g.ny, iy);
-    gc.oz = corner(fz, g.nz, iz);
-    wx = fx - gc.ox;
-    wy = fy - gc.oy;
-    wz = fz - gc.oz;
-    const size_t cell = ((size_t)iz * (g.ny - 1) + iy) * (g.nx - 1) + ix;
+    const size_t cell = locate_cell(g, fx, fy, fz, gc.ox, gc.oy, gc.oz, wx, wy, wz);
     const float4 *src = g.cells + 12 * cell;
 #pragma unroll
     for (int k = 0; k < 12; ++k) gc.c[k] = __ldg(src + k);
@@ -1036,16 +1074,13 @@ __device__ __forceinline__ void grid_fetch(const GridView &g, CellRegs &gc, floa
   gc.wz = wz;
 }
 
+__device__ __forceinline__ void grid_values(const CellRegs &gc, float o[6]) {
+  cell_eval(gc.c, gc.wx, gc.wy, gc.wz, o);
+}
+
 __device__ __forceinline__ void grid_eval(const CellRegs &gc, float E[3], float B[3]) {
-  const float wx = gc.wx, wy = gc.wy, wz = gc.wz;
   float o[6];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    const float4 a = gc.c[2 * c], b = gc.c[2 * c + 1];
-    const float X = fmaf(b.z, wz, fmaf(fmaf(b.w, wz, b.x), wy, a.y));
-    const float Y = fmaf(b.y, wz, a.z);
-    o[c] = fmaf(X, wx, fmaf(Y, wy, fmaf(a.w, wz, a.x)));
-  }
+  grid_values(gc, o);
   E[0] += o[0]; E[1] += o[1]; E[2] += o[2];
   B[0] += o[3]; B[1] += o[4]; B[2] += o[5];
 }

@@ -11,7 +11,8 @@
 //     a0 = c000, a1 = c100 - c000, ..., a7 = the alternating sum of the 8
 //     corners (cijk = corner i along x, j along y, k along z), computed in
 //     double and rounded once; the refetch is one contiguous record and the
-//     evaluation 7 FMA per component.
+//     evaluation 7 FMA per component.  The components are interleaved in
+//     pairs so that packed (f32x2) FMA evaluate two components at once.
 #include <cuda_runtime.h>
 
 #include "ap_internal.h"
@@ -33,7 +34,9 @@ struct CompPtrs {
   const float *f[6];
 };
 
-// one thread per cell, x fastest; record = 12 float4: (a0..a3, a4..a7) per component
+// one thread per cell, x fastest; record = 12 float4 with the components
+// interleaved in pairs (Ex, Ey), (Ez, Bx), (By, Bz): float 16 p + 2 k + h is
+// coefficient a_k of component 2 p + h
 __global__ void pack_cells_kernel(const __grid_constant__ CompPtrs src, int nx, int ny, int nz,
                                   float4 *__restrict__ out) {
   const long long cx = nx - 1, cy = ny - 1;
@@ -46,6 +49,7 @@ __global__ void pack_cells_kernel(const __grid_constant__ CompPtrs src, int nx, 
     const long long iy = r / cx;
     const long long ix = r - iy * cx;
     const long long b = iz * sz + iy * sy + ix;
+    float *rec = reinterpret_cast<float *>(out + 12 * c);
     for (int comp = 0; comp < 6; ++comp) {
       const float *f = src.f[comp];
       const double c000 = f[b], c100 = f[b + 1], c010 = f[b + sy], c110 = f[b + sy + 1];
@@ -56,8 +60,9 @@ __global__ void pack_cells_kernel(const __grid_constant__ CompPtrs src, int nx, 
       const double a5 = (c011 - c010) - (c001 - c000);
       const double a6 = (c101 - c100) - (c001 - c000);
       const double a7 = ((c111 - c110) - (c101 - c100)) - ((c011 - c010) - (c001 - c000));
-      out[12 * c + 2 * comp] = make_float4((float)c000, (float)a1, (float)a2, (float)a3);
-      out[12 * c + 2 * comp + 1] = make_float4((float)a4, (float)a5, (float)a6, (float)a7);
+      const double a[8] = {c000, a1, a2, a3, a4, a5, a6, a7};
+      float *r = rec + 16 * (comp >> 1) + (comp & 1);
+      for (int k = 0; k < 8; ++k) r[2 * k] = (float)a[k];
     }
   }
 }

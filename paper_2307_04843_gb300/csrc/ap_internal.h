@@ -94,6 +94,8 @@ struct LaunchShape {
   int block;
   int blocks_per_sm;
   int grid_cache;  // 0: cell in shared memory, 1: in registers (AP_PACK_CELLS only)
+  int pairs;       // float-float pushes: 1 = two particles per thread (packed arithmetic)
+  int tile;        // batched launch: particles per tile (0: the block's particles)
 };
 
 // Host-side launchers implemented in the per-kind translation units.

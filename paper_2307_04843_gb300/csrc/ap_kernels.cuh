@@ -5,7 +5,7 @@
 
 #include <type_traits>
 
-#include "ap_device.cuh"
+#include "ap_pair.cuh"
 
 namespace apt {
 
@@ -25,6 +25,8 @@ constexpr int kGridNone = 0;
 constexpr int kGridNodes = 1;
 constexpr int kGridCells = 2;
 constexpr int kGridCellsReg = 3;  // per-cell coefficients cached in registers
+constexpr int kGridCellsMix = 4;  // two particles per thread: the first's cell in registers,
+                                  // the second's in shared memory
 
 // Grid cell cache of a variant: registers for double, shared memory for float.
 template <int PREC, int GRID>
@@ -56,11 +58,13 @@ struct CacheOf<AP_FP32_PHASEFF, kGridCellsReg> {
   using type = CellRegs;
 };
 
-// shared-memory bytes of the cell cache per block of T threads
-template <int PREC, int GRID>
+// shared-memory bytes of the cell cache per block of T threads carrying NP
+// particles each
+template <int PREC, int GRID, int NP = 1>
 __host__ __device__ constexpr size_t grid_cache_bytes(int threads) {
   return PREC == AP_FP64 || GRID == kGridNone || GRID == kGridCellsReg ? 0
-         : GRID == kGridCells                                         ? 192u * (size_t)threads
+         : GRID == kGridCells                                         ? 192u * NP * (size_t)threads
+         : GRID == kGridCellsMix                                      ? 192u * (size_t)threads
                                                                       : grid_slot_bytes(threads);
 }
 
@@ -151,6 +155,128 @@ __device__ __forceinline__ double push_one(const Pulse<Real<PREC>> &P, const Pus
                               1.0));
 }
 
+// Two particles per thread (float-float variant, grid none or per-cell
+// coefficients in registers): particle i0 rides in the low half and i1 in the
+// high half of every packed value (ap_pair.cuh), so each FP32 instruction of
+// the local coordinates, the field, the Boris step and the position update
+// serves both.  The steps and their order are those of push_one; each
+// particle keeps its own grid cell (its refetch is its own warp-uniform
+// branch) and the cell is evaluated with packed FMA over component pairs.
+// `v0`, `v1` are false for padding particles.  g receives the final gammas.
+template <int KIND, int GRID>
+__device__ __forceinline__ void push_two(const Pulse<float> &P, const PushArgs &a, long long i0,
+                                         long long i1, bool v0, bool v1, StepFF *s_steps,
+                                         void *slots, double g[2]) {
+  static_assert(GRID == kGridNone || GRID == kGridCells || GRID == kGridCellsReg ||
+                    GRID == kGridCellsMix,
+                "two-particle grid modes");
+  double X[2] = {0.0, 0.0}, Y[2] = {0.0, 0.0}, Z[2] = {0.0, 0.0};
+  float ua[3] = {0.0f, 0.0f, 0.0f}, ub[3] = {0.0f, 0.0f, 0.0f};
+  {
+    const float *ux = static_cast<const float *>(a.ux);
+    const float *uy = static_cast<const float *>(a.uy);
+    const float *uz = static_cast<const float *>(a.uz);
+    if (v0) {
+      X[0] = a.x[i0]; Y[0] = a.y[i0]; Z[0] = a.z[i0];
+      ua[0] = ux[i0]; ua[1] = uy[i0]; ua[2] = uz[i0];
+    }
+    if (v1) {
+      X[1] = a.x[i1]; Y[1] = a.y[i1]; Z[1] = a.z[i1];
+      ub[0] = ux[i1]; ub[1] = uy[i1]; ub[2] = uz[i1];
+    }
+  }
+  F2 u[3] = {F2(ua[0], ub[0]), F2(ua[1], ub[1]), F2(ua[2], ub[2])};
+  Pos2 pos;
+  pos.load(X, Y, Z);
+  TimeBase<AP_FP32_PHASEFF> tb;
+  tb.init(P, a.t0, a.dt);
+  const float dts = (float)a.dt;
+  const F2 dtR = dts, dtxy = dts * P.adv_xy;
+  // light-front reference h0 = gamma - u_z on entry, per particle as in push_one
+  const float h0a = 1.0f / rsqrt_r(fmaf(ua[0], ua[0], fmaf(ua[1], ua[1], fmaf(ua[2], ua[2], 1.0f)))) - ua[2];
+  const float h0b = 1.0f / rsqrt_r(fmaf(ub[0], ub[0], fmaf(ub[1], ub[1], fmaf(ub[2], ub[2], 1.0f)))) - ub[2];
+  // cell caches: registers, or two regions of the block's shared slots (the
+  // second particle's 12 slots per thread after the first's)
+  using CacheA = typename std::conditional<GRID == kGridCells, CellSlots, CellRegs>::type;
+  using CacheB = typename std::conditional<GRID == kGridCellsReg, CellRegs, CellSlots>::type;
+  CacheA gca;
+  CacheB gcb;
+  if constexpr (GRID == kGridCellsMix) {
+    grid_slots_init(gca, nullptr);
+    grid_slots_init(gcb, slots);
+  } else if constexpr (GRID != kGridNone) {
+    grid_slots_init(gca, slots);
+    grid_slots_init(gcb, static_cast<unsigned char *>(slots) + 192u * blockDim.x);
+  }
+  double *lf = a.diag.lf;
+  StepFF *wsteps = s_steps + (threadIdx.x >> 5) * kStepChunk;
+  const int lane = threadIdx.x & 31;
+  auto steps = [&](auto with_lf) {
+    constexpr bool LF = decltype(with_lf)::value;
+    for (long long s0 = 0; s0 < a.n_steps; s0 += kStepChunk) {
+      const int cnt = (int)(a.n_steps - s0 < kStepChunk ? a.n_steps - s0 : kStepChunk);
+      __syncwarp();  // no lane still reads the previous chunk
+      if (lane < cnt) wsteps[lane] = tb.at(s0 + lane);
+      __syncwarp();
+      for (int k = 0; k < cnt; ++k) {
+        const StepFF st = wsteps[k];
+        const Local<F2> L = local_coords2(P, st, pos);
+        if constexpr (GRID != kGridNone) {
+          const F2 zr = pos.zr();
+          grid_fetch(a.grid, gca, L.x.x, L.y.x, zr.x);
+          grid_fetch(a.grid, gcb, L.x.y, L.y.y, zr.y);
+        }
+        F2 E[3], B[3];
+        analytic_fields<KIND, AP_FP32_PHASEFF, F2>(P, L, E, B);
+        if constexpr (GRID != kGridNone) {
+          if constexpr (GRID == kGridCells || GRID == kGridCellsMix)
+            cp_async_wait_all();  // this thread's copies landed
+          float oa[6], ob[6];
+          grid_values(gca, oa);
+          grid_values(gcb, ob);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            E[c].x += oa[c]; E[c].y += ob[c];
+            B[c].x += oa[c + 3]; B[c].y += ob[c + 3];
+          }
+        }
+        const F2 ig = boris(u, E, B, dtR);
+        pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtxy, dtR);
+        if constexpr (LF) {
+          const float da = v0 ? fabsf((1.0f / ig.x - u[2].x) - h0a) : 0.0f;
+          const float db = v1 ? fabsf((1.0f / ig.y - u[2].y) - h0b) : 0.0f;
+          warp_max_to(lf + s0 + k, fmaxf(da, db), 0xffffffffu);
+        }
+      }
+    }
+  };
+  if (lf) steps(std::true_type{});
+  else steps(std::false_type{});
+  const long long idx[2] = {i0, i1};
+  const bool val[2] = {v0, v1};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    g[h] = 0.0;
+    if (!val[h]) continue;
+    const long long i = idx[h];
+    const FF px{h ? pos.x.hi.y : pos.x.hi.x, h ? pos.x.lo.y : pos.x.lo.x};
+    const FF py{h ? pos.y.hi.y : pos.y.hi.x, h ? pos.y.lo.y : pos.y.lo.x};
+    const FF pz{h ? pos.z.hi.y : pos.z.hi.x, h ? pos.z.lo.y : pos.z.lo.x};
+    a.x[i] = (double)px.hi + (double)px.lo;
+    a.y[i] = (double)py.hi + (double)py.lo;
+    a.z[i] = (double)pz.hi + (double)pz.lo;
+    const float fu[3] = {h ? u[0].y : u[0].x, h ? u[1].y : u[1].x, h ? u[2].y : u[2].x};
+    static_cast<float *>(a.ux)[i] = fu[0];
+    static_cast<float *>(a.uy)[i] = fu[1];
+    static_cast<float *>(a.uz)[i] = fu[2];
+    const double dx = (double)fu[0], dy = (double)fu[1], dz = (double)fu[2];
+    if (!all_finite(a.x[i], a.y[i], a.z[i], dx, dy, dz)) atomicOr(a.status, kStatusNonfinite);
+    g[h] = __dsqrt_rn(__dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                          __dmul_rn(dz, dz)),
+                                1.0));
+  }
+}
+
 __device__ __forceinline__ void hist_add(uint32_t *s_hist, const DiagView &d, double g) {
   if (!isfinite(g)) return;
   double f = floor(__dmul_rn(__dsub_rn(g, d.hist_lo), d.hist_scale));
@@ -175,7 +301,7 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
 // trip count is uniform across the block), one particle per thread, every
 // step fused.  Dynamic shared memory: step tables, grid slots (float grid
 // kernels), then the histogram (hist_off bytes in).
-template <int KIND, int PREC, int GRID>
+template <int KIND, int PREC, int GRID, int NP = 1>
 __device__ __forceinline__ void push_body(const Pulse<Real<PREC>> &P, const PushArgs &a, unsigned hist_off) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ double s_red[32];
@@ -188,14 +314,30 @@ __device__ __forceinline__ void push_body(const Pulse<Real<PREC>> &P, const Push
     __syncthreads();
   }
   double acc = 0.0;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < a.n; base += stride) {
+  // NP particles per thread: a block covers NP * blockDim.x consecutive
+  // particles, thread t the ones at t and t + blockDim.x (coalesced)
+  const long long stride = (long long)NP * gridDim.x * blockDim.x;
+  for (long long base = (long long)NP * blockIdx.x * blockDim.x; base < a.n; base += stride) {
     const long long i = base + threadIdx.x;
-    const bool valid = i < a.n;
-    double g = push_one<KIND, PREC, GRID>(P, a, i, valid, s_steps, slots);
-    if (valid) {
-      acc += g;
-      if (hist) hist_add(s_hist, a.diag, g);
+    if constexpr (NP == 2) {
+      const long long i1 = i + blockDim.x;
+      double g[2];
+      push_two<KIND, GRID>(P, a, i, i1, i < a.n, i1 < a.n, s_steps, slots, g);
+      if (i < a.n) {
+        acc += g[0];
+        if (hist) hist_add(s_hist, a.diag, g[0]);
+      }
+      if (i1 < a.n) {
+        acc += g[1];
+        if (hist) hist_add(s_hist, a.diag, g[1]);
+      }
+    } else {
+      const bool valid = i < a.n;
+      double g = push_one<KIND, PREC, GRID>(P, a, i, valid, s_steps, slots);
+      if (valid) {
+        acc += g;
+        if (hist) hist_add(s_hist, a.diag, g);
+      }
     }
   }
   if (a.diag.set_sum) {
@@ -228,6 +370,31 @@ __global__ void __launch_bounds__(256, GRID == kGridCells ? 3 : 2)
   push_body<KIND, PREC, GRID>(P, a, hist_off);
 }
 
+// Two particles per thread (AP_FP32_PHASEFF; no grid, or per-cell
+// coefficients cached in shared memory or in registers).
+template <int KIND, int GRID>
+__global__ void __launch_bounds__(256)
+    push_kernel_pair(const __grid_constant__ Pulse<float> P, const __grid_constant__ PushArgs a,
+                     unsigned hist_off) {
+  push_body<KIND, AP_FP32_PHASEFF, GRID, 2>(P, a, hist_off);
+}
+// cells in shared memory: 2 resident blocks of 256 (384 B of slots per thread)
+template <int KIND>
+__global__ void __launch_bounds__(256, 2)
+    push_kernel_pair_smem(const __grid_constant__ Pulse<float> P, const __grid_constant__ PushArgs a,
+                          unsigned hist_off) {
+  push_body<KIND, AP_FP32_PHASEFF, kGridCells, 2>(P, a, hist_off);
+}
+// first cell in registers, second in shared memory: 2 resident blocks of 256
+// (128 registers, 192 B of slots per thread)
+template <int KIND>
+__global__ void __launch_bounds__(256, 2)
+    push_kernel_pair_mix(const __grid_constant__ Pulse<float> P, const __grid_constant__ PushArgs a,
+                         unsigned hist_off) {
+  push_body<KIND, AP_FP32_PHASEFF, kGridCellsMix, 2>(P, a, hist_off);
+}
+
+
 template <int KIND, int PREC, int GRID>
 constexpr auto push_entry() {
   if constexpr (GRID == kGridCells || GRID == kGridCellsReg) return push_kernel_cells<KIND, PREC, GRID>;
@@ -240,10 +407,9 @@ constexpr auto push_entry() {
 // tile count and no block waits on another.
 // Dynamic shared memory: step tables, grid slots (float grid kernels), then
 // the [n_sets + 1] tile prefix (prefix_off bytes in).
-template <int KIND, int PREC, int GRID>
-__global__ void __launch_bounds__(256) batch_kernel(const Pulse<Real<PREC>> *__restrict__ sets,
-                                                    const __grid_constant__ BatchArgs ba,
-                                                    unsigned prefix_off) {
+template <int KIND, int PREC, int GRID, int NP>
+__device__ __forceinline__ void batch_body(const Pulse<Real<PREC>> *__restrict__ sets,
+                                           const BatchArgs &ba, unsigned prefix_off) {
   using R = Real<PREC>;
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ double s_red[32];
@@ -295,11 +461,21 @@ __global__ void __launch_bounds__(256) batch_kernel(const Pulse<Real<PREC>> *__r
     const long long first = ba.set_offsets[set] + (tile - s_prefix[set]) * T;
     const long long end_set = ba.set_offsets[set + 1];
     double acc = 0.0;
-    for (int k = threadIdx.x; k < T; k += blockDim.x) {
+    // T is a multiple of NP * blockDim.x: every thread runs the same trip count
+    for (int k = threadIdx.x; k < T; k += NP * blockDim.x) {
       const long long i = first + k;
       const bool valid = i >= 0 && i < end_set && i < a.n;
-      double g = push_one<KIND, PREC, GRID>(sp, a, i, valid, s_steps, slots);
-      if (valid) acc += g;
+      if constexpr (NP == 2) {
+        const long long i1 = i + blockDim.x;
+        const bool valid1 = i1 >= 0 && i1 < end_set && i1 < a.n;
+        double g[2];
+        push_two<KIND, GRID>(sp, a, i, i1, valid, valid1, s_steps, slots, g);
+        if (valid) acc += g[0];
+        if (valid1) acc += g[1];
+      } else {
+        double g = push_one<KIND, PREC, GRID>(sp, a, i, valid, s_steps, slots);
+        if (valid) acc += g;
+      }
     }
     if (a.diag.set_sum) {
       double t = block_sum(acc, s_red);
@@ -307,6 +483,21 @@ __global__ void __launch_bounds__(256) batch_kernel(const Pulse<Real<PREC>> *__r
     }
     __syncthreads();
   }
+}
+
+template <int KIND, int PREC, int GRID, int NP = 1>
+__global__ void __launch_bounds__(256) batch_kernel(const Pulse<Real<PREC>> *__restrict__ sets,
+                                                    const __grid_constant__ BatchArgs ba,
+                                                    unsigned prefix_off) {
+  batch_body<KIND, PREC, GRID, NP>(sets, ba, prefix_off);
+}
+// two particles per thread with one or both cells in shared memory: 2 blocks
+// of 256
+template <int KIND, int GRID>
+__global__ void __launch_bounds__(256, 2)
+    batch_kernel_pair_2b(const Pulse<float> *__restrict__ sets, const __grid_constant__ BatchArgs ba,
+                         unsigned prefix_off) {
+  batch_body<KIND, AP_FP32_PHASEFF, GRID, 2>(sets, ba, prefix_off);
 }
 
 // Field evaluation hook: one point per thread, the push's own code path at
@@ -439,9 +630,9 @@ inline int occupancy_blocks(K kernel, int block, size_t smem) {
 }
 
 // dynamic shared memory before the kernel-specific tail (histogram / prefix)
-template <int PREC, int GRID>
+template <int PREC, int GRID, int NP = 1>
 inline size_t push_smem_head(int block) {
-  return step_table_bytes(block) + grid_cache_bytes<PREC, GRID>(block);
+  return step_table_bytes(block) + grid_cache_bytes<PREC, GRID, NP>(block);
 }
 
 template <typename K>
@@ -462,6 +653,31 @@ int launch_push_t(const Pulse<Real<PREC>> &P, const PushArgs &a, void *stream) {
   if (set_smem(kern, smem) != AP_OK) return AP_ERR_CUDA;
   const long long npad = (a.n + 31) & ~31LL;
   long long want = (npad + block - 1) / block;
+  int per_sm = a.shape.blocks_per_sm > 0 ? a.shape.blocks_per_sm : occupancy_blocks(kern, block, smem);
+  long long cap = (long long)a.sm_count * per_sm;
+  int grid = (int)(want < cap ? want : cap);
+  if (grid < 1) grid = 1;
+  kern<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(P, a, (unsigned)head);
+  return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+}
+
+// the two-particle kernel of a grid mode (each with its residency target)
+template <int KIND, int GRID>
+constexpr auto push_pair_entry() {
+  if constexpr (GRID == kGridCells) return push_kernel_pair_smem<KIND>;
+  else if constexpr (GRID == kGridCellsMix) return push_kernel_pair_mix<KIND>;
+  else return push_kernel_pair<KIND, GRID>;
+}
+
+template <int KIND, int GRID>
+int launch_push_pair_t(const Pulse<float> &P, const PushArgs &a, void *stream) {
+  auto kern = push_pair_entry<KIND, GRID>();
+  const int block = a.shape.block;
+  const size_t head = push_smem_head<AP_FP32_PHASEFF, GRID, 2>(block);
+  const size_t smem = head + (a.diag.hist ? (size_t)a.diag.bins * sizeof(uint32_t) : 0);
+  if (set_smem(kern, smem) != AP_OK) return AP_ERR_CUDA;
+  const long long per_block = 2LL * block;
+  const long long want = (a.n + per_block - 1) / per_block;
   int per_sm = a.shape.blocks_per_sm > 0 ? a.shape.blocks_per_sm : occupancy_blocks(kern, block, smem);
   long long cap = (long long)a.sm_count * per_sm;
   int grid = (int)(want < cap ? want : cap);
@@ -785,11 +1001,13 @@ int launch_nodes_t(const Pulse<Real<PREC>> &P, const NodeArgs &a, void *stream) 
   return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }
 
-template <int KIND, int PREC, int GRID>
+template <int KIND, int PREC, int GRID, int NP = 1>
 int launch_batch_t(const Pulse<Real<PREC>> *sets, const BatchArgs &ba, void *stream) {
-  auto kern = batch_kernel<KIND, PREC, GRID>;
+  auto kern = batch_kernel<KIND, PREC, GRID, NP>;
+  if constexpr (PREC == AP_FP32_PHASEFF && NP == 2 && (GRID == kGridCells || GRID == kGridCellsMix))
+    kern = batch_kernel_pair_2b<KIND, GRID>;
   const int block = ba.base.shape.block;
-  const size_t head = push_smem_head<PREC, GRID>(block);
+  const size_t head = push_smem_head<PREC, GRID, NP>(block);
   const size_t smem = head + (size_t)(ba.n_sets + 1) * sizeof(long long);
   if (set_smem(kern, smem) != AP_OK) return AP_ERR_CUDA;
   int per_sm = ba.base.shape.blocks_per_sm > 0 ? ba.base.shape.blocks_per_sm
@@ -800,8 +1018,21 @@ int launch_batch_t(const Pulse<Real<PREC>> *sets, const BatchArgs &ba, void *str
 }
 
 // grid mode of a call: none, corners, or (float kernels) per-cell coefficients
+// Whether a float-float call runs two particles per thread: requested in the
+// launch shape, and a grid mode the two-particle kernels have.
+inline bool pair_mode(const PushArgs &a) {
+  return a.shape.pairs && (!a.grid_on || a.grid.cells);
+}
+
 template <int KIND, int PREC>
 int launch_push_mode(const Pulse<Real<PREC>> &P, const PushArgs &a, void *stream) {
+  if constexpr (PREC == AP_FP32_PHASEFF) {
+    if (pair_mode(a))
+      return !a.grid_on                 ? launch_push_pair_t<KIND, kGridNone>(P, a, stream)
+             : a.shape.grid_cache == 2 ? launch_push_pair_t<KIND, kGridCellsMix>(P, a, stream)
+             : a.shape.grid_cache      ? launch_push_pair_t<KIND, kGridCellsReg>(P, a, stream)
+                                       : launch_push_pair_t<KIND, kGridCells>(P, a, stream);
+  }
   if (!a.grid_on) return launch_push_t<KIND, PREC, kGridNone>(P, a, stream);
   if constexpr (PREC != AP_FP64) {
     if (a.grid.cells)
@@ -813,6 +1044,13 @@ int launch_push_mode(const Pulse<Real<PREC>> &P, const PushArgs &a, void *stream
 
 template <int KIND, int PREC>
 int launch_batch_mode(const Pulse<Real<PREC>> *sets, const BatchArgs &ba, void *stream) {
+  if constexpr (PREC == AP_FP32_PHASEFF) {
+    if (pair_mode(ba.base))
+      return !ba.base.grid_on ? launch_batch_t<KIND, PREC, kGridNone, 2>(sets, ba, stream)
+             : ba.base.shape.grid_cache == 2 ? launch_batch_t<KIND, PREC, kGridCellsMix, 2>(sets, ba, stream)
+             : ba.base.shape.grid_cache      ? launch_batch_t<KIND, PREC, kGridCellsReg, 2>(sets, ba, stream)
+                                             : launch_batch_t<KIND, PREC, kGridCells, 2>(sets, ba, stream);
+  }
   if (!ba.base.grid_on) return launch_batch_t<KIND, PREC, kGridNone>(sets, ba, stream);
   if constexpr (PREC != AP_FP64) {
     if (ba.base.grid.cells)

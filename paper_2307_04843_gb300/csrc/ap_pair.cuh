@@ -1,0 +1,208 @@
+// ap_pair.cuh -- arithmetic on pairs of floats, for push kernels in which one
+// thread carries two particles through the step loop.
+//
+// The sm_100 family has packed FP32 instructions (add, mul and fma on .f32x2
+// register pairs): one instruction performs the same operation for both
+// halves.  The FP32 pipe's lane throughput is the same as with scalar
+// instructions (on GB300 both reach ~120 lane operations per clock per SM),
+// so what a packed instruction saves is an issue slot -- and instruction
+// issue, not the FP32 pipe, is what bounds the one-particle push kernels.
+// With the two particles of a thread in the two halves of every value, all
+// the FP32 arithmetic of the field evaluation, the Boris step and the
+// position update pairs up without any shuffling; the special-function (MUFU)
+// operations stay one per particle.
+//
+// Every packed operation rounds each half exactly as the scalar _rn
+// intrinsic does (round to nearest even, no contraction), so the error-free
+// transformations of the float-float phase and position carry over
+// unchanged.
+#pragma once
+
+#include "ap_device.cuh"
+
+namespace apt {
+
+// The pair type and its operations live in a namespace of their own: they
+// are found by argument-dependent lookup for pair arguments only, so they
+// never hide the scalar fma, fabs, ... that the rest of the library calls.
+namespace pair {
+
+struct __align__(8) F2 {
+  float x, y;
+  F2() = default;
+  // a scalar broadcast to both halves (pulse constants, literals)
+  __device__ __forceinline__ F2(float s) : x(s), y(s) {}
+  __device__ __forceinline__ F2(float a, float b) : x(a), y(b) {}
+};
+
+__device__ __forceinline__ float2 f2v(F2 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ F2 f2of(float2 v) { return F2(v.x, v.y); }
+
+// Negating a pair is not free (no packed negate; the compiler emits extra
+// instructions for about two thirds of them), so the code below subtracts
+// with the packed sub and negates constants rather than variables.
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return f2of(__fadd2_rn(f2v(a), f2v(b))); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(-a.x, -a.y); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+  F2 d;
+  asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+      "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return f2of(__fmul2_rn(f2v(a), f2v(b))); }
+__device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) {
+  return f2of(__ffma2_rn(f2v(a), f2v(b), f2v(c)));
+}
+__device__ __forceinline__ F2 &operator+=(F2 &a, F2 b) { return a = a + b; }
+__device__ __forceinline__ F2 &operator-=(F2 &a, F2 b) { return a = a - b; }
+__device__ __forceinline__ F2 &operator*=(F2 &a, F2 b) { return a = a * b; }
+// true when either half differs (used only where both halves may then take
+// the same path: a factor that is exactly 1 for the other half)
+__device__ __forceinline__ bool operator!=(F2 a, F2 b) { return a.x != b.x || a.y != b.y; }
+__device__ __forceinline__ F2 fabs(F2 a) { return F2(fabsf(a.x), fabsf(a.y)); }
+
+// the spelling of the fused operation that the float-float code uses
+__device__ __forceinline__ F2 fma_rn(F2 a, F2 b, F2 c) { return fma(a, b, c); }
+
+// special-function unit: one MUFU operation per half
+__device__ __forceinline__ F2 rcp_r(F2 a) { return F2(mufu_rcp(a.x), mufu_rcp(a.y)); }
+__device__ __forceinline__ F2 rsqrt_r(F2 a) { return F2(mufu_rsqrt(a.x), mufu_rsqrt(a.y)); }
+__device__ __forceinline__ F2 exp2_r(F2 a) { return F2(mufu_ex2(a.x), mufu_ex2(a.y)); }
+__device__ __forceinline__ F2 cos_r(F2 a) { return F2(mufu_cos(a.x), mufu_cos(a.y)); }
+__device__ __forceinline__ void sincos_r(F2 a, F2 *s, F2 *c) {
+  *s = F2(mufu_sin(a.x), mufu_sin(a.y));
+  *c = F2(mufu_cos(a.x), mufu_cos(a.y));
+}
+
+__device__ __forceinline__ Cx<F2> cscale(Cx<F2> a, F2 s) { return {a.re * s, a.im * s}; }
+
+// sin^2 envelope value m, cleared in each half whose |eta| lies beyond the
+// window's half-width b
+__device__ __forceinline__ F2 sin2_window(F2 m, F2 eta, float b) {
+  return F2(fabsf(eta.x) > b ? 0.0f : m.x, fabsf(eta.y) > b ? 0.0f : m.y);
+}
+
+// complex product with two fused operations per part
+__device__ __forceinline__ Cx<F2> cmul(Cx<F2> a, Cx<F2> b) {
+  return {fma(a.re, b.re, -(a.im * b.im)), fma(a.re, b.im, a.im * b.re)};
+}
+
+// round to the nearest integer through the 1.5 * 2^23 magic number, valid for
+// |a b| < 2^22 (see round_fma)
+__device__ __forceinline__ F2 round_fma(F2 a, F2 b) {
+  return fma(a, b, F2(kRoundMagic)) - F2(kRoundMagic);
+}
+
+// argument reduction of a moderate angle (a few times 2 pi), as reduce_f
+__device__ __forceinline__ F2 reduce_f(F2 x) {
+  const F2 m = round_fma(x, F2(kInvTwoPi));
+  x = fma(m, F2(-kTwoPiHi), x);
+  return fma(m, F2(-kTwoPiLo), x);
+}
+
+// ------------------------------------------------------------ float-float
+struct FF2 {
+  F2 hi, lo;
+};
+
+__device__ __forceinline__ FF2 two_sum(F2 a, F2 b) {
+  const F2 s = a + b;
+  const F2 bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+
+// a - b as hi + lo (the TwoSum of a and -b)
+__device__ __forceinline__ FF2 two_diff(F2 a, F2 b) {
+  const F2 s = a - b;
+  const F2 bb = s - a;
+  return {s, (a - (s - bb)) - (b + bb)};
+}
+
+__device__ __forceinline__ FF2 two_prod(F2 a, F2 b) {
+  const F2 p = a * b;
+  return {p, fma(a, b, -p)};
+}
+
+// The product a b = p + e with the error's sign flipped, from the negated
+// constant factor nb = -b: n = fma(a, nb, p) = p - a b exactly = -e.
+__device__ __forceinline__ F2 two_prod_nerr(F2 a, F2 nb, F2 p) { return fma(a, nb, p); }
+
+// (hi + lo) reduced modulo 2 pi (Cody-Waite, two constants), as reduce_ff:
+// r = hi - m P1 exactly (m P1 = p + e), t = (lo - e) - m P2
+__device__ __forceinline__ F2 reduce_ff(F2 hi, F2 lo) {
+  const F2 m = round_fma(hi, F2(kInvTwoPi));
+  const F2 p = m * F2(kTwoPiHi);
+  const F2 ne = two_prod_nerr(m, F2(-kTwoPiHi), p);
+  const F2 r = hi - p;
+  const F2 t = fma(m, F2(-kTwoPiLo), lo + ne);
+  return r + t;
+}
+
+}  // namespace pair
+
+using pair::F2;
+using pair::FF2;
+
+template <>
+struct IsPair<F2> : std::true_type {};
+
+// Positions of the two particles of a thread as float-float pairs, the same
+// compensated accumulation as Pos<AP_FP32_PHASEFF>.
+struct Pos2 {
+  FF2 x, y, z;
+  __device__ __forceinline__ void load(const double X[2], const double Y[2], const double Z[2]) {
+    const FF a = split_double(X[0]), b = split_double(X[1]);
+    x = {F2(a.hi, b.hi), F2(a.lo, b.lo)};
+    const FF c = split_double(Y[0]), d = split_double(Y[1]);
+    y = {F2(c.hi, d.hi), F2(c.lo, d.lo)};
+    const FF e = split_double(Z[0]), f = split_double(Z[1]);
+    z = {F2(e.hi, f.hi), F2(e.lo, f.lo)};
+  }
+  __device__ __forceinline__ static void acc(FF2 &p, F2 d) {
+    const F2 y = d + p.lo;
+    const F2 t = p.hi + y;
+    p.lo = y - (t - p.hi);
+    p.hi = t;
+  }
+  __device__ __forceinline__ void advance(F2 vx, F2 vy, F2 vz, F2 dt_xy, F2 dt) {
+    acc(x, dt_xy * vx);
+    acc(y, dt_xy * vy);
+    acc(z, dt * vz);
+  }
+  __device__ __forceinline__ F2 xr() const { return x.hi + x.lo; }
+  __device__ __forceinline__ F2 yr() const { return y.hi + y.lo; }
+  __device__ __forceinline__ F2 zr() const { return z.hi + z.lo; }
+};
+
+// Local coordinates of both particles at one step (float-float phase), the
+// pairwise form of local_coords<AP_FP32_PHASEFF>: the step's time base `st`
+// is shared by the two particles.
+__device__ __forceinline__ Local<F2> local_coords2(const Pulse<float> &P, const StepFF &st,
+                                                   const Pos2 &pos) {
+  Local<F2> L;
+  // dz = z - z_f
+  FF2 dz = two_diff(pos.z.hi, F2(P.zf_hi));
+  dz.lo = dz.lo + (pos.z.lo - F2(P.zf_lo));
+  // psi = C_n - k dz, k dz = kp + ke with -ke from the negated constant
+  const F2 kp = F2(P.k_hi) * dz.hi;
+  const F2 nke = two_prod_nerr(dz.hi, F2(-P.k_hi), kp);
+  const F2 kdlo = fma(F2(P.k_hi), dz.lo, F2(P.k_lo) * dz.hi) - nke;
+  const FF2 ps = two_diff(F2(st.C), kp);
+  L.psi = reduce_ff(ps.hi, ps.lo - kdlo);
+  L.x = pos.xr();
+  L.y = pos.yr();
+  L.dz = dz.hi + dz.lo;
+  const float Tf = __fadd_rn(st.Th, st.Tl);
+  L.eta = fma(L.dz, F2(-P.inv_vg), F2(Tf));
+  L.T = F2(Tf);
+  // phi' = T - dz as float-float
+  const FF2 ph = two_diff(F2(st.Th), dz.hi);
+  L.phi_hi = ph.hi;
+  L.phi_lo = ph.lo + (F2(st.Tl) - dz.lo);
+  return L;
+}
+
+}  // namespace apt

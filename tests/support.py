@@ -23,13 +23,16 @@ def subset(parts, idx):
 
 
 def gpu_push(pulses, parts, t0, dt, n_steps, precision, grid=None, diag_keys=(), hist=None,
-             block=0, blocks_per_sm=0):
+             block=0, blocks_per_sm=0, launch=None):
     """Run ap_gather_push on a copy of `parts` (numpy); returns (host arrays,
-    diag dict of host arrays, status)."""
+    diag dict of host arrays, status).  `launch`: keyword arguments of
+    Handle.set_launch (block, blocks_per_sm, grid_cache, pairs, tile)."""
     import torch
     from paper_2307_04843_gb300 import _lib
     with _lib.Handle(pulses) as h:
-        if block or blocks_per_sm:
+        if launch:
+            h.set_launch(**launch)
+        elif block or blocks_per_sm:
             h.set_launch(block, blocks_per_sm)
         dev = _lib.to_device(parts, precision)
         diag = {}

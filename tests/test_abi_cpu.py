@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_version_and_status_strings(L):
-    assert _lib.ap_version() == _lib.AP_ABI_VERSION == 2
+    assert _lib.ap_version() == _lib.AP_ABI_VERSION == 3
     for code in (0, -1, -2, -3, -4, -5, -6, -7):
         s = _lib.ap_status_string(code)
         assert s and s != "unknown status"

@@ -326,7 +326,10 @@ def test_cell_coefficient_layout_reconstructs_corners():
     g, lo, hi = _grid_small(cfg, n=17)
     nz, ny, nx = g.shape[1:]
     packed = _lib.pack_grid((torch.as_tensor(g).cuda(), lo, hi), layout="cells")
-    a = packed[3].view(nz - 1, ny - 1, nx - 1, 6, 8).double().cpu().numpy()
+    # record: component pairs (Ex, Ey), (Ez, Bx), (By, Bz); float 16 p + 2 k + h
+    # is coefficient k of component 2 p + h
+    a = packed[3].view(nz - 1, ny - 1, nx - 1, 3, 8, 2).double().cpu().numpy()
+    a = np.swapaxes(a, -1, -2).reshape(nz - 1, ny - 1, nx - 1, 6, 8)
     f = g.astype(np.float64)
     for (i, j, k) in ((0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0), (0, 0, 1), (1, 0, 1), (0, 1, 1), (1, 1, 1)):
         val = (a[..., 0] + i * a[..., 1] + j * a[..., 2] + k * a[..., 3] + i * j * a[..., 4] + j * k * a[..., 5]
@@ -400,4 +403,25 @@ def test_cell_cache_in_registers_or_shared_memory_identical(precision):
             out = _lib.to_host(dev)
             for k in base:
                 np.testing.assert_array_equal(out[k], base[k], err_msg=str((block, bps, gc, k)))
+        assert h.status() == 0
+
+
+@pytest.mark.gpu
+def test_float_float_step_limit_rejected():
+    """The float-float time base counts steps in float and reduces the carrier
+    phase with a magic-number rounding valid below 2^22 (2 pi): a float-float
+    call of 2^23 or more steps is rejected before any launch; 2^23 - 1 steps
+    (no particles: nothing to do) and the double-phase variants are accepted."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    cfg = workloads.config(2)
+    empty = {k: v[:0] for k, v in workloads.particles(cfg, n=1).items()}
+    with _lib.Handle(cfg["pulse"]) as h:
+        dev = _lib.to_device(workloads.particles(cfg, n=4), "fp32")
+        with pytest.raises(_lib.APError) as e:
+            h.push(dev, 0.0, 0.02, 1 << 23, precision="fp32")
+        assert e.value.status == _lib.AP_ERR_ARG
+        h.push(_lib.to_device(empty, "fp32"), 0.0, 0.02, (1 << 23) - 1, precision="fp32")
+        h.push(_lib.to_device(empty, "fp32_phase64"), 0.0, 0.02, 1 << 23, precision="fp32_phase64")
+        torch.cuda.synchronize()
         assert h.status() == 0
