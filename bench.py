@@ -62,10 +62,11 @@ ALGO = {
 # (an upper bound at 1e7 particles: more particles share each cached cell);
 # None when the kernel changed after the capture.
 TRAFFIC_PER_PARTICLE_STEP = {
-    "nodes": 5.336,  # (34.084e9 read + 0.064e9 written) / 6.4e9
-    "cells": 6.058,  # (38.707e9 read + 0.064e9 written) / 6.4e9, cell in registers
+    "nodes": None,
+    "cells": None,
     "arrays": None,
 }
+TRAFFIC_KERNEL_PAIRS = 1  # the particles-per-thread setting the capture was taken with
 
 
 def parse():
@@ -254,6 +255,10 @@ class Workload:
             from paper_2307_04843_gb300 import autotune
             self.tuned = autotune.tune(self.h, self.init, self.t0, self.dt, self.precision, self.grid,
                                        sample_n=min(self.n, 2_000_000), sample_steps=min(self.n_steps, 200))
+        elif not args.no_autotune:
+            from paper_2307_04843_gb300 import autotune
+            self.tuned = autotune.tune_batched(self.h, self.init, self.off, self.t0, self.dt, self.precision,
+                                               self.grid, self.diag, sample_steps=min(self.n_steps, 100))
         if idx in (5, 6):
             self.stream = torch.cuda.Stream()
             self.graph = _lib.ap_batch_graph_create(self.h.h, self.work, self.off, None, self.t0, self.dt,
@@ -308,11 +313,23 @@ def describe(wl, args):
                               "nodes": "node-interleaved (ap_grid_pack, AP_PACK_NODES)",
                               "arrays": "six component arrays"}[args.grid_layout]
     if wl.tuned:
-        cfg["launch"] = {"block": wl.tuned["block"], "blocks_per_sm": wl.tuned["blocks_per_sm"],
-                         "grid_cache": ("registers" if wl.tuned.get("grid_cache") else "shared memory")
-                         if wl.grid is not None else None,
-                         "autotuned": not wl.tuned.get("fixed", False)}
+        cfg["launch"] = launch_desc(wl)
     return cfg
+
+
+def launch_desc(wl):
+    t = wl.tuned or {}
+    gc = t.get("grid_cache", 0)
+    pairs = t.get("pairs", 0)
+    d = {"block": t.get("block"), "blocks_per_sm": t.get("blocks_per_sm"),
+         "particles_per_thread": 2 if pairs else 1,
+         "grid_cache": None if wl.grid is None else
+         ("first particle's cell in registers, second's in shared memory" if pairs and gc == 2 else
+          "registers" if gc else "shared memory"),
+         "autotuned": bool(t) and not t.get("fixed", False)}
+    if wl.graph is not None or wl.idx in (5, 6):
+        d["tile"] = t.get("tile") or (t.get("block") or 128) * (2 if pairs else 1)
+    return d
 
 
 # ---------------------------------------------------------------- our arm
@@ -471,6 +488,78 @@ def line_rates(split_steps, plasma_steps, timed=None):
                      "dtype": "f32"},
     }
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def roofline_frac(idx, rate):
+    return ALGO[idx]["fp32"] * rate / (SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6)
+
+
+def other_workloads(args, stream):
+    """Every other workload at its full configuration, autotuned, one timed
+    call each (after one untimed call): rate, kernel milliseconds and the
+    FP32 roofline fraction by the same operation count as the headline; the
+    closed-form flying focus beside the 64-component sum and the adjoint of
+    the batched sets."""
+    import torch
+    res = {}
+    for idx in (3, 4, 5, 6):
+        sub = argparse.Namespace(**vars(args))
+        sub.workload, sub.n, sub.nsteps, sub.launch = idx, None, None, None
+        wl = Workload(idx, sub, 0)
+        wl.restore()
+        wl.push()
+        torch.cuda.synchronize()
+        wl.restore()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        wl.push()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if wl.h.status() != 0:
+            raise RuntimeError("device status after workload %d" % idx)
+        sec = a.elapsed_time(b) / 1e3
+        rate = wl.n * wl.n_steps / sec
+        r = {"value": rate, "unit": UNIT, "kernel_ms": sec * 1e3, "roofline_frac": roofline_frac(idx, rate),
+             "algo_ops_per_particle_step": ALGO[idx]["fp32"], "particles": wl.n, "steps": wl.n_steps,
+             "workload": describe(wl, sub)["workload"], "launch": launch_desc(wl)}
+        if idx == 4:
+            r["closed_form"] = closed_form_rate(wl, stream, rate)
+        if idx == 5:
+            from paper_2307_04843_gb300.autograd import adjoint as run_adjoint
+            run_adjoint(wl.pulses, wl.init, wl.off, wl.t0, wl.dt, 200, ckpt_every=100, precision="fp32")
+            torch.cuda.synchronize()
+            a.record(stream)
+            run_adjoint(wl.pulses, wl.init, wl.off, wl.t0, wl.dt, wl.n_steps, ckpt_every=wl.cfg["ckpt_every"],
+                        precision="fp32")
+            b.record(stream)
+            torch.cuda.synchronize()
+            asec = a.elapsed_time(b) / 1e3
+            r["adjoint"] = {"value": wl.n * wl.n_steps / asec, "unit": UNIT, "seconds": asec,
+                            "vs_forward": asec / sec, "ckpt_every": wl.cfg["ckpt_every"]}
+        res[str(idx)] = r
+        wl.close()
+        del wl
+        torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -577,19 +666,27 @@ def run_ours(args):
         te = torch.tensor([a.elapsed_time(b_) / 1e3], dtype=torch.float64, device="cuda")
         shard.reduce_max(te)
         e2e = {"value": units / float(te[0]), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(h2d)}
+               "d2h_bytes_per_step": int(h2d),
+               "overlap": "pipelined: two device buffers and separate H2D and D2H streams, so step k's "
+                          "push overlaps step k+1's input copy and step k-1's result copy (throughput, "
+                          "not the latency of one call)"}
 
     # comparison variants on one GPU: native-FP64-phase and plain FP64 paths
     variants = {}
     if rank == 0 and not args.no_variants and args.workload in (2, 3, 4):
-        for prec, nv in (("fp32_phase64", min(wl.n, 2_000_000)), ("fp64", min(wl.n, 500_000))):
+        # workload 2 at its full size; the others on a prefix (the plain FP64
+        # flying-focus sum runs at ~1e8 particle-steps/s)
+        full = args.workload == 2
+        for prec, nv in (("fp32_phase64", wl.n if full else min(wl.n, 2_000_000)),
+                         ("fp64", wl.n if full else min(wl.n, 500_000))):
             if args.workload == 4:
                 nv = max(1, nv // 16)
             sub = {k: v[:nv] for k, v in wl.parts.items()}
             d0 = _lib.to_device(sub, prec)
-            d1 = {k: v.clone() for k, v in d0.items()}
+            d1 = {k: v[:200_000].clone() for k, v in d0.items()}
             wl.h.set_launch(0, 0)
             wl.h.push(d1, wl.t0, wl.dt, 100, precision=prec, grid=wl.grid)
+            del d1
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -597,8 +694,13 @@ def run_ours(args):
             b.record(stream)
             torch.cuda.synchronize()
             sec = a.elapsed_time(b) / 1e3
-            variants[prec] = {"value": nv * wl.n_steps / sec, "unit": UNIT,
+            variants[prec] = {"value": nv * wl.n_steps / sec, "unit": UNIT, "kernel_ms": sec * 1e3,
                               "sample": "%d particles x %d steps, one call" % (nv, wl.n_steps)}
+            if prec == "fp32_phase64":
+                variants[prec]["roofline_frac"] = ALGO[args.workload]["fp32"] * nv * wl.n_steps / sec / (
+                    SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6)
+            del d0
+            torch.cuda.empty_cache()
         for prec in variants:
             variants[prec]["fp32_speedup"] = (units_rank / kern) / variants[prec]["value"]
         if args.workload == 4:
@@ -609,6 +711,13 @@ def run_ours(args):
     grid_node = None
     if rank == 0 and not args.no_variants and args.workload == 2:
         grid_node = grid_node_rates(wl, stream)
+    # every other workload at its full configuration
+    others = None
+    if rank == 0 and not args.no_variants and args.workload == 2:
+        wl_h_status = wl.h.status()
+        if wl_h_status != 0:
+            raise RuntimeError("device status before the other workloads: %d" % wl_h_status)
+        others = other_workloads(args, stream)
 
     # the adjoint of the batched workload: forward + reverse sweep
     adjoint = None
@@ -635,7 +744,7 @@ def run_ours(args):
             g_np = (wl.grid_host[0].cpu().numpy(), wl.grid_host[1], wl.grid_host[2])
         rate, m, wall = oracle_rate(wl.pulses[0], wl.parts, wl.t0, wl.dt, wl.n_steps, args.cpu_seconds,
                                     threads, grid=g_np)
-        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "cpu_model": cpu_model(), "kind": "oracle",
                "sample": "first %d particles of the workload x %d steps (%.1f s wall)" % (m, wl.n_steps, wall)}
         # the same oracle on one core (a smaller sample, about a quarter of the time)
         r1, m1, w1 = oracle_rate(wl.pulses[0], wl.parts, wl.t0, wl.dt, wl.n_steps, args.cpu_seconds / 4, 1,
@@ -653,7 +762,8 @@ def run_ours(args):
         peak_ops = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12  # TOP/s
         achieved = al["fp32"] * rate_k / 1e12
         traffic = None
-        if args.workload == 2 and TRAFFIC_PER_PARTICLE_STEP.get(args.grid_layout) is not None:
+        if args.workload == 2 and TRAFFIC_PER_PARTICLE_STEP.get(args.grid_layout) is not None and \
+                (wl.tuned or {}).get("pairs", 0) == TRAFFIC_KERNEL_PAIRS:
             traffic = TRAFFIC_PER_PARTICLE_STEP[args.grid_layout] * units_rank
         roofline = {"bound": "alu", "pipe": "fp32", "achieved": achieved, "peak": peak_ops, "unit": "TOP/s",
                     "frac": achieved / peak_ops, "traffic": traffic,
@@ -676,6 +786,8 @@ def run_ours(args):
         line["adjoint"] = adjoint
     if grid_node is not None:
         line["grid_node"] = grid_node
+    if others is not None:
+        line["workloads"] = others
     if rank == 0:
         print(json.dumps(line), flush=True)
     wl.close()

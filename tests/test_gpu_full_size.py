@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 from paper_2307_04843_gb300 import workloads
-from support import THREADS, rel_u_err, subset
+from support import THREADS, conditioning, explained_by_conditioning, fp64_momenta, rel_u_err, subset
 
 
 def _check(out, ref):
@@ -104,7 +104,16 @@ def test_workload4_full_size_samples(tmp_path):
     idx = np.unique(np.concatenate([np.random.default_rng(4).choice(near, 8, replace=False),
                                     _sample(cfg["n"], 6, 4)]))
     ref = oracle.push(cfg["pulse"], subset(parts, idx), cfg["t0"], cfg["dt"], cfg["n_steps"], threads=THREADS)
-    _check(subset(out, idx), ref)
+    e = rel_u_err(subset(out, idx), ref)
+    assert np.median(e) <= 1e-4, np.median(e)
+    # electrons near the moving focus can be ill-conditioned (see
+    # test_gpu_ensemble): above 1e-3 only where the conditioning explains it
+    over = np.flatnonzero(e > 1e-3)
+    if over.size:
+        sub = subset(parts, idx)
+        ref64 = fp64_momenta(cfg["pulse"], sub, cfg["t0"], cfg["dt"], cfg["n_steps"])
+        d7, dr = conditioning(cfg["pulse"], sub, over, ref64, cfg["t0"], cfg["dt"], cfg["n_steps"], None, 97)
+        assert np.all(explained_by_conditioning(e[over], d7, dr)), (e[over], d7, dr)
     assert np.max(np.abs(ref["ux"])) > 0.1
 
 
