@@ -26,9 +26,8 @@
  *     library allocates only its handle and the handle's small parameter
  *     buffers (in ap_init_pulse), never on the push path.
  *   - Calls that take a stream are asynchronous and stream-ordered.  Errors
- *     found on the device (non-finite state, exhausted bounded wait) are
- *     recorded in the handle's device status word and reported by
- *     ap_sync_status.
+ *     found on the device (a non-finite particle state) are recorded in the
+ *     handle's device status word and reported by ap_sync_status.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
  *   - Particle state semantics (leapfrog): on entry x is at t0 and u at
  *     t0 - dt/2; after n_steps steps x is at t0 + n_steps dt and u at
@@ -54,7 +53,9 @@ extern "C" {
 #define AP_ERR_ALIGN -2      /* a device pointer is not 16-byte aligned */
 #define AP_ERR_CUDA -3       /* a CUDA runtime call failed */
 #define AP_ERR_NONFINITE -4  /* a particle state or field became NaN/Inf */
-#define AP_ERR_TIMEOUT -5    /* a bounded device-side wait gave up */
+#define AP_ERR_TIMEOUT -5    /* reserved: no entry point returns it.  No kernel of this library
+                                waits on a flag, on another block or on another rank (every
+                                loop is bounded by a count), so no device-side wait can expire */
 #define AP_ERR_WORKSPACE -6  /* caller workspace too small */
 #define AP_ERR_UNSUPPORTED -7 /* combination not built (e.g. Yee dispersion with a flying focus) */
 
@@ -358,8 +359,11 @@ int ap_gather_push_batched(ap_handle h, const ap_particles *p, const ap_grid *g,
  * the particle arrays, grid and diagnostics.  Arguments and results are those
  * of ap_gather_push_batched.
  *   - The first call on a device looks up the array's device address (with
- *     that device current) and caches it; make that first call before any
- *     stream capture.
+ *     that device current) and caches it with the identity of the device's
+ *     CUDA context; a call in a new context of that device (after
+ *     cudaDeviceReset, for instance) looks it up again.  Make the first call
+ *     on a device, and the first after its context was re-created, before
+ *     any stream capture.
  *   - Every call on a device shares the one array; the tile counter in it is
  *     zeroed by each call on `stream`, but calls that overlap on the GPU race
  *     on it and must be serialised by the caller.
@@ -405,8 +409,7 @@ int ap_push_adjoint(ap_handle h, const ap_particles *p0, const ap_grid *g, doubl
                     void *stream);
 
 /* Waits for `stream`, then returns and clears the handle's device status
- * word: AP_OK, AP_ERR_NONFINITE or AP_ERR_TIMEOUT; AP_ERR_CUDA if the wait
- * itself failed. */
+ * word: AP_OK or AP_ERR_NONFINITE; AP_ERR_CUDA if the wait itself failed. */
 int ap_sync_status(ap_handle h, void *stream);
 
 /* Number of sets in the handle, or AP_ERR_ARG. */

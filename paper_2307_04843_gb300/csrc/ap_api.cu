@@ -581,7 +581,7 @@ const char *ap_status_string(int status) {
     case AP_ERR_ALIGN: return "device pointer not 16-byte aligned";
     case AP_ERR_CUDA: return "CUDA runtime error";
     case AP_ERR_NONFINITE: return "non-finite particle state or field";
-    case AP_ERR_TIMEOUT: return "bounded device wait gave up";
+    case AP_ERR_TIMEOUT: return "reserved (no device-side wait exists in this library)";
     case AP_ERR_WORKSPACE: return "workspace too small";
     case AP_ERR_UNSUPPORTED: return "unsupported combination";
     default: return "unknown status";
@@ -834,7 +834,6 @@ int ap_sync_status(ap_handle h, void *stream) {
       cudaStreamSynchronize(s) != cudaSuccess)
     return AP_ERR_CUDA;
   if (v & apt::kStatusNonfinite) return AP_ERR_NONFINITE;
-  if (v & apt::kStatusTimeout) return AP_ERR_TIMEOUT;
   return AP_OK;
 }
 

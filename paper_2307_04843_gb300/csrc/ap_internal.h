@@ -190,6 +190,5 @@ int drop_cell_layout(GridView &v);
 
 // status bits written by kernels
 constexpr int kStatusNonfinite = 1;
-constexpr int kStatusTimeout = 2;
 
 }  // namespace apt

@@ -9,6 +9,7 @@
 // workspace; this entry point instead keeps that scratch (the tile-queue
 // counter of the persistent launch) in a file-scope __device__ array that
 // every GPU loading the library holds until the process exits.
+#include <cuda.h>  // driver types only: the two driver calls are resolved at run time
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -26,17 +27,53 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void *g_scratch_ptr[kMaxDevices] = {nullptr};
+unsigned long long g_context_id[kMaxDevices] = {0};
 
-// Device address of the scratch array on the current device, looked up
-// once per device with that device current.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Process-unique id of the calling thread's current CUDA context, 0 when it
+// cannot be read.  The driver functions are resolved through the runtime,
+// so the library does not link the driver library.  Called under g_mutex.
+unsigned long long current_context_id() {
+  static bool resolved = false;
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!resolved) {
+    resolved = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(p);
+  }
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS)
+    return id;
+  return 0;
+}
+
+// Device address of the scratch array on the current device.  It is looked
+// up once per device with that device current, and again whenever the
+// device's context is not the one the cached address belongs to (a context
+// re-created after cudaDeviceReset loads the module afresh, at a new
+// address); where the context cannot be identified it is looked up on every
+// call.
 int scratch_for_current_device(void **out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AP_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_ptr[dev] || ctx == 0 || ctx != g_context_id[dev]) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_batch_scratch) != cudaSuccess || !p) return AP_ERR_CUDA;
     g_scratch_ptr[dev] = p;
+    g_context_id[dev] = current_context_id();  // current now, if it was not before the lookup
   }
   *out = g_scratch_ptr[dev];
   return AP_OK;
