@@ -338,11 +338,12 @@ NODE_N = 256           # staggered grid edge for the node-evaluation rate
 # FP32 operations of the Gaussian (longitudinal terms on) on the six
 # staggered positions of the nodes: the position part once per component of a
 # node (transverse exponent, angle and its reduction, complex assembly, the one
-# component written: 21), and the z/t part once per (y, z) row for each of its
-# two z levels (float-float carrier phase and envelope argument 32, envelope
-# 2, q = 1/(1 - i zeta) 3), since every node of a row shares them
+# component written: 21).  The z/t part (float-float carrier phase and
+# envelope argument 32, envelope 2, q = 1/(1 - i zeta) 3, for each of the two
+# z levels) is computed once per z index per warp's run of rows: fewer than
+# 0.01 operations per node, not counted.
 NODE_OPS_PER_NODE = 6 * 21
-NODE_OPS_PER_ROW = 2 * 37
+NODE_OPS_PER_ROW = 0
 YEE_LINES, YEE_NZ, YEE_STEPS = 152, 8192, 2000
 # 1-D lines with a cold-plasma current (Sec. 4): n_e = 1e-3 n_c, a g = 4
 # super-Gaussian of tau = 30 at 20 cells per wavelength, c dt/dz = 0.9

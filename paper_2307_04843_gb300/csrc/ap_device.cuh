@@ -535,22 +535,43 @@ __device__ __forceinline__ void current_plane(const Pulse<R> &P, const Local<R> 
 // MOVING: closed-form flying focus (Sec. 3.3): the same profile with
 // x_f - x -> xi0 - xi, i.e. zeta = ((z - z_f) - beta_f (t - t_f)) / z_R',
 // z_R' = (1 - beta_f) z_R (inv_zR holds 1/z_R').
+// The Gaussian beam in two parts: what depends on z and t only (the
+// envelope, q and the carrier phase), which the grid-node kernels compute
+// once per z level and share along a row of nodes, and the transverse part.
+template <typename R>
+struct BeamZ {
+  Cx<R> q;     // 1 / (1 - i zeta)
+  R amp_mul;   // A times the envelope's multiplicative factor
+  R l2;        // the envelope's base-2 exponent
+  R psi;       // reduced carrier phase
+};
+
 template <bool MOVING = false, class PT, typename R>
-__device__ __forceinline__ void fields_gauss(const PT &P, const Local<R> &L, R E[3], R B[3]) {
+__device__ __forceinline__ BeamZ<R> gauss_z(const PT &P, const Local<R> &L) {
   R mul, l2;
   envelope(P, L.eta, mul, l2);
   R zeta;
   if constexpr (MOVING) zeta = fma(-P.beta_f, L.T, L.dz) * P.inv_zR;
   else zeta = L.dz * P.inv_zR;
   R inv = rcp_r(fma(zeta, zeta, R(1)));
-  Cx<R> q{inv, zeta * inv};
-  R a = (L.x * L.x + L.y * L.y) * P.inv_w0sq;
-  R mag = P.amp * mul * exp2_r(fma(a * q.re, R(-kLog2e), l2));
-  R ang = reduce_angle<R>(L.psi - a * q.im);
+  return {Cx<R>{inv, zeta * inv}, P.amp * mul, l2, L.psi};
+}
+
+template <class PT, typename R>
+__device__ __forceinline__ void gauss_xy(const PT &P, const BeamZ<R> &Z, R x, R y, R E[3], R B[3]) {
+  const Cx<R> q = Z.q;
+  R a = (x * x + y * y) * P.inv_w0sq;
+  R mag = Z.amp_mul * exp2_r(fma(a * q.re, R(-kLog2e), Z.l2));
+  R ang = reduce_angle<R>(Z.psi - a * q.im);
   R s, c;
   sincos_r(ang, &s, &c);
   Cx<R> U = cmul(q, Cx<R>{mag * c, mag * s});
-  finish_beam(P, L.x, L.y, U, cmul(q, U), R(-2) * P.inv_w0sq, P.lon != 0, E, B);
+  finish_beam(P, x, y, U, cmul(q, U), R(-2) * P.inv_w0sq, P.lon != 0, E, B);
+}
+
+template <bool MOVING = false, class PT, typename R>
+__device__ __forceinline__ void fields_gauss(const PT &P, const Local<R> &L, R E[3], R B[3]) {
+  gauss_xy(P, gauss_z<MOVING>(P, L), L.x, L.y, E, B);
 }
 
 // Laguerre-Gaussian LG_pl (textbook; the paper names the family in Sec. 3.1):
@@ -1001,6 +1022,16 @@ __device__ __forceinline__ void grid_slots_init(CellSlots &gc, void *slots_base)
   gc.step = 16u * blockDim.x;
 }
 
+// The record of the cell at grid units (fx, fy, fz) into the cache, and the
+// weights inside it: 12 16-byte cp.async copies into the thread's slots.
+__device__ __forceinline__ void cell_refetch(const GridView &g, CellSlots &gc, float fx, float fy, float fz,
+                                             float &wx, float &wy, float &wz) {
+  const size_t cell = locate_cell(g, fx, fy, fz, gc.ox, gc.oy, gc.oz, wx, wy, wz);
+  const float4 *src = g.cells + 12 * cell;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) cp_async16(gc.s0 + k * gc.step, src + k);
+}
+
 // Every lane of the warp calls this together (warp-uniform refetch branch).
 __device__ __forceinline__ void grid_fetch(const GridView &g, CellSlots &gc, float x, float y,
                                            float z) {
@@ -1011,12 +1042,7 @@ __device__ __forceinline__ void grid_fetch(const GridView &g, CellSlots &gc, flo
   // inside the cached cell (faces included) iff max |w - 1/2| <= 1/2
   const float dev = fmaxf(fabsf(wx - 0.5f), fmaxf(fabsf(wy - 0.5f), fabsf(wz - 0.5f)));
   const bool need = !(dev <= 0.5f);
-  if (__any_sync(0xffffffffu, need) && need) {
-    const size_t cell = locate_cell(g, fx, fy, fz, gc.ox, gc.oy, gc.oz, wx, wy, wz);
-    const float4 *src = g.cells + 12 * cell;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) cp_async16(gc.s0 + k * gc.step, src + k);
-  }
+  if (__any_sync(0xffffffffu, need) && need) cell_refetch(g, gc, fx, fy, fz, wx, wy, wz);
   gc.wx = wx;
   gc.wy = wy;
   gc.wz = wz;
@@ -1054,6 +1080,15 @@ __device__ __forceinline__ void grid_slots_init(CellRegs &gc, void *) {
   for (int k = 0; k < 12; ++k) gc.c[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
+// The same into the cache registers: 12 16-byte loads.
+__device__ __forceinline__ void cell_refetch(const GridView &g, CellRegs &gc, float fx, float fy, float fz,
+                                             float &wx, float &wy, float &wz) {
+  const size_t cell = locate_cell(g, fx, fy, fz, gc.ox, gc.oy, gc.oz, wx, wy, wz);
+  const float4 *src = g.cells + 12 * cell;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) gc.c[k] = __ldg(src + k);
+}
+
 __device__ __forceinline__ void grid_fetch(const GridView &g, CellRegs &gc, float x, float y,
                                            float z) {
   const float fx = grid_unit<float>(x, g.inv_d[0], g.off[0], g.nx);
@@ -1063,12 +1098,7 @@ __device__ __forceinline__ void grid_fetch(const GridView &g, CellRegs &gc, floa
   // inside the cached cell (faces included) iff max |w - 1/2| <= 1/2
   const float dev = fmaxf(fabsf(wx - 0.5f), fmaxf(fabsf(wy - 0.5f), fabsf(wz - 0.5f)));
   const bool need = !(dev <= 0.5f);
-  if (__any_sync(0xffffffffu, need) && need) {
-    const size_t cell = locate_cell(g, fx, fy, fz, gc.ox, gc.oy, gc.oz, wx, wy, wz);
-    const float4 *src = g.cells + 12 * cell;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) gc.c[k] = __ldg(src + k);
-  }
+  if (__any_sync(0xffffffffu, need) && need) cell_refetch(g, gc, fx, fy, fz, wx, wy, wz);
   gc.wx = wx;
   gc.wy = wy;
   gc.wz = wz;

@@ -187,7 +187,7 @@ __device__ __forceinline__ void push_two(const Pulse<float> &P, const PushArgs &
   }
   F2 u[3] = {F2(ua[0], ub[0]), F2(ua[1], ub[1]), F2(ua[2], ub[2])};
   Pos2 pos;
-  pos.load(X, Y, Z);
+  pos.load(X, Y, Z, P.z_f);
   TimeBase<AP_FP32_PHASEFF> tb;
   tb.init(P, a.t0, a.dt);
   const float dts = (float)a.dt;
@@ -221,11 +221,7 @@ __device__ __forceinline__ void push_two(const Pulse<float> &P, const PushArgs &
       for (int k = 0; k < cnt; ++k) {
         const StepFF st = wsteps[k];
         const Local<F2> L = local_coords2(P, st, pos);
-        if constexpr (GRID != kGridNone) {
-          const F2 zr = pos.zr();
-          grid_fetch(a.grid, gca, L.x.x, L.y.x, zr.x);
-          grid_fetch(a.grid, gcb, L.x.y, L.y.y, zr.y);
-        }
+        if constexpr (GRID != kGridNone) grid_fetch2(a.grid, gca, gcb, L.x, L.y, pos.zr(P.zf_hi, P.zf_lo));
         F2 E[3], B[3];
         analytic_fields<KIND, AP_FP32_PHASEFF, F2>(P, L, E, B);
         if constexpr (GRID != kGridNone) {
@@ -261,10 +257,10 @@ __device__ __forceinline__ void push_two(const Pulse<float> &P, const PushArgs &
     const long long i = idx[h];
     const FF px{h ? pos.x.hi.y : pos.x.hi.x, h ? pos.x.lo.y : pos.x.lo.x};
     const FF py{h ? pos.y.hi.y : pos.y.hi.x, h ? pos.y.lo.y : pos.y.lo.x};
-    const FF pz{h ? pos.z.hi.y : pos.z.hi.x, h ? pos.z.lo.y : pos.z.lo.x};
+    const FF pz{h ? pos.dz.hi.y : pos.dz.hi.x, h ? pos.dz.lo.y : pos.dz.lo.x};
     a.x[i] = (double)px.hi + (double)px.lo;
     a.y[i] = (double)py.hi + (double)py.lo;
-    a.z[i] = (double)pz.hi + (double)pz.lo;
+    a.z[i] = ((double)pz.hi + (double)pz.lo) + P.z_f;
     const float fu[3] = {h ? u[0].y : u[0].x, h ? u[1].y : u[1].x, h ? u[2].y : u[2].x};
     static_cast<float *>(a.ux)[i] = fu[0];
     static_cast<float *>(a.uy)[i] = fu[1];
@@ -852,6 +848,93 @@ __global__ void __launch_bounds__(256) nodes_row_kernel(const __grid_constant__ 
   }
 }
 
+// The row kernel with two nodes per lane and iteration (float-float, beams):
+// lane l takes x = l + 64 m and l + 64 m + 32, the two halves of every packed
+// value (ap_pair.cuh), so the position part of the six evaluations -- the
+// only per-node work -- issues once for both nodes.  Each warp takes a
+// contiguous run of rows, so the z/t part of its rows (carrier phase and
+// envelope argument; for Gaussian beams also the envelope and q) is computed
+// only when the z index changes, once per run of up to ny rows, instead of
+// once per row.  Stores stay coalesced: the warp writes 32 consecutive
+// elements for each half.
+template <int KIND, typename T>
+__global__ void __launch_bounds__(256) nodes_row_pair_kernel(const __grid_constant__ Pulse<float> P,
+                                                             const __grid_constant__ NodeArgs a) {
+  using W = typename std::conditional<(sizeof(T) > sizeof(float)), T, float>::type;
+  constexpr bool kGaussZ = KIND == AP_GAUSS || KIND == AP_FLYING_CF;
+  unsigned want = 0u;
+  for (int q = 0; q < a.n_comp; ++q) want |= 1u << a.comp[q];
+  const long long rows = (long long)a.ny * a.nz;
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const long long per = (rows + warps - 1) / warps;
+  const long long r0 = wid * per, r1 = r0 + per < rows ? r0 + per : rows;
+  const float flane = (float)lane;
+  TimeBase<AP_FP32_PHASEFF> tb;
+  tb.init(P, a.t, 0.0);
+  const StepFF st = tb.at(0);
+  constexpr int kOx[6] = {1, 0, 0, 0, 1, 1}, kOy[6] = {0, 1, 0, 1, 0, 1}, kOz[6] = {0, 0, 1, 1, 1, 0};
+  int kcur = -1;
+  Local<F2> Lz[2];
+  BeamZ<F2> Bz[2];
+  for (long long r = r0; r < r1; ++r) {
+    const int k = (int)(r / a.ny);
+    const int j = (int)(r - (long long)k * a.ny);
+    if (k != kcur) {  // uniform across the warp
+      kcur = k;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        Pos<AP_FP32_PHASEFF> pos;
+        pos.x = FF{0.0f, 0.0f};
+        pos.y = FF{0.0f, 0.0f};
+        pos.z = node_coord_ff((float)k + (h ? 0.5f : 0.0f), a.lo_hi[2], a.lo_lo[2], a.d_hi[2], a.d_lo[2]);
+        const Local<float> l = local_coords<AP_FP32_PHASEFF>(P, st, pos);
+        if constexpr (kGaussZ) {
+          const BeamZ<float> b = gauss_z<KIND == AP_FLYING_CF>(P, l);
+          Bz[h] = BeamZ<F2>{Cx<F2>{F2(b.q.re), F2(b.q.im)}, F2(b.amp_mul), F2(b.l2), F2(b.psi)};
+        } else {
+          Lz[h] = Local<F2>{F2(l.x), F2(l.y), F2(l.dz), F2(l.psi), F2(l.eta), F2(l.T), F2(l.phi_hi),
+                            F2(l.phi_lo)};
+        }
+      }
+    }
+    const float ys[2] = {fmaf((float)j, a.d_hi[1], a.lo_hi[1]), fmaf((float)j + 0.5f, a.d_hi[1], a.lo_hi[1])};
+    const long long base = r * a.nx;
+    float fi = flane;
+    for (int i = lane; i < a.nx; i += 64, fi += 64.0f) {
+      const bool second = i + 32 < a.nx;
+      F2 xs[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float o = h ? 0.5f : 0.0f;
+        xs[h] = fma(F2(fi + o, fi + (32.0f + o)), F2(a.d_hi[0]), F2(a.lo_hi[0]));
+      }
+      F2 v[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        F2 E[3], B[3];
+        if constexpr (kGaussZ) {
+          gauss_xy(P, Bz[kOz[c]], xs[kOx[c]], F2(ys[kOy[c]]), E, B);
+        } else {
+          Local<F2> L = Lz[kOz[c]];
+          L.x = xs[kOx[c]];
+          L.y = F2(ys[kOy[c]]);
+          analytic_fields<KIND, AP_FP32_PHASEFF, F2>(P, L, E, B);
+        }
+        v[c] = c < 3 ? E[c] : B[c - 3];
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        if (!((want >> c) & 1u)) continue;
+        T *f = static_cast<T *>(a.f[c]) + base;
+        f[i] = a.accumulate ? (T)((W)f[i] + (W)v[c].x) : (T)v[c].x;
+        if (second) f[i + 32] = a.accumulate ? (T)((W)f[i + 32] + (W)v[c].y) : (T)v[c].y;
+      }
+    }
+  }
+}
+
 // One warp writes the value v along a row of n elements (store, or add to
 // what the row holds, rounding once to T): a scalar head up to the first
 // 16-byte boundary, then 16-byte vector stores, then a scalar tail.  The row
@@ -975,6 +1058,18 @@ int launch_nodes_t(const Pulse<Real<PREC>> &P, const NodeArgs &a, void *stream) 
     if (gx > cap) gx = cap;
     if (gx < 1) gx = 1;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if constexpr (PREC == AP_FP32_PHASEFF && KIND != AP_PLANE) {
+      // beams in float-float arithmetic: two nodes per lane, packed; one
+      // resident wave of blocks, each warp a contiguous run of rows
+      if (!a.current) {
+        auto kern = a.f64 ? nodes_row_pair_kernel<KIND, double> : nodes_row_pair_kernel<KIND, float>;
+        long long gp = (long long)a.sm_count * occupancy_blocks(kern, block, 0);
+        if (gp > (rows + 7) / 8) gp = (rows + 7) / 8;
+        if (gp < 1) gp = 1;
+        kern<<<(unsigned)gp, block, 0, s>>>(P, a);
+        return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+      }
+    }
     if (a.f64) nodes_row_kernel<KIND, PREC, double><<<(unsigned)gx, block, 0, s>>>(P, a);
     else nodes_row_kernel<KIND, PREC, float><<<(unsigned)gx, block, 0, s>>>(P, a);
     return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;

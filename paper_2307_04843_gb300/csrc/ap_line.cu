@@ -72,30 +72,34 @@ __device__ __forceinline__ Local<float> node_local_ff(const Pulse<float> &P, con
   return L;
 }
 
-// E1 at t_n and J1 at t_n + dt/2 at one node of the float split line, for a
-// plane wave polarised along x (Eqs. plane_func, j1): the J1 carrier phase is
-// the E1 phase advanced by omega dt/2, applied as a fixed rotation
-// (sin, cos of omega dt/2 in sdl, cdl); the envelope and its log-derivatives
-// are evaluated at eta and eta + dt/2.
-__device__ __forceinline__ void line_sources_ff(const Pulse<float> &P, const StepFF &st, float kd_hi,
-                                                float kd_lo, float dz, float sdl, float cdl, float hdt,
-                                                float &E1, float &J1) {
-  const Local<float> L = node_local_ff(P, st, kd_hi, kd_lo, dz);
-  float mul, l2;
-  envelope(P, L.eta, mul, l2);
-  float a = P.amp * mul;
-  if (l2 != 0.0f) a *= exp2_r(l2);
-  float s, c;
-  sincos_r(L.psi, &s, &c);
+// E1 at t_n and J1 at t_n + dt/2 at two nodes of the float split line at once
+// (the halves of every packed value, ap_pair.cuh: one issue slot per FP32
+// operation for both nodes, the MUFU operations one per node), for a plane
+// wave polarised along x (Eqs. plane_func, j1): the J1 carrier phase is the
+// E1 phase advanced by omega dt/2, applied as a fixed rotation (sin, cos of
+// omega dt/2 in sdl, cdl); the envelope and its log-derivatives are evaluated
+// at eta and eta + dt/2.
+__device__ __forceinline__ void line_sources_ff2(const Pulse<float> &P, const StepFF &st, F2 kd_hi, F2 kd_lo,
+                                                 F2 dz, float sdl, float cdl, float hdt, F2 &E1, F2 &J1) {
+  const FF2 ps = two_diff(F2(st.C), kd_hi);
+  const F2 psi = reduce_ff(ps.hi, ps.lo - kd_lo);
+  const float Tf = __fadd_rn(st.Th, st.Tl);
+  const F2 eta0 = fma(dz, F2(-P.inv_vg), F2(Tf));
+  F2 mul, l2;
+  envelope(P, eta0, mul, l2);
+  F2 a = F2(P.amp) * mul;
+  if (l2 != F2(0.0f)) a *= exp2_r(l2);  // exp2(0) = 1 exactly for a half without an exponent
+  F2 s, c;
+  sincos_r(psi, &s, &c);
   E1 = a * c;
-  const float eta = L.eta + hdt;
+  const F2 eta = eta0 + F2(hdt);
   envelope(P, eta, mul, l2);
-  float aj = P.jamp * P.amp * mul;
-  if (l2 != 0.0f) aj *= exp2_r(l2);
-  const float sj = fmaf(s, cdl, c * sdl), cj = fmaf(c, cdl, -(s * sdl));
-  float L1, L2;
+  F2 aj = F2(P.jamp * P.amp) * mul;
+  if (l2 != F2(0.0f)) aj *= exp2_r(l2);
+  const F2 sj = fma(s, F2(cdl), c * F2(sdl)), cj = fma(s, F2(-sdl), c * F2(cdl));
+  F2 L1, L2;
   envelope_logd(P, eta, L1, L2);
-  const Cx<float> V = finite_duration(Cx<float>{aj * cj, aj * sj}, 1.0f, L1, L2, P.inv_w);
+  const Cx<F2> V = finite_duration(Cx<F2>{aj * cj, aj * sj}, 1.0f, L1, L2, P.inv_w);
   J1 = V.im;  // Re[p (-i V)] with p = (1, 0)
 }
 
@@ -176,6 +180,26 @@ __global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant_
       st_j = tb.at(2 * n + 1);
     }
     // J^{n+1/2} = J^{n-1/2} + a_k (E1 + E2)^n;  E^{n+1} = (E^n - r dB) - dt (J - J1)^{n+1/2}
+    if constexpr (kFF) {
+      // the thread's nodes k and k + bd in the two halves of one packed
+      // source evaluation; each node's update as below
+      auto update = [&](int k, float e1, float j1) {
+        const T ek = e[k];
+        const T jk = l_add(j[k], l_mul(q[k], l_add(e1, ek)));
+        j[k] = jk;
+        if (k >= 1) e[k] = l_sub(l_sub(ek, l_mul(r, l_sub(b[k], b[k - 1]))), l_mul(dt, l_sub(jk, j1)));
+      };
+      for (int k = t; k < nz; k += 2 * bd) {
+        const int k2 = k + bd;
+        const bool two = k2 < nz;
+        const int kk = two ? k2 : k;  // the second half repeats node k when k + bd is past the line
+        F2 e1, j1;
+        line_sources_ff2(P, st_e, F2(kdh[k], kdh[kk]), F2(kdl[k], kdl[kk]), F2(dzn[k], dzn[kk]), sdl, cdl, hdt,
+                         e1, j1);
+        update(k, e1.x, j1.x);
+        if (two) update(k2, e1.y, j1.y);
+      }
+    } else
     for (int k = t; k < nz; k += bd) {
       const T ek = e[k];
       T drive = ek;

@@ -150,16 +150,19 @@ template <>
 struct IsPair<F2> : std::true_type {};
 
 // Positions of the two particles of a thread as float-float pairs, the same
-// compensated accumulation as Pos<AP_FP32_PHASEFF>.
+// compensated accumulation as Pos<AP_FP32_PHASEFF>.  The longitudinal
+// coordinate is held relative to the pulse's focus, dz = z - z_f (formed in
+// double on load), since the carrier phase needs dz to float-float accuracy
+// every step and the absolute z only in float (for the grid).
 struct Pos2 {
-  FF2 x, y, z;
-  __device__ __forceinline__ void load(const double X[2], const double Y[2], const double Z[2]) {
+  FF2 x, y, dz;
+  __device__ __forceinline__ void load(const double X[2], const double Y[2], const double Z[2], double zf) {
     const FF a = split_double(X[0]), b = split_double(X[1]);
     x = {F2(a.hi, b.hi), F2(a.lo, b.lo)};
     const FF c = split_double(Y[0]), d = split_double(Y[1]);
     y = {F2(c.hi, d.hi), F2(c.lo, d.lo)};
-    const FF e = split_double(Z[0]), f = split_double(Z[1]);
-    z = {F2(e.hi, f.hi), F2(e.lo, f.lo)};
+    const FF e = split_double(Z[0] - zf), f = split_double(Z[1] - zf);
+    dz = {F2(e.hi, f.hi), F2(e.lo, f.lo)};
   }
   __device__ __forceinline__ static void acc(FF2 &p, F2 d) {
     const F2 y = d + p.lo;
@@ -170,11 +173,14 @@ struct Pos2 {
   __device__ __forceinline__ void advance(F2 vx, F2 vy, F2 vz, F2 dt_xy, F2 dt) {
     acc(x, dt_xy * vx);
     acc(y, dt_xy * vy);
-    acc(z, dt * vz);
+    acc(dz, dt * vz);
   }
   __device__ __forceinline__ F2 xr() const { return x.hi + x.lo; }
   __device__ __forceinline__ F2 yr() const { return y.hi + y.lo; }
-  __device__ __forceinline__ F2 zr() const { return z.hi + z.lo; }
+  // absolute z in float, from z_f = zf_hi + zf_lo
+  __device__ __forceinline__ F2 zr(float zf_hi, float zf_lo) const {
+    return (dz.hi + F2(zf_hi)) + (dz.lo + F2(zf_lo));
+  }
 };
 
 // Local coordinates of both particles at one step (float-float phase), the
@@ -183,9 +189,7 @@ struct Pos2 {
 __device__ __forceinline__ Local<F2> local_coords2(const Pulse<float> &P, const StepFF &st,
                                                    const Pos2 &pos) {
   Local<F2> L;
-  // dz = z - z_f
-  FF2 dz = two_diff(pos.z.hi, F2(P.zf_hi));
-  dz.lo = dz.lo + (pos.z.lo - F2(P.zf_lo));
+  const FF2 dz = pos.dz;  // z - z_f
   // psi = C_n - k dz, k dz = kp + ke with -ke from the negated constant
   const F2 kp = F2(P.k_hi) * dz.hi;
   const F2 nke = two_prod_nerr(dz.hi, F2(-P.k_hi), kp);
@@ -203,6 +207,31 @@ __device__ __forceinline__ Local<F2> local_coords2(const Pulse<float> &P, const 
   L.phi_hi = ph.hi;
   L.phi_lo = ph.lo + (F2(st.Tl) - dz.lo);
   return L;
+}
+
+// The cell test and weights of a thread's two particles with packed
+// arithmetic (grid units, offsets from each cached cell), then each
+// particle's own warp-uniform refetch branch, as grid_fetch does per particle.
+template <class CA, class CB>
+__device__ __forceinline__ void grid_fetch2(const GridView &g, CA &ga, CB &gb, F2 x, F2 y, F2 z) {
+  F2 f[3] = {fma(x, F2(g.inv_d[0]), F2(g.off[0])), fma(y, F2(g.inv_d[1]), F2(g.off[1])),
+             fma(z, F2(g.inv_d[2]), F2(g.off[2]))};
+  const int n[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float top = (float)(n[a] - 1);
+    f[a] = F2(fminf(fmaxf(f[a].x, 0.0f), top), fminf(fmaxf(f[a].y, 0.0f), top));
+  }
+  F2 w[3] = {f[0] - F2(ga.ox, gb.ox), f[1] - F2(ga.oy, gb.oy), f[2] - F2(ga.oz, gb.oz)};
+  // inside the cached cell (faces included) iff max |w - 1/2| <= 1/2
+  const F2 d0 = w[0] - F2(0.5f), d1 = w[1] - F2(0.5f), d2 = w[2] - F2(0.5f);
+  const bool need_a = !(fmaxf(fabsf(d0.x), fmaxf(fabsf(d1.x), fabsf(d2.x))) <= 0.5f);
+  const bool need_b = !(fmaxf(fabsf(d0.y), fmaxf(fabsf(d1.y), fabsf(d2.y))) <= 0.5f);
+  float wa[3] = {w[0].x, w[1].x, w[2].x}, wb[3] = {w[0].y, w[1].y, w[2].y};
+  if (__any_sync(0xffffffffu, need_a) && need_a) cell_refetch(g, ga, f[0].x, f[1].x, f[2].x, wa[0], wa[1], wa[2]);
+  if (__any_sync(0xffffffffu, need_b) && need_b) cell_refetch(g, gb, f[0].y, f[1].y, f[2].y, wb[0], wb[1], wb[2]);
+  ga.wx = wa[0]; ga.wy = wa[1]; ga.wz = wa[2];
+  gb.wx = wb[0]; gb.wy = wb[1]; gb.wz = wb[2];
 }
 
 }  // namespace apt
