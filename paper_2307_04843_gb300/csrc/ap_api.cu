@@ -408,6 +408,8 @@ int make_grid(const ap_grid *g, apt::GridView &v) {
     v.inv_d[a] = (float)inv;
     v.off_d[a] = -g->lo[a] * inv;
     v.off[a] = (float)v.off_d[a];
+    v.top[a] = (float)(n[a] - 1);
+    v.top2[a] = (float)(n[a] - 2);
   }
   v.nx = g->nx;
   v.ny = g->ny;

@@ -714,10 +714,10 @@ __device__ __forceinline__ void grid_cache_reset(GridCache<R> &gc) {
   gc.ox = gc.oy = gc.oz = R(-16);
 }
 
-// position in grid units, clamped to the node range [0, n - 1]
+// position in grid units, clamped to the node range [0, top = n - 1]
 template <typename R>
-__device__ __forceinline__ R grid_unit(R v, R inv_d, R off, int n) {
-  return fmin(fmax(fma(v, inv_d, off), R(0)), R(n - 1));
+__device__ __forceinline__ R grid_unit(R v, R inv_d, R off, R top) {
+  return fmin(fmax(fma(v, inv_d, off), R(0)), top);
 }
 
 // Phase 1 of the gather, called at the start of a step: the particle's
@@ -728,13 +728,13 @@ template <typename R>
 __device__ __forceinline__ void grid_fetch(const GridView &g, GridCache<R> &gc, R x, R y, R z) {
   R fx, fy, fz;
   if constexpr (std::is_same<R, double>::value) {
-    fx = grid_unit<R>(x, g.inv_d_d[0], g.off_d[0], g.nx);
-    fy = grid_unit<R>(y, g.inv_d_d[1], g.off_d[1], g.ny);
-    fz = grid_unit<R>(z, g.inv_d_d[2], g.off_d[2], g.nz);
+    fx = grid_unit<R>(x, g.inv_d_d[0], g.off_d[0], R(g.nx - 1));
+    fy = grid_unit<R>(y, g.inv_d_d[1], g.off_d[1], R(g.ny - 1));
+    fz = grid_unit<R>(z, g.inv_d_d[2], g.off_d[2], R(g.nz - 1));
   } else {
-    fx = grid_unit<R>(x, g.inv_d[0], g.off[0], g.nx);
-    fy = grid_unit<R>(y, g.inv_d[1], g.off[1], g.ny);
-    fz = grid_unit<R>(z, g.inv_d[2], g.off[2], g.nz);
+    fx = grid_unit<R>(x, g.inv_d[0], g.off[0], R(g.top[0]));
+    fy = grid_unit<R>(y, g.inv_d[1], g.off[1], R(g.top[1]));
+    fz = grid_unit<R>(z, g.inv_d[2], g.off[2], R(g.top[2]));
   }
   R wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
   // still inside the cached cell (the upper face included, as for the last
@@ -883,25 +883,25 @@ __device__ __forceinline__ void grid_slots_init(GridSlots &gc, void *slots_base)
 // Every lane of the warp calls this together (warp-uniform refetch branch).
 __device__ __forceinline__ void grid_fetch(const GridView &g, GridSlots &gc, float x, float y,
                                            float z) {
-  const float fx = grid_unit<float>(x, g.inv_d[0], g.off[0], g.nx);
-  const float fy = grid_unit<float>(y, g.inv_d[1], g.off[1], g.ny);
-  const float fz = grid_unit<float>(z, g.inv_d[2], g.off[2], g.nz);
+  const float fx = grid_unit<float>(x, g.inv_d[0], g.off[0], g.top[0]);
+  const float fy = grid_unit<float>(y, g.inv_d[1], g.off[1], g.top[1]);
+  const float fz = grid_unit<float>(z, g.inv_d[2], g.off[2], g.top[2]);
   float wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
   // inside the cached cell (faces included) iff max |w - 1/2| <= 1/2
   const float dev = fmaxf(fabsf(wx - 0.5f), fmaxf(fabsf(wy - 0.5f), fabsf(wz - 0.5f)));
   const bool need = !(dev <= 0.5f);
   if (__any_sync(0xffffffffu, need) && need) {
     // lower cell corner without the conversion pipe (see the register cache)
-    auto corner = [](float f, int n, int &i) {
+    auto corner = [](float f, float top2, int &i) {
       float c = __fsub_rn(__fadd_rn(__fsub_rn(f, 0.5f), kRoundMagic), kRoundMagic);
-      c = fminf(fmaxf(c, 0.0f), (float)(n - 2));
+      c = fminf(fmaxf(c, 0.0f), top2);
       i = __float_as_int(__fadd_rn(c, kRoundMagic)) - __float_as_int(kRoundMagic);
       return c;
     };
     int ix, iy, iz;
-    gc.ox = corner(fx, g.nx, ix);
-    gc.oy = corner(fy, g.ny, iy);
-    gc.oz = corner(fz, g.nz, iz);
+    gc.ox = corner(fx, g.top2[0], ix);
+    gc.oy = corner(fy, g.top2[1], iy);
+    gc.oz = corner(fz, g.top2[2], iz);
     wx = fx - gc.ox;
     wy = fy - gc.oy;
     wz = fz - gc.oz;
@@ -993,33 +993,36 @@ __device__ __forceinline__ size_t cell_index(const GridView &g, int ix, int iy, 
 __device__ __forceinline__ size_t locate_cell(const GridView &g, float fx, float fy, float fz,
                                               float &ox, float &oy, float &oz, float &wx, float &wy,
                                               float &wz) {
-  auto corner = [](float f, int n, int &i) {
+  auto corner = [](float f, float top2, int &i) {
     float c = __fsub_rn(__fadd_rn(__fsub_rn(f, 0.5f), kRoundMagic), kRoundMagic);
-    c = fminf(fmaxf(c, 0.0f), (float)(n - 2));
+    c = fminf(fmaxf(c, 0.0f), top2);
     i = __float_as_int(__fadd_rn(c, kRoundMagic)) - __float_as_int(kRoundMagic);
     return c;
   };
   int ix, iy, iz;
-  ox = corner(fx, g.nx, ix);
-  oy = corner(fy, g.ny, iy);
-  oz = corner(fz, g.nz, iz);
+  ox = corner(fx, g.top2[0], ix);
+  oy = corner(fy, g.top2[1], iy);
+  oz = corner(fz, g.top2[2], iz);
   wx = fx - ox;
   wy = fy - oy;
   wz = fz - oz;
   return cell_index(g, ix, iy, iz);
 }
 
+// Slot k of thread t lies at 16 t + k kCellSlotStride: a compile-time stride
+// (room for blocks of up to 256 threads), so the 12 slot addresses of a step
+// are immediate offsets from one register.
+constexpr unsigned kCellSlotStride = 16u * 256u;
+
 struct CellSlots {
   float ox, oy, oz;  // lower corner of the cached cell in grid units
   float wx, wy, wz;  // weights of the current step
   unsigned s0;       // shared-window address of this thread's slot 0
-  unsigned step;     // bytes between consecutive slots of one thread
 };
 
 __device__ __forceinline__ void grid_slots_init(CellSlots &gc, void *slots_base) {
   gc.ox = gc.oy = gc.oz = -16.0f;
   gc.s0 = (unsigned)__cvta_generic_to_shared(slots_base) + 16u * threadIdx.x;
-  gc.step = 16u * blockDim.x;
 }
 
 // The record of the cell at grid units (fx, fy, fz) into the cache, and the
@@ -1029,15 +1032,15 @@ __device__ __forceinline__ void cell_refetch(const GridView &g, CellSlots &gc, f
   const size_t cell = locate_cell(g, fx, fy, fz, gc.ox, gc.oy, gc.oz, wx, wy, wz);
   const float4 *src = g.cells + 12 * cell;
 #pragma unroll
-  for (int k = 0; k < 12; ++k) cp_async16(gc.s0 + k * gc.step, src + k);
+  for (int k = 0; k < 12; ++k) cp_async16(gc.s0 + k * kCellSlotStride, src + k);
 }
 
 // Every lane of the warp calls this together (warp-uniform refetch branch).
 __device__ __forceinline__ void grid_fetch(const GridView &g, CellSlots &gc, float x, float y,
                                            float z) {
-  const float fx = grid_unit<float>(x, g.inv_d[0], g.off[0], g.nx);
-  const float fy = grid_unit<float>(y, g.inv_d[1], g.off[1], g.ny);
-  const float fz = grid_unit<float>(z, g.inv_d[2], g.off[2], g.nz);
+  const float fx = grid_unit<float>(x, g.inv_d[0], g.off[0], g.top[0]);
+  const float fy = grid_unit<float>(y, g.inv_d[1], g.off[1], g.top[1]);
+  const float fz = grid_unit<float>(z, g.inv_d[2], g.off[2], g.top[2]);
   float wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
   // inside the cached cell (faces included) iff max |w - 1/2| <= 1/2
   const float dev = fmaxf(fabsf(wx - 0.5f), fmaxf(fabsf(wy - 0.5f), fabsf(wz - 0.5f)));
@@ -1053,7 +1056,7 @@ __device__ __forceinline__ void grid_fetch(const GridView &g, CellSlots &gc, flo
 __device__ __forceinline__ void grid_values(const CellSlots &gc, float o[6]) {
   float4 c[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) c[k] = lds128(gc.s0 + k * gc.step);
+  for (int k = 0; k < 12; ++k) c[k] = lds128(gc.s0 + k * kCellSlotStride);
   cell_eval(c, gc.wx, gc.wy, gc.wz, o);
 }
 
@@ -1091,9 +1094,9 @@ __device__ __forceinline__ void cell_refetch(const GridView &g, CellRegs &gc, fl
 
 __device__ __forceinline__ void grid_fetch(const GridView &g, CellRegs &gc, float x, float y,
                                            float z) {
-  const float fx = grid_unit<float>(x, g.inv_d[0], g.off[0], g.nx);
-  const float fy = grid_unit<float>(y, g.inv_d[1], g.off[1], g.ny);
-  const float fz = grid_unit<float>(z, g.inv_d[2], g.off[2], g.nz);
+  const float fx = grid_unit<float>(x, g.inv_d[0], g.off[0], g.top[0]);
+  const float fy = grid_unit<float>(y, g.inv_d[1], g.off[1], g.top[1]);
+  const float fz = grid_unit<float>(z, g.inv_d[2], g.off[2], g.top[2]);
   float wx = fx - gc.ox, wy = fy - gc.oy, wz = fz - gc.oz;
   // inside the cached cell (faces included) iff max |w - 1/2| <= 1/2
   const float dev = fmaxf(fabsf(wx - 0.5f), fmaxf(fabsf(wy - 0.5f), fabsf(wz - 0.5f)));

@@ -79,6 +79,7 @@ struct GridView {
   double lo_d[3], inv_d_d[3];
   float off[3];           // -lo / d: grid units u = x inv_d + off
   double off_d[3];
+  float top[3], top2[3];  // n - 1 and n - 2 as floats (no per-step conversion)
 };
 
 // Diagnostics view.

@@ -63,8 +63,8 @@ struct CacheOf<AP_FP32_PHASEFF, kGridCellsReg> {
 template <int PREC, int GRID, int NP = 1>
 __host__ __device__ constexpr size_t grid_cache_bytes(int threads) {
   return PREC == AP_FP64 || GRID == kGridNone || GRID == kGridCellsReg ? 0
-         : GRID == kGridCells                                         ? 192u * NP * (size_t)threads
-         : GRID == kGridCellsMix                                      ? 192u * (size_t)threads
+         : GRID == kGridCells                                         ? 12u * kCellSlotStride * NP
+         : GRID == kGridCellsMix                                      ? 12u * kCellSlotStride
                                                                       : grid_slot_bytes(threads);
 }
 
@@ -206,7 +206,7 @@ __device__ __forceinline__ void push_two(const Pulse<float> &P, const PushArgs &
     grid_slots_init(gcb, slots);
   } else if constexpr (GRID != kGridNone) {
     grid_slots_init(gca, slots);
-    grid_slots_init(gcb, static_cast<unsigned char *>(slots) + 192u * blockDim.x);
+    grid_slots_init(gcb, static_cast<unsigned char *>(slots) + 12u * kCellSlotStride);
   }
   double *lf = a.diag.lf;
   StepFF *wsteps = s_steps + (threadIdx.x >> 5) * kStepChunk;

@@ -216,12 +216,9 @@ template <class CA, class CB>
 __device__ __forceinline__ void grid_fetch2(const GridView &g, CA &ga, CB &gb, F2 x, F2 y, F2 z) {
   F2 f[3] = {fma(x, F2(g.inv_d[0]), F2(g.off[0])), fma(y, F2(g.inv_d[1]), F2(g.off[1])),
              fma(z, F2(g.inv_d[2]), F2(g.off[2]))};
-  const int n[3] = {g.nx, g.ny, g.nz};
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float top = (float)(n[a] - 1);
-    f[a] = F2(fminf(fmaxf(f[a].x, 0.0f), top), fminf(fmaxf(f[a].y, 0.0f), top));
-  }
+  for (int a = 0; a < 3; ++a)
+    f[a] = F2(fminf(fmaxf(f[a].x, 0.0f), g.top[a]), fminf(fmaxf(f[a].y, 0.0f), g.top[a]));
   F2 w[3] = {f[0] - F2(ga.ox, gb.ox), f[1] - F2(ga.oy, gb.oy), f[2] - F2(ga.oz, gb.oz)};
   // inside the cached cell (faces included) iff max |w - 1/2| <= 1/2
   const F2 d0 = w[0] - F2(0.5f), d1 = w[1] - F2(0.5f), d2 = w[2] - F2(0.5f);
