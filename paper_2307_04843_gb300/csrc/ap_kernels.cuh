@@ -218,6 +218,7 @@ __device__ __forceinline__ void push_two(const Pulse<float> &P, const PushArgs &
       __syncwarp();  // no lane still reads the previous chunk
       if (lane < cnt) wsteps[lane] = tb.at(s0 + lane);
       __syncwarp();
+#pragma unroll 2
       for (int k = 0; k < cnt; ++k) {
         const StepFF st = wsteps[k];
         const Local<F2> L = local_coords2(P, st, pos);
