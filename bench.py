@@ -61,12 +61,17 @@ ALGO = {
 # ncu capture of the 1.6e6-particle x 4000-step case, scaled by particle-steps
 # (an upper bound at 1e7 particles: more particles share each cached cell);
 # None when the kernel changed after the capture.
+# DRAM bytes per particle-step of the workload-2 push kernel from the committed
+# ncu capture of the 1.6e6-particle x 4000-step case, scaled by particle-steps
+# (an upper bound at 1e7 particles: more particles share each cached cell);
+# None when the kernel changed after the capture.  The capture is of the
+# two-particle kernel with the hybrid cell cache (the autotuner's choice).
 TRAFFIC_PER_PARTICLE_STEP = {
     "nodes": None,
-    "cells": None,
+    "cells": 6.0486,  # (38.6484e9 read + 0.0626e9 written) / 6.4e9
     "arrays": None,
 }
-TRAFFIC_KERNEL_PAIRS = 1  # the particles-per-thread setting the capture was taken with
+TRAFFIC_KERNEL = dict(pairs=1, grid_cache=2)  # the launch setting the capture was taken with
 
 
 def parse():
@@ -94,6 +99,9 @@ def parse():
     ap.add_argument("--lines-only", action="store_true",
                     help="run only the Sec. 4 lines, one split-line and one traditional-line call "
                          "(a small case for profiling); prints their rates")
+    ap.add_argument("--legs-only", action="store_true",
+                    help="run only the grid-node, 1-D Yee and Sec. 4 line calls of the bench (the grid_node "
+                         "key; a case for profiling those kernels); prints their rates")
     ap.add_argument("--split-steps", type=int, default=200)
     ap.add_argument("--plasma-steps", type=int, default=2000)
     return ap.parse_args()
@@ -764,7 +772,7 @@ def run_ours(args):
         achieved = al["fp32"] * rate_k / 1e12
         traffic = None
         if args.workload == 2 and TRAFFIC_PER_PARTICLE_STEP.get(args.grid_layout) is not None and \
-                (wl.tuned or {}).get("pairs", 0) == TRAFFIC_KERNEL_PAIRS:
+                all((wl.tuned or {}).get(k, 0) == v for k, v in TRAFFIC_KERNEL.items()):
             traffic = TRAFFIC_PER_PARTICLE_STEP[args.grid_layout] * units_rank
         roofline = {"bound": "alu", "pipe": "fp32", "achieved": achieved, "peak": peak_ops, "unit": "TOP/s",
                     "frac": achieved / peak_ops, "traffic": traffic,
@@ -855,6 +863,15 @@ def main():
             import torch
             torch.cuda.set_device(0)
             print(json.dumps(line_rates(args.split_steps, args.plasma_steps)))
+            return
+        if args.legs_only:
+            import torch
+            from paper_2307_04843_gb300 import _lib, workloads
+            torch.cuda.set_device(0)
+            cfg = workloads.config(2)
+            legs = argparse.Namespace(cfg=cfg, h=_lib.Handle(cfg["pulse"]))
+            print(json.dumps(grid_node_rates(legs, torch.cuda.current_stream())))
+            legs.h.close()
             return
         run_ours(args)
 

@@ -879,9 +879,14 @@ __global__ void __launch_bounds__(256) nodes_row_pair_kernel(const __grid_consta
   int kcur = -1;
   Local<F2> Lz[2];
   BeamZ<F2> Bz[2];
-  for (long long r = r0; r < r1; ++r) {
-    const int k = (int)(r / a.ny);
-    const int j = (int)(r - (long long)k * a.ny);
+  // (j, k) of the run's first row by one division, then stepped row by row
+  int k = (int)(r0 / a.ny);
+  int j = (int)(r0 - (long long)k * a.ny);
+  for (long long r = r0; r < r1; ++r, ++j) {
+    if (j == a.ny) {
+      j = 0;
+      ++k;
+    }
     if (k != kcur) {  // uniform across the warp
       kcur = k;
 #pragma unroll
