@@ -163,10 +163,21 @@ __device__ __forceinline__ double push_one(const Pulse<Real<PREC>> &P, const Pus
 // particle keeps its own grid cell (its refetch is its own warp-uniform
 // branch) and the cell is evaluated with packed FMA over component pairs.
 // `v0`, `v1` are false for padding particles.  g receives the final gammas.
+// The block's pre-broadcast grid constants for grid_fetch2 (written by the
+// first four threads; the caller synchronises the block before use).
+__device__ __forceinline__ void grid_pair_consts(const GridView &g, float4 *gk) {
+  if (threadIdx.x < 3) {
+    const int ax = threadIdx.x;
+    gk[ax] = make_float4(g.inv_d[ax], g.inv_d[ax], g.off[ax], g.off[ax]);
+  } else if (threadIdx.x == 3) {
+    gk[3] = make_float4(0.5f, 0.5f, 0.0f, 0.0f);
+  }
+}
+
 template <int KIND, int GRID>
 __device__ __forceinline__ void push_two(const Pulse<float> &P, const PushArgs &a, long long i0,
                                          long long i1, bool v0, bool v1, StepFF *s_steps,
-                                         void *slots, double g[2]) {
+                                         void *slots, const float4 *gk, double g[2]) {
   static_assert(GRID == kGridNone || GRID == kGridCells || GRID == kGridCellsReg ||
                     GRID == kGridCellsMix,
                 "two-particle grid modes");
@@ -222,7 +233,8 @@ __device__ __forceinline__ void push_two(const Pulse<float> &P, const PushArgs &
       for (int k = 0; k < cnt; ++k) {
         const StepFF st = wsteps[k];
         const Local<F2> L = local_coords2(P, st, pos);
-        if constexpr (GRID != kGridNone) grid_fetch2(a.grid, gca, gcb, L.x, L.y, pos.zr(P.zf_hi, P.zf_lo));
+        if constexpr (GRID != kGridNone)
+          grid_fetch2(a.grid, gca, gcb, L.x, L.y, pos.zr(P.zf_hi, P.zf_lo), gk);
         F2 E[3], B[3];
         analytic_fields<KIND, AP_FP32_PHASEFF, F2>(P, L, E, B);
         if constexpr (GRID != kGridNone) {
@@ -310,6 +322,11 @@ __device__ __forceinline__ void push_body(const Pulse<Real<PREC>> &P, const Push
     for (int b = threadIdx.x; b < a.diag.bins; b += blockDim.x) s_hist[b] = 0u;
     __syncthreads();
   }
+  __shared__ float4 s_gridk[4];
+  if constexpr (NP == 2) {
+    grid_pair_consts(a.grid, s_gridk);
+    __syncthreads();
+  }
   double acc = 0.0;
   // NP particles per thread: a block covers NP * blockDim.x consecutive
   // particles, thread t the ones at t and t + blockDim.x (coalesced)
@@ -319,7 +336,7 @@ __device__ __forceinline__ void push_body(const Pulse<Real<PREC>> &P, const Push
     if constexpr (NP == 2) {
       const long long i1 = i + blockDim.x;
       double g[2];
-      push_two<KIND, GRID>(P, a, i, i1, i < a.n, i1 < a.n, s_steps, slots, g);
+      push_two<KIND, GRID>(P, a, i, i1, i < a.n, i1 < a.n, s_steps, slots, s_gridk, g);
       if (i < a.n) {
         acc += g[0];
         if (hist) hist_add(s_hist, a.diag, g[0]);
@@ -419,6 +436,8 @@ __device__ __forceinline__ void batch_body(const Pulse<Real<PREC>> *__restrict__
   Pulse<R> &sp = *reinterpret_cast<Pulse<R> *>(s_pulse_raw);
   const PushArgs &a = ba.base;
   const int T = ba.tile;
+  __shared__ float4 s_gridk[4];
+  if constexpr (NP == 2) grid_pair_consts(a.grid, s_gridk);  // the prefix's barrier follows
   // tile prefix over sets: tiles of set s = ceil(N_s / T)
   if (threadIdx.x == 0) {
     long long acc = 0;
@@ -466,7 +485,7 @@ __device__ __forceinline__ void batch_body(const Pulse<Real<PREC>> *__restrict__
         const long long i1 = i + blockDim.x;
         const bool valid1 = i1 >= 0 && i1 < end_set && i1 < a.n;
         double g[2];
-        push_two<KIND, GRID>(sp, a, i, i1, valid, valid1, s_steps, slots, g);
+        push_two<KIND, GRID>(sp, a, i, i1, valid, valid1, s_steps, slots, s_gridk, g);
         if (valid) acc += g[0];
         if (valid1) acc += g[1];
       } else {

@@ -212,16 +212,24 @@ __device__ __forceinline__ Local<F2> local_coords2(const Pulse<float> &P, const 
 // The cell test and weights of a thread's two particles with packed
 // arithmetic (grid units, offsets from each cached cell), then each
 // particle's own warp-uniform refetch branch, as grid_fetch does per particle.
+// gk: the grid's inverse spacings and offsets pre-broadcast in shared memory,
+// gk[a] = (inv_d[a], inv_d[a], off[a], off[a]), and gk[3] = (1/2, 1/2, -, -):
+// a 16-byte load yields both pair operands, where constants kept in the
+// kernel parameters would be re-broadcast into register pairs every step
+// (the two-particle kernels run at their register limit).
 template <class CA, class CB>
-__device__ __forceinline__ void grid_fetch2(const GridView &g, CA &ga, CB &gb, F2 x, F2 y, F2 z) {
-  F2 f[3] = {fma(x, F2(g.inv_d[0]), F2(g.off[0])), fma(y, F2(g.inv_d[1]), F2(g.off[1])),
-             fma(z, F2(g.inv_d[2]), F2(g.off[2]))};
+__device__ __forceinline__ void grid_fetch2(const GridView &g, CA &ga, CB &gb, F2 x, F2 y, F2 z,
+                                            const float4 *gk) {
+  const float4 kx = gk[0], ky = gk[1], kz = gk[2], kh = gk[3];
+  F2 f[3] = {fma(x, F2(kx.x, kx.y), F2(kx.z, kx.w)), fma(y, F2(ky.x, ky.y), F2(ky.z, ky.w)),
+             fma(z, F2(kz.x, kz.y), F2(kz.z, kz.w))};
 #pragma unroll
   for (int a = 0; a < 3; ++a)
     f[a] = F2(fminf(fmaxf(f[a].x, 0.0f), g.top[a]), fminf(fmaxf(f[a].y, 0.0f), g.top[a]));
   F2 w[3] = {f[0] - F2(ga.ox, gb.ox), f[1] - F2(ga.oy, gb.oy), f[2] - F2(ga.oz, gb.oz)};
   // inside the cached cell (faces included) iff max |w - 1/2| <= 1/2
-  const F2 d0 = w[0] - F2(0.5f), d1 = w[1] - F2(0.5f), d2 = w[2] - F2(0.5f);
+  const F2 half(kh.x, kh.y);
+  const F2 d0 = w[0] - half, d1 = w[1] - half, d2 = w[2] - half;
   const bool need_a = !(fmaxf(fabsf(d0.x), fmaxf(fabsf(d1.x), fabsf(d2.x))) <= 0.5f);
   const bool need_b = !(fmaxf(fabsf(d0.y), fmaxf(fabsf(d1.y), fabsf(d2.y))) <= 0.5f);
   float wa[3] = {w[0].x, w[1].x, w[2].x}, wb[3] = {w[0].y, w[1].y, w[2].y};
