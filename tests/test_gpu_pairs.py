@@ -243,3 +243,90 @@ def test_pairs_batched_tile_not_multiple_rejected():
             _lib.ap_gather_push_batched(h.h, dev, torch.as_tensor(off).cuda(), None, 0.0, 0.02, 5, "fp32",
                                         None, ws)
         assert e.value.status == _lib.AP_ERR_ARG
+
+
+@pytest.mark.gpu
+def test_pairs_plasma_pulse_push():
+    """A circularly polarised plane wave in a plasma (Sec. 4: k, v_g, B0/E0
+    and B's finite-duration terms) pushes 3001 electrons with two particles
+    per thread as the oracle does."""
+    pulse = dict(kind="plane", pol="cp", env="gauss", env_len=15.0, a0=0.8, omega_p=0.3, t_focus=30.0)
+    rng = np.random.default_rng(21)
+    n = 3001
+    parts = dict(x=rng.uniform(-1, 1, n), y=rng.uniform(-1, 1, n), z=rng.uniform(-20.0, 20.0, n),
+                 ux=rng.normal(0, 0.05, n), uy=rng.normal(0, 0.05, n), uz=rng.normal(0, 0.05, n))
+    out, _, st = gpu_push(pulse, parts, 0.0, 0.05, 1200, "fp32", launch=PAIRS)
+    assert st == 0
+    idx = np.arange(0, n, 150)
+    sub = {k: v[idx] for k, v in parts.items()}
+    ref = oracle.push(pulse, sub, 0.0, 0.05, 1200)
+    _check({k: v[idx] for k, v in out.items()}, ref)
+    assert np.max(np.abs(ref["ux"])) > 0.3
+
+
+@pytest.mark.gpu
+def test_pairs_super_gaussian_and_lg_negative_l():
+    """Two particles per thread through (a) a super-Gaussian (g = 3) plane
+    wave and (b) an LG_{2,-3} beam with circular polarisation and
+    longitudinal terms: the run-time loops of the envelope, the Laguerre
+    recurrence and the (x - i y) powers in packed form, against the oracle."""
+    rng = np.random.default_rng(29)
+    n = 257
+    pulses = [dict(kind="plane", pol="y", env="sgauss", sg_order=3, env_len=12.0, a0=2.0, t_focus=15.0),
+              dict(kind="lg", pol="cm", env="gauss", env_len=20.0, a0=3.0, w0=2 * L, lg_p=2, lg_l=-3,
+                   longitudinal=True, t_focus=20.0)]
+    for pulse in pulses:
+        parts = dict(x=rng.uniform(-1, 1, n) * 2 * L, y=rng.uniform(-1, 1, n) * 2 * L,
+                     z=rng.uniform(-1, 1, n) * 2 * L, ux=np.zeros(n), uy=np.zeros(n), uz=np.zeros(n))
+        out, _, st = gpu_push(pulse, parts, 0.0, 0.02, 2000, "fp32", launch=PAIRS)
+        assert st == 0
+        ref = oracle.push(pulse, parts, 0.0, 0.02, 2000, threads=THREADS)
+        _check(out, ref)
+        assert np.max(np.abs(ref["ux"]) + np.abs(ref["uy"])) > 0.5, pulse["kind"]
+
+
+@pytest.mark.gpu
+def test_pairs_one_d_sweep_holds_transverse_positions():
+    """1D-3V sets (workload-6 shape, 30 lines x 41 electrons) in the batched
+    launch with two particles per thread: transverse positions held to the
+    float-float representation, momenta and per-line sums as the oracle's."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    cfg = workloads.config(6)
+    sets, parts, off = workloads.sweep_lines(cfg, per_set=41)
+    n_steps = 2000
+    with _lib.Handle(sets) as h:
+        h.set_launch(block=64, pairs=1, tile=256)
+        dev = _lib.to_device(parts, "fp32")
+        d_off = torch.as_tensor(off).cuda()
+        ws = torch.zeros(_lib.ap_batch_workspace_bytes(h.h) // 4, dtype=torch.int32, device="cuda")
+        diag = dict(set_sum=torch.zeros(len(sets), dtype=torch.float64, device="cuda"))
+        _lib.ap_gather_push_batched(h.h, dev, d_off, None, cfg["t0"], cfg["dt"], n_steps, "fp32", diag, ws)
+        assert h.status() == 0
+        out = _lib.to_host(dev)
+        sums = diag["set_sum"].cpu().numpy()
+    for k in ("x", "y"):
+        assert np.all(np.abs(out[k] - parts[k]) <= 2.0 ** -46 * np.abs(parts[k])), k
+    ref = oracle.push(sets[0], parts, cfg["t0"], cfg["dt"], n_steps, threads=THREADS)
+    _check(out, ref)
+    np.testing.assert_allclose(sums, oracle.set_gamma_sums(off, ref["ux"], ref["uy"], ref["uz"]), rtol=1e-5)
+
+
+@pytest.mark.gpu
+def test_launch_shape_arguments_checked():
+    """ap_set_launch rejects particles-per-thread settings other than 0 or 1,
+    cell placements other than 0, 1, 2, negative tiles and bad blocks; a
+    rejected call leaves the handle usable."""
+    from paper_2307_04843_gb300 import _lib
+    cfg = workloads.config(2)
+    with _lib.Handle(cfg["pulse"]) as h:
+        for bad in (dict(pairs=2), dict(pairs=-1), dict(grid_cache=3), dict(tile=-1), dict(block=48),
+                    dict(block=512), dict(blocks_per_sm=-1)):
+            with pytest.raises(_lib.APError) as e:
+                h.set_launch(**bad)
+            assert e.value.status == _lib.AP_ERR_ARG, bad
+        h.set_launch(block=96, pairs=1, grid_cache=2, tile=192)
+        parts = workloads.particles(cfg, n=100)
+        dev = _lib.to_device(parts, "fp32")
+        h.push(dev, -5.0, 0.02, 50, precision="fp32")
+        assert h.status() == 0
