@@ -11,10 +11,12 @@
 //             (lu^n, lE, lB) = Boris^T(lu')                          (hand-written VJP)
 //             lx^n = lx^{n+1} + (dF/dx)^T (lE, lB),  g += (dF/dtheta)^T (lE, lB)
 //
-// with seed lu^N = u^N / (gamma^N N_s), lx^N = 0.  dF/dx and dF/dtheta come
-// from the field functions instantiated with forward-mode dual numbers
-// seeded in (x, y, z - z_f, w0, beta_f); a0 enters linearly (dF/da0 = F / a0)
-// and z_f only through z - z_f (dF/dz_f = -dF/dz for the analytic part).
+// with seed lu^N = u^N / (gamma^N N_s), lx^N = 0.  dF/dx and dF/dtheta are
+// the derivatives in (x, y, z - z_f, w0, beta_f): in closed form for the
+// Gaussian beam and the closed-form flying focus (beam_jacobian), and from
+// the field functions instantiated with forward-mode dual numbers for the
+// other kinds; a0 enters linearly (dF/da0 = F / a0) and z_f only through
+// z - z_f (dF/dz_f = -dF/dz for the analytic part).
 //
 // Memory: one persistent launch; every resident thread slot pushes its
 // particle forward storing a checkpoint every K steps, then sweeps the
@@ -186,6 +188,139 @@ __device__ __forceinline__ void fields_ad(const PulseAD<R, NT> &A, const Local<D
   else fields_lg(A, L, E, B);
 }
 
+// Logarithmic derivative Gamma'/Gamma of the envelope at eta, given the
+// factor `mul` that `envelope` returned (zero outside the sin^2 window and
+// for a continuous wave).  SIN2: Gamma = cos^2(env_a eta), so -2 env_a
+// tan(env_a eta); GAUSS: Gamma = 2^(-env_a eta^2); SGAUSS: Gamma =
+// 2^(-env_b u^(2g)), u = env_a eta.
+template <typename R>
+__device__ __forceinline__ R envelope_dlog(const Pulse<R> &P, R eta, R mul) {
+  constexpr double kLn2 = 0.69314718055994531;
+  switch (P.env) {
+    case AP_ENV_SIN2: {
+      if (mul == R(0)) return R(0);
+      R s, c;
+      sincos_r(eta * P.env_a, &s, &c);
+      return R(-2) * P.env_a * s * rcp_r(c);
+    }
+    case AP_ENV_GAUSS:
+      return R(-2 * kLn2) * P.env_a * eta;
+    case AP_ENV_SGAUSS: {
+      const R u = eta * P.env_a;
+      const R s = u * u;
+      R p = R(1);  // s^(g-1)
+      for (int i = 1; i < P.sg_order; ++i) p *= s;
+      return R(-2 * kLn2) * P.env_b * R(P.sg_order) * P.env_a * u * p;
+    }
+    default:
+      return R(0);
+  }
+}
+
+// The Gaussian beam (MOVING: the closed-form flying focus) at unit a0, with
+// its derivatives J[c][j] in the directions j = (x, y, z - z_f, w0[, beta_f])
+// in closed form rather than by dual numbers.  The value part is the
+// arithmetic of gauss_z and gauss_xy.  With G the amplitude times the
+// envelope and a = r^2/w0^2, the profile is U0 = G e^{i psi} exp(-a q),
+// U = q U0 and W = q U (the longitudinal terms' factor), and dq/dzeta =
+// i q^2; so every derivative is a complex factor times U or W:
+//   dU/dj = U alpha_j,  alpha_j = i q (1 - a q) zeta_j - a_j q + L1 eta_j + i psi_j,
+//   dW/dj = W beta_j,   beta_j = alpha_j + i q zeta_j,
+// L1 = Gamma'/Gamma, where zeta_j, a_j, eta_j, psi_j are the derivatives of
+// zeta, a, eta = T - (z - z_f)/v_g and psi = C - k (z - z_f).  The fields
+// are linear in U and W (finish_beam), with the longitudinal terms also
+// linear in x, y and g = -2/w0^2, whose derivatives add those terms at unit
+// x, at unit y, and times g'/g = -2/w0.
+template <int POL, bool LON, bool MOVING, typename R, int NT>
+__device__ __forceinline__ void beam_jacobian_t(const Pulse<R> &P, const Local<R> &L, R F[6],
+                                                R J[6][NT]) {
+  static_assert(NT == (MOVING ? 5 : 4), "tangent count");
+  R mul, l2;
+  envelope(P, L.eta, mul, l2);
+  R zeta;
+  if constexpr (MOVING) zeta = fma(-P.beta_f, L.T, L.dz) * P.inv_zR;
+  else zeta = L.dz * P.inv_zR;
+  const R inv = rcp_r(fma(zeta, zeta, R(1)));
+  const Cx<R> q{inv, zeta * inv};
+  const R x = L.x, y = L.y;
+  const R a = (x * x + y * y) * P.inv_w0sq;
+  const R mag = (P.amp_unit * mul) * exp2_r(fma(a * q.re, R(-kLog2e), l2));
+  const R ang = reduce_angle<R>(L.psi - a * q.im);
+  R sn, cs;
+  sincos_r(ang, &sn, &cs);
+  const Cx<R> U = cmul(q, Cx<R>{mag * cs, mag * sn});
+  const Cx<R> W = cmul(q, U);
+  const R g = R(-2) * P.inv_w0sq;
+  R E[3], B[3];
+  finish_beam_pol<POL>(P, x, y, U, W, g, LON, E, B);
+  for (int c = 0; c < 3; ++c) {
+    F[c] = E[c];
+    F[c + 3] = B[c];
+  }
+  // shared factors: i q and i q (1 - a q)
+  const Cx<R> iq{-q.im, q.re};
+  const Cx<R> Q1 = cmul(iq, Cx<R>{R(1) - a * q.re, -a * q.im});
+  const R L1 = envelope_dlog(P, L.eta, mul);
+  const R w2 = R(2) * P.inv_w0sq, m2w = R(-2) * P.inv_w0;
+  R zj[NT], aj[NT], ej[NT], pj[NT];
+  zj[0] = R(0); aj[0] = w2 * x; ej[0] = R(0); pj[0] = R(0);
+  zj[1] = R(0); aj[1] = w2 * y; ej[1] = R(0); pj[1] = R(0);
+  zj[2] = P.inv_zR; aj[2] = R(0); ej[2] = -P.inv_vg * L1; pj[2] = -R(P.k);
+  zj[3] = m2w * zeta; aj[3] = m2w * a; ej[3] = R(0); pj[3] = R(0);
+  if constexpr (NT == 5) {
+    zj[4] = fma(-L.T, P.inv_zR, zeta * P.inv_1mb);
+    aj[4] = R(0); ej[4] = R(0); pj[4] = R(0);
+  }
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const Cx<R> al{zj[j] * Q1.re - aj[j] * q.re + ej[j], zj[j] * Q1.im - aj[j] * q.im + pj[j]};
+    const Cx<R> be{al.re + zj[j] * iq.re, al.im + zj[j] * iq.im};
+    R Ej[3], Bj[3];
+    finish_beam_pol<POL>(P, x, y, cmul(U, al), cmul(W, be), g, LON, Ej, Bj);
+    for (int c = 0; c < 3; ++c) {
+      J[c][j] = Ej[c];
+      J[c + 3][j] = Bj[c];
+    }
+  }
+  if constexpr (LON) {
+    // the longitudinal terms' own x, y and g factors (components E_z, B_z)
+    const Cx<R> zero{R(0), R(0)};
+    R Ex[3], Bx[3], Ey[3], By[3], Eg[3], Bg[3];
+    finish_beam_pol<POL>(P, R(1), R(0), zero, W, g, true, Ex, Bx);
+    finish_beam_pol<POL>(P, R(0), R(1), zero, W, g, true, Ey, By);
+    finish_beam_pol<POL>(P, x, y, zero, W, g, true, Eg, Bg);
+    J[2][0] += Ex[2]; J[5][0] += Bx[2];
+    J[2][1] += Ey[2]; J[5][1] += By[2];
+    J[2][3] += m2w * Eg[2]; J[5][3] += m2w * Bg[2];
+  }
+}
+
+// beam_jacobian_t with the polarisation and the longitudinal switch (uniform
+// over a set) selected once rather than in each of its field assemblies.
+template <bool MOVING, typename R, int NT>
+__device__ __forceinline__ void beam_jacobian(const Pulse<R> &P, const Local<R> &L, R F[6],
+                                              R J[6][NT]) {
+  const bool lon = P.lon != 0;
+  switch (P.pol) {
+    case AP_LIN_X:
+      if (lon) beam_jacobian_t<AP_LIN_X, true, MOVING>(P, L, F, J);
+      else beam_jacobian_t<AP_LIN_X, false, MOVING>(P, L, F, J);
+      break;
+    case AP_LIN_Y:
+      if (lon) beam_jacobian_t<AP_LIN_Y, true, MOVING>(P, L, F, J);
+      else beam_jacobian_t<AP_LIN_Y, false, MOVING>(P, L, F, J);
+      break;
+    case AP_CIRC_P:
+      if (lon) beam_jacobian_t<AP_CIRC_P, true, MOVING>(P, L, F, J);
+      else beam_jacobian_t<AP_CIRC_P, false, MOVING>(P, L, F, J);
+      break;
+    default:
+      if (lon) beam_jacobian_t<AP_CIRC_M, true, MOVING>(P, L, F, J);
+      else beam_jacobian_t<AP_CIRC_M, false, MOVING>(P, L, F, J);
+      break;
+  }
+}
+
 // One reverse step.  State before the step (pos, u), step value st, adjoints
 // lx, lu of the state after the step (updated in place to the state before),
 // gradient accumulators g[0..3] = d/d(a0, w0, z_f, beta_f).
@@ -204,32 +339,49 @@ __device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P,
   const R a0 = P.a0;
   // fields with derivatives in (x, y, z - z_f, w0, beta_f)
   Local<R> L = local_coords<PREC>(P, st, pos);
-  Local<DR> LD;
-  LD.x = DR::seed(L.x, 0);
-  LD.y = DR::seed(L.y, 1);
-  LD.dz = DR::seed(L.dz, 2);
-  LD.psi = DR(L.psi);
-  LD.psi.d[2] = -R(P.k);  // psi = C - k (z - z_f)
-  LD.eta = DR(L.eta);
-  LD.eta.d[2] = -P.inv_vg;  // eta = T - (z - z_f) / v_g
-  LD.T = DR(L.T);
-  LD.phi_hi = DR(R(0));
-  LD.phi_lo = DR(R(0));
-  DR Ed[3], Bd[3];
-  fields_ad<KIND, R, NT>(A, LD, Ed, Bd);
   R F[6], dFx[6][3], dFth[6][kNp];  // field, d/dx, d/d(a0, w0, z_f, beta_f)
-  const DR *Fd[6] = {&Ed[0], &Ed[1], &Ed[2], &Bd[0], &Bd[1], &Bd[2]};
-  for (int c = 0; c < 6; ++c) {
-    const DR &f = *Fd[c];
-    F[c] = a0 * f.v;
-    dFx[c][0] = a0 * f.d[0];
-    dFx[c][1] = a0 * f.d[1];
-    dFx[c][2] = a0 * f.d[2];
-    dFth[c][0] = f.v;
-    dFth[c][1] = a0 * f.d[3];
-    dFth[c][2] = -a0 * f.d[2];
-    if constexpr (NT == 5) dFth[c][3] = a0 * f.d[4];
-    else dFth[c][3] = R(0);
+  if constexpr (KIND == AP_GAUSS || KIND == AP_FLYING_CF) {
+    R f[6], Jc[6][NT];
+    beam_jacobian<KIND == AP_FLYING_CF, R, NT>(P, L, f, Jc);
+    for (int c = 0; c < 6; ++c) {
+      F[c] = a0 * f[c];
+      dFx[c][0] = a0 * Jc[c][0];
+      dFx[c][1] = a0 * Jc[c][1];
+      dFx[c][2] = a0 * Jc[c][2];
+      dFth[c][0] = f[c];
+      dFth[c][1] = a0 * Jc[c][3];
+      dFth[c][2] = -a0 * Jc[c][2];
+      if constexpr (NT == 5) dFth[c][3] = a0 * Jc[c][4];
+      else dFth[c][3] = R(0);
+    }
+  } else {
+    // the other kinds: dual numbers through the generic field functions
+    Local<DR> LD;
+    LD.x = DR::seed(L.x, 0);
+    LD.y = DR::seed(L.y, 1);
+    LD.dz = DR::seed(L.dz, 2);
+    LD.psi = DR(L.psi);
+    LD.psi.d[2] = -R(P.k);  // psi = C - k (z - z_f)
+    LD.eta = DR(L.eta);
+    LD.eta.d[2] = -P.inv_vg;  // eta = T - (z - z_f) / v_g
+    LD.T = DR(L.T);
+    LD.phi_hi = DR(R(0));
+    LD.phi_lo = DR(R(0));
+    DR Ed[3], Bd[3];
+    fields_ad<KIND, R, NT>(A, LD, Ed, Bd);
+    const DR *Fd[6] = {&Ed[0], &Ed[1], &Ed[2], &Bd[0], &Bd[1], &Bd[2]};
+    for (int c = 0; c < 6; ++c) {
+      const DR &f = *Fd[c];
+      F[c] = a0 * f.v;
+      dFx[c][0] = a0 * f.d[0];
+      dFx[c][1] = a0 * f.d[1];
+      dFx[c][2] = a0 * f.d[2];
+      dFth[c][0] = f.v;
+      dFth[c][1] = a0 * f.d[3];
+      dFth[c][2] = -a0 * f.d[2];
+      if constexpr (NT == 5) dFth[c][3] = a0 * f.d[4];
+      else dFth[c][3] = R(0);
+    }
   }
   if constexpr (GRID) {
     GridGrad<R> gg;
@@ -310,6 +462,11 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const Pulse<Real<PRE
   __shared__ StepFF s_steps[kAdjMaxK];
   __shared__ __align__(16) unsigned char s_pulse_raw[sizeof(Pulse<R>)];
   __shared__ long long s_prefix[AP_MAX_SETS + 1];
+  // dynamic: the tape state of the next reverse step, copied in while the
+  // current one is computed (double buffer [2][W][kAdjBlock], this thread's
+  // column only)
+  extern __shared__ __align__(16) unsigned char s_adj_dyn[];
+  T *s_next = reinterpret_cast<T *>(s_adj_dyn);
   Pulse<R> &P = *reinterpret_cast<Pulse<R> *>(s_pulse_raw);
   const PushArgs &a = aa.base;
   const int Tt = blockDim.x;
@@ -420,9 +577,25 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const Pulse<Real<PRE
         R ig = boris(u, E, B, dtR);
         pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtxy, dtR);
       }
+      // the tape entries this thread just stored are read back by its own
+      // asynchronous copies
+      __threadfence_block();
+      auto stage = [&](int k) {
+        const T *src = tp + (size_t)k * IO::W * stride;
+#pragma unroll
+        for (int w = 0; w < IO::W; ++w) {
+          const unsigned dst = (unsigned)__cvta_generic_to_shared(
+              s_next + ((k & 1) * IO::W + w) * kAdjBlock + threadIdx.x);
+          if constexpr (sizeof(T) == 8) cp_async8(dst, src + (size_t)w * stride);
+          else cp_async4(dst, src + (size_t)w * stride);
+        }
+      };
       R gs[kNp] = {R(0), R(0), R(0), R(0)};
+      stage(cnt - 1);
       for (int k = cnt - 1; k >= 0; --k) {
-        IO::get(tp + (size_t)k * IO::W * stride, stride, pos, u);
+        cp_async_wait_all();
+        IO::get(s_next + (k & 1) * IO::W * kAdjBlock + threadIdx.x, kAdjBlock, pos, u);
+        if (k > 0) stage(k - 1);
         typename TimeBase<PREC>::Step st;
         if constexpr (PREC == AP_FP32_PHASEFF) st = s_steps[k];
         else st = tb.at(s0 + k);
@@ -451,8 +624,12 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const Pulse<Real<PRE
 
 template <int KIND, int PREC, bool GRID>
 int launch_adjoint_t(const Pulse<Real<PREC>> *sets, const AdjArgs &aa, int grid, void *stream) {
-  adjoint_kernel<KIND, PREC, GRID>
-      <<<grid, kAdjBlock, 0, static_cast<cudaStream_t>(stream)>>>(sets, aa);
+  auto kern = adjoint_kernel<KIND, PREC, GRID>;
+  const size_t dyn = 2 * (size_t)StateIO<PREC>::W * kAdjBlock * sizeof(typename StateIO<PREC>::T);
+  // static (about 40 KB) plus dynamic shared memory passes 48 KB: opt in
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+    return AP_ERR_CUDA;
+  kern<<<grid, kAdjBlock, dyn, static_cast<cudaStream_t>(stream)>>>(sets, aa);
   return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }
 

@@ -416,30 +416,38 @@ __device__ __forceinline__ void assemble(const PT &P, Cx<R> U, Cx<R> DE, Cx<R> D
 // focus sums W over components with the 1/k_j factors inside), specialised
 // per polarisation (a uniform branch): DE = g (p_x x + p_y y) W and
 // DB = g (-p_y x + p_x y) W, E_z = (v_phi/omega) Im DE, B_z = (B0/E0)(c/omega) Im DB.
-template <class PT, typename R>
-__device__ __forceinline__ void finish_beam(const PT &P, R x, R y, Cx<R> U, Cx<R> W, R g,
-                                            bool lon, R E[3], R B[3]) {
+// finish_beam_pol takes the polarisation as a compile-time parameter, for
+// code that assembles several field sets per step and selects it once.
+template <int POL, class PT, typename R>
+__device__ __forceinline__ void finish_beam_pol(const PT &P, R x, R y, Cx<R> U, Cx<R> W, R g,
+                                                bool lon, R E[3], R B[3]) {
   const R br = P.bratio;
   const R ce = P.lonE * g, cb = br * P.lonB * g;
   E[2] = R(0);
   B[2] = R(0);
+  if constexpr (POL == AP_LIN_X) {
+    E[0] = U.re; E[1] = R(0); B[0] = R(0); B[1] = br * U.re;
+    if (lon) { E[2] = ce * x * W.im; B[2] = cb * y * W.im; }
+  } else if constexpr (POL == AP_LIN_Y) {
+    E[0] = R(0); E[1] = U.re; B[0] = -br * U.re; B[1] = R(0);
+    if (lon) { E[2] = ce * y * W.im; B[2] = -cb * x * W.im; }
+  } else if constexpr (POL == AP_CIRC_P) {  // p = (1, -i)
+    E[0] = U.re; E[1] = U.im; B[0] = -br * U.im; B[1] = br * U.re;
+    if (lon) { E[2] = ce * (x * W.im - y * W.re); B[2] = cb * (x * W.re + y * W.im); }
+  } else {  // AP_CIRC_M, p = (1, +i)
+    E[0] = U.re; E[1] = -U.im; B[0] = br * U.im; B[1] = br * U.re;
+    if (lon) { E[2] = ce * (x * W.im + y * W.re); B[2] = cb * (y * W.im - x * W.re); }
+  }
+}
+
+template <class PT, typename R>
+__device__ __forceinline__ void finish_beam(const PT &P, R x, R y, Cx<R> U, Cx<R> W, R g,
+                                            bool lon, R E[3], R B[3]) {
   switch (P.pol) {
-    case AP_LIN_X:
-      E[0] = U.re; E[1] = R(0); B[0] = R(0); B[1] = br * U.re;
-      if (lon) { E[2] = ce * x * W.im; B[2] = cb * y * W.im; }
-      break;
-    case AP_LIN_Y:
-      E[0] = R(0); E[1] = U.re; B[0] = -br * U.re; B[1] = R(0);
-      if (lon) { E[2] = ce * y * W.im; B[2] = -cb * x * W.im; }
-      break;
-    case AP_CIRC_P:  // p = (1, -i)
-      E[0] = U.re; E[1] = U.im; B[0] = -br * U.im; B[1] = br * U.re;
-      if (lon) { E[2] = ce * (x * W.im - y * W.re); B[2] = cb * (x * W.re + y * W.im); }
-      break;
-    default:  // AP_CIRC_M, p = (1, +i)
-      E[0] = U.re; E[1] = -U.im; B[0] = br * U.im; B[1] = br * U.re;
-      if (lon) { E[2] = ce * (x * W.im + y * W.re); B[2] = cb * (y * W.im - x * W.re); }
-      break;
+    case AP_LIN_X: finish_beam_pol<AP_LIN_X>(P, x, y, U, W, g, lon, E, B); break;
+    case AP_LIN_Y: finish_beam_pol<AP_LIN_Y>(P, x, y, U, W, g, lon, E, B); break;
+    case AP_CIRC_P: finish_beam_pol<AP_CIRC_P>(P, x, y, U, W, g, lon, E, B); break;
+    default: finish_beam_pol<AP_CIRC_M>(P, x, y, U, W, g, lon, E, B); break;
   }
 }
 
@@ -864,6 +872,9 @@ __device__ __forceinline__ void cp_async16(unsigned dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async4(unsigned dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(unsigned dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ float4 lds128(unsigned addr) {

@@ -149,6 +149,39 @@ def test_adjoint_flying_focus_closed_form_vs_oracle_fd(precision):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("kind,pol,env", [("gauss", "y", "sgauss"), ("gauss", "cp", "sin2"),
+                                          ("gauss", "cm", "cw"), ("flying_cf", "cp", "sin2"),
+                                          ("flying_cf", "y", "sgauss")])
+def test_adjoint_beam_polarisations_envelopes_vs_oracle_fd(kind, pol, env):
+    """The closed-form beam Jacobian for every polarisation and envelope
+    (the other tests take linear x and a Gaussian envelope)."""
+    pulse = dict(kind=kind, pol=pol, env=env, env_len=14.0, a0=3.0, w0=2.2 * L, z_focus=0.7, t_focus=0.0,
+                 longitudinal=True)
+    if env == "sgauss":
+        pulse["sg_order"] = 2
+    if env == "cw":
+        pulse["a0"] = 0.5
+    if kind == "flying_cf":
+        pulse["beta_f"] = -0.4
+    rng = np.random.default_rng(37)
+    n = 24
+    parts = dict(x=rng.uniform(-1, 1, n) * 2 * L, y=rng.uniform(-1, 1, n) * 2 * L,
+                 z=rng.uniform(-1, 1, n) * L, ux=rng.normal(0, 0.05, n), uy=rng.normal(0, 0.05, n),
+                 uz=np.zeros(n))
+    off = np.array([0, n], dtype=np.int64)
+    t0, dt, n_steps, K = -6.0, 0.02, 420, 100
+    names = NAMES + (("beta_f",) if kind == "flying_cf" else ())
+    g = oracle.grad_fd(pulse, parts, t0, dt, n_steps, names=names, rel_h=1e-4,
+                       scale=dict(z_focus=L, beta_f=0.1))
+    gmax = max(abs(g[k]) for k in names)
+    for precision in ("fp64", "fp32"):
+        _, dJ = _run_adjoint([pulse], off, parts, t0, dt, n_steps, K, precision)
+        for k, name in enumerate(names):
+            assert abs(dJ[0, k] - g[name]) <= 1e-3 * max(abs(g[name]), 1e-2 * gmax), \
+                (precision, kind, pol, env, name, dJ[0, k], g[name])
+
+
+@pytest.mark.gpu
 def test_adjoint_one_d_lines_vs_oracle_fd():
     """1D-3V set (transverse position held): the position update and its
     reverse use dt only along z."""
