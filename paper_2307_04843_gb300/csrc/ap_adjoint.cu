@@ -194,14 +194,20 @@ __device__ __forceinline__ void fields_ad(const PulseAD<R, NT> &A, const Local<D
 // tan(env_a eta); GAUSS: Gamma = 2^(-env_a eta^2); SGAUSS: Gamma =
 // 2^(-env_b u^(2g)), u = env_a eta.
 template <typename R>
-__device__ __forceinline__ R envelope_dlog(const Pulse<R> &P, R eta, R mul) {
+__device__ __forceinline__ R unless_zero(R v, R m) { return m == R(0) ? R(0) : v; }
+__device__ __forceinline__ F2 unless_zero(F2 v, F2 m) {
+  return F2(m.x == 0.0f ? 0.0f : v.x, m.y == 0.0f ? 0.0f : v.y);
+}
+
+template <class PT, typename R>
+__device__ __forceinline__ R envelope_dlog(const PT &P, R eta, R mul) {
   constexpr double kLn2 = 0.69314718055994531;
   switch (P.env) {
     case AP_ENV_SIN2: {
-      if (mul == R(0)) return R(0);
+      // evaluated in both halves of a pair, each cleared where its factor is 0
       R s, c;
       sincos_r(eta * P.env_a, &s, &c);
-      return R(-2) * P.env_a * s * rcp_r(c);
+      return unless_zero(R(-2) * P.env_a * s * rcp_r(c), mul);
     }
     case AP_ENV_GAUSS:
       return R(-2 * kLn2) * P.env_a * eta;
@@ -217,180 +223,17 @@ __device__ __forceinline__ R envelope_dlog(const Pulse<R> &P, R eta, R mul) {
   }
 }
 
-// The Gaussian beam (MOVING: the closed-form flying focus) at unit a0, with
-// its derivatives J[c][j] in the directions j = (x, y, z - z_f, w0[, beta_f])
-// in closed form rather than by dual numbers.  The value part is the
-// arithmetic of gauss_z and gauss_xy.  With G the amplitude times the
-// envelope and a = r^2/w0^2, the profile is U0 = G e^{i psi} exp(-a q),
-// U = q U0 and W = q U (the longitudinal terms' factor), and dq/dzeta =
-// i q^2; so every derivative is a complex factor times U or W:
-//   dU/dj = U alpha_j,  alpha_j = i q (1 - a q) zeta_j - a_j q + L1 eta_j + i psi_j,
-//   dW/dj = W beta_j,   beta_j = alpha_j + i q zeta_j,
-// L1 = Gamma'/Gamma, where zeta_j, a_j, eta_j, psi_j are the derivatives of
-// zeta, a, eta = T - (z - z_f)/v_g and psi = C - k (z - z_f).  The fields
-// are linear in U and W (finish_beam), with the longitudinal terms also
-// linear in x, y and g = -2/w0^2, whose derivatives add those terms at unit
-// x, at unit y, and times g'/g = -2/w0.
-template <int POL, bool LON, bool MOVING, typename R, int NT>
-__device__ __forceinline__ void beam_jacobian_t(const Pulse<R> &P, const Local<R> &L, R F[6],
-                                                R J[6][NT]) {
-  static_assert(NT == (MOVING ? 5 : 4), "tangent count");
-  R mul, l2;
-  envelope(P, L.eta, mul, l2);
-  R zeta;
-  if constexpr (MOVING) zeta = fma(-P.beta_f, L.T, L.dz) * P.inv_zR;
-  else zeta = L.dz * P.inv_zR;
-  const R inv = rcp_r(fma(zeta, zeta, R(1)));
-  const Cx<R> q{inv, zeta * inv};
-  const R x = L.x, y = L.y;
-  const R a = (x * x + y * y) * P.inv_w0sq;
-  const R mag = (P.amp_unit * mul) * exp2_r(fma(a * q.re, R(-kLog2e), l2));
-  const R ang = reduce_angle<R>(L.psi - a * q.im);
-  R sn, cs;
-  sincos_r(ang, &sn, &cs);
-  const Cx<R> U = cmul(q, Cx<R>{mag * cs, mag * sn});
-  const Cx<R> W = cmul(q, U);
-  const R g = R(-2) * P.inv_w0sq;
-  R E[3], B[3];
-  finish_beam_pol<POL>(P, x, y, U, W, g, LON, E, B);
-  for (int c = 0; c < 3; ++c) {
-    F[c] = E[c];
-    F[c + 3] = B[c];
-  }
-  // shared factors: i q and i q (1 - a q)
-  const Cx<R> iq{-q.im, q.re};
-  const Cx<R> Q1 = cmul(iq, Cx<R>{R(1) - a * q.re, -a * q.im});
-  const R L1 = envelope_dlog(P, L.eta, mul);
-  const R w2 = R(2) * P.inv_w0sq, m2w = R(-2) * P.inv_w0;
-  R zj[NT], aj[NT], ej[NT], pj[NT];
-  zj[0] = R(0); aj[0] = w2 * x; ej[0] = R(0); pj[0] = R(0);
-  zj[1] = R(0); aj[1] = w2 * y; ej[1] = R(0); pj[1] = R(0);
-  zj[2] = P.inv_zR; aj[2] = R(0); ej[2] = -P.inv_vg * L1; pj[2] = -R(P.k);
-  zj[3] = m2w * zeta; aj[3] = m2w * a; ej[3] = R(0); pj[3] = R(0);
-  if constexpr (NT == 5) {
-    zj[4] = fma(-L.T, P.inv_zR, zeta * P.inv_1mb);
-    aj[4] = R(0); ej[4] = R(0); pj[4] = R(0);
-  }
-#pragma unroll
-  for (int j = 0; j < NT; ++j) {
-    const Cx<R> al{zj[j] * Q1.re - aj[j] * q.re + ej[j], zj[j] * Q1.im - aj[j] * q.im + pj[j]};
-    const Cx<R> be{al.re + zj[j] * iq.re, al.im + zj[j] * iq.im};
-    R Ej[3], Bj[3];
-    finish_beam_pol<POL>(P, x, y, cmul(U, al), cmul(W, be), g, LON, Ej, Bj);
-    for (int c = 0; c < 3; ++c) {
-      J[c][j] = Ej[c];
-      J[c + 3][j] = Bj[c];
-    }
-  }
-  if constexpr (LON) {
-    // the longitudinal terms' own x, y and g factors (components E_z, B_z)
-    const Cx<R> zero{R(0), R(0)};
-    R Ex[3], Bx[3], Ey[3], By[3], Eg[3], Bg[3];
-    finish_beam_pol<POL>(P, R(1), R(0), zero, W, g, true, Ex, Bx);
-    finish_beam_pol<POL>(P, R(0), R(1), zero, W, g, true, Ey, By);
-    finish_beam_pol<POL>(P, x, y, zero, W, g, true, Eg, Bg);
-    J[2][0] += Ex[2]; J[5][0] += Bx[2];
-    J[2][1] += Ey[2]; J[5][1] += By[2];
-    J[2][3] += m2w * Eg[2]; J[5][3] += m2w * Bg[2];
-  }
-}
-
-// beam_jacobian_t with the polarisation and the longitudinal switch (uniform
-// over a set) selected once rather than in each of its field assemblies.
-template <bool MOVING, typename R, int NT>
-__device__ __forceinline__ void beam_jacobian(const Pulse<R> &P, const Local<R> &L, R F[6],
-                                              R J[6][NT]) {
-  const bool lon = P.lon != 0;
-  switch (P.pol) {
-    case AP_LIN_X:
-      if (lon) beam_jacobian_t<AP_LIN_X, true, MOVING>(P, L, F, J);
-      else beam_jacobian_t<AP_LIN_X, false, MOVING>(P, L, F, J);
-      break;
-    case AP_LIN_Y:
-      if (lon) beam_jacobian_t<AP_LIN_Y, true, MOVING>(P, L, F, J);
-      else beam_jacobian_t<AP_LIN_Y, false, MOVING>(P, L, F, J);
-      break;
-    case AP_CIRC_P:
-      if (lon) beam_jacobian_t<AP_CIRC_P, true, MOVING>(P, L, F, J);
-      else beam_jacobian_t<AP_CIRC_P, false, MOVING>(P, L, F, J);
-      break;
-    default:
-      if (lon) beam_jacobian_t<AP_CIRC_M, true, MOVING>(P, L, F, J);
-      else beam_jacobian_t<AP_CIRC_M, false, MOVING>(P, L, F, J);
-      break;
-  }
-}
-
-// One reverse step.  State before the step (pos, u), step value st, adjoints
-// lx, lu of the state after the step (updated in place to the state before),
-// gradient accumulators g[0..3] = d/d(a0, w0, z_f, beta_f).
-template <int KIND, int PREC, bool GRID>
-__device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P,
-                                             const PulseAD<Real<PREC>, tangents<KIND>()> &A,
-                                             const AdjArgs &aa, const typename TimeBase<PREC>::Step &st,
-                                             const Pos<PREC> &pos, const Real<PREC> u[3],
-                                             Real<PREC> lx[3], Real<PREC> lu[3], Real<PREC> g[kNp],
-                                             GridCache<Real<PREC>> &gc) {
-  using R = Real<PREC>;
-  constexpr int NT = tangents<KIND>();
-  using DR = Dual<R, NT>;
-  const R dt = (R)aa.base.dt;
+// The reverse of one Boris step and position update, given the fields F at
+// the step's position: from the adjoints lx, lu of the state after the step,
+// the cotangent Fb of the fields (E, B), with lu updated to the momentum
+// adjoint before the step (lx changes only through the fields:
+// lx += (dF/dx)^T Fb).  Generic over the arithmetic type (float, double, or
+// the packed pair of the two-particle kernel); adv_xy = 0 holds the
+// transverse position (1D-3V).
+template <typename R>
+__device__ __forceinline__ void boris_cotangent(const R F[6], const R u[3], R dt, R adv_xy,
+                                                const R lx[3], R lu[3], R Fb[6]) {
   const R h = R(-0.5) * dt;
-  const R a0 = P.a0;
-  // fields with derivatives in (x, y, z - z_f, w0, beta_f)
-  Local<R> L = local_coords<PREC>(P, st, pos);
-  R F[6], dFx[6][3], dFth[6][kNp];  // field, d/dx, d/d(a0, w0, z_f, beta_f)
-  if constexpr (KIND == AP_GAUSS || KIND == AP_FLYING_CF) {
-    R f[6], Jc[6][NT];
-    beam_jacobian<KIND == AP_FLYING_CF, R, NT>(P, L, f, Jc);
-    for (int c = 0; c < 6; ++c) {
-      F[c] = a0 * f[c];
-      dFx[c][0] = a0 * Jc[c][0];
-      dFx[c][1] = a0 * Jc[c][1];
-      dFx[c][2] = a0 * Jc[c][2];
-      dFth[c][0] = f[c];
-      dFth[c][1] = a0 * Jc[c][3];
-      dFth[c][2] = -a0 * Jc[c][2];
-      if constexpr (NT == 5) dFth[c][3] = a0 * Jc[c][4];
-      else dFth[c][3] = R(0);
-    }
-  } else {
-    // the other kinds: dual numbers through the generic field functions
-    Local<DR> LD;
-    LD.x = DR::seed(L.x, 0);
-    LD.y = DR::seed(L.y, 1);
-    LD.dz = DR::seed(L.dz, 2);
-    LD.psi = DR(L.psi);
-    LD.psi.d[2] = -R(P.k);  // psi = C - k (z - z_f)
-    LD.eta = DR(L.eta);
-    LD.eta.d[2] = -P.inv_vg;  // eta = T - (z - z_f) / v_g
-    LD.T = DR(L.T);
-    LD.phi_hi = DR(R(0));
-    LD.phi_lo = DR(R(0));
-    DR Ed[3], Bd[3];
-    fields_ad<KIND, R, NT>(A, LD, Ed, Bd);
-    const DR *Fd[6] = {&Ed[0], &Ed[1], &Ed[2], &Bd[0], &Bd[1], &Bd[2]};
-    for (int c = 0; c < 6; ++c) {
-      const DR &f = *Fd[c];
-      F[c] = a0 * f.v;
-      dFx[c][0] = a0 * f.d[0];
-      dFx[c][1] = a0 * f.d[1];
-      dFx[c][2] = a0 * f.d[2];
-      dFth[c][0] = f.v;
-      dFth[c][1] = a0 * f.d[3];
-      dFth[c][2] = -a0 * f.d[2];
-      if constexpr (NT == 5) dFth[c][3] = a0 * f.d[4];
-      else dFth[c][3] = R(0);
-    }
-  }
-  if constexpr (GRID) {
-    GridGrad<R> gg;
-    grid_value_grad<R>(aa.base.grid, gc, L.x, L.y, pos.zr(), gg);
-    for (int c = 0; c < 6; ++c) {
-      F[c] += gg.v[c];
-      for (int k = 0; k < 3; ++k) dFx[c][k] += gg.g[c][k];
-    }
-  }
   const R E[3] = {F[0], F[1], F[2]}, B[3] = {F[3], F[4], F[5]};
   // Boris forward intermediates
   R am[3] = {fma(h, E[0], u[0]), fma(h, E[1], u[1]), fma(h, E[2], u[2])};
@@ -408,7 +251,7 @@ __device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P,
   R v[3] = {un[0] * ign, un[1] * ign, un[2] * ign};
   // position update: x'_k = x_k + dt_k u'_k / gamma', dt_k = (dt_xy, dt_xy, dt)
   // (dt_xy = 0 for a 1D-3V set): d x'_k / d u'_j = dt_k ign (delta_kj - v_k v_j)
-  const R dtk[3] = {dt * P.adv_xy, dt * P.adv_xy, dt};
+  const R dtk[3] = {dt * adv_xy, dt * adv_xy, dt};
   R vl = dtk[0] * v[0] * lx[0] + dtk[1] * v[1] * lx[1] + dtk[2] * v[2] * lx[2];
   R ub[3];
   for (int k = 0; k < 3; ++k) ub[k] = lu[k] + ign * (dtk[k] * lx[k] - v[k] * vl);
@@ -442,11 +285,219 @@ __device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P,
     Eb[k] += h * ab[k];
     lu[k] = ab[k];
   }
-  // fields: position and parameter adjoints
-  const R Fb[6] = {Eb[0], Eb[1], Eb[2], Bb[0], Bb[1], Bb[2]};
-  for (int c = 0; c < 6; ++c) {
-    for (int k = 0; k < 3; ++k) lx[k] += Fb[c] * dFx[c][k];
-    for (int k = 0; k < kNp; ++k) g[k] += Fb[c] * dFth[c][k];
+  for (int k = 0; k < 3; ++k) {
+    Fb[k] = Eb[k];
+    Fb[k + 3] = Bb[k];
+  }
+}
+
+// The grid's share of a reverse step: its interpolated fields join the
+// analytic ones before the Boris reverse, and its gradient joins the
+// position adjoint after it.
+struct NoGridPart {
+  template <typename R>
+  __device__ __forceinline__ void add(R *) const {}
+  template <typename R>
+  __device__ __forceinline__ void contract(const R *, R *) const {}
+};
+template <typename R>
+struct GridPart {
+  GridGrad<R> gg;
+  __device__ __forceinline__ void add(R F[6]) const {
+    for (int c = 0; c < 6; ++c) F[c] += gg.v[c];
+  }
+  __device__ __forceinline__ void contract(const R Fb[6], R lx[3]) const {
+    for (int c = 0; c < 6; ++c)
+      for (int k = 0; k < 3; ++k) lx[k] += Fb[c] * gg.g[c][k];
+  }
+};
+
+// One reverse step of the Gaussian beam (MOVING: the closed-form flying
+// focus), with the field derivatives in the directions j = (x, y, z - z_f,
+// w0[, beta_f]) in closed form rather than by dual numbers, each contracted
+// with the field cotangent Fb as soon as it is formed (no Jacobian is kept).
+// The value part is the arithmetic of gauss_z and gauss_xy.  With G the
+// amplitude times the envelope and a = r^2/w0^2, the profile is
+// U0 = G e^{i psi} exp(-a q), U = q U0 and W = q U (the longitudinal terms'
+// factor), and dq/dzeta = i q^2; so every derivative is a complex factor
+// times U or W:
+//   dU/dj = U alpha_j,  alpha_j = i q (1 - a q) zeta_j - a_j q + L1 eta_j + i psi_j,
+//   dW/dj = W beta_j,   beta_j = alpha_j + i q zeta_j,
+// L1 = Gamma'/Gamma, where zeta_j, a_j, eta_j, psi_j are the derivatives of
+// zeta, a, eta = T - (z - z_f)/v_g and psi = C - k (z - z_f).  The fields
+// are linear in U and W (finish_beam), with the longitudinal terms also
+// linear in x, y and g = -2/w0^2, whose derivatives add those terms at unit
+// x, at unit y, and times g'/g = -2/w0.  Order: the value and the factors
+// the derivatives share, the Boris reverse for Fb, then Fb . dF/dj per
+// direction.  F = a0 f with f the unit-a0 fields: dF/da0 = f, d/dz_f =
+// -d/d(z - z_f).
+template <int POL, bool LON, bool MOVING, class PT, typename R, class GP>
+__device__ __forceinline__ void beam_reverse_t(const PT &P, const Local<R> &L, R a0, const R u[3],
+                                               R dt, R adv_xy, R lx[3], R lu[3], R gr[kNp],
+                                               const GP &grid) {
+  constexpr int NT = MOVING ? 5 : 4;
+  R mul, l2;
+  envelope(P, L.eta, mul, l2);
+  R zeta;
+  if constexpr (MOVING) zeta = fma(-P.beta_f, L.T, L.dz) * P.inv_zR;
+  else zeta = L.dz * P.inv_zR;
+  const R inv = rcp_r(fma(zeta, zeta, R(1)));
+  const Cx<R> q{inv, zeta * inv};
+  const R x = L.x, y = L.y;
+  const R a = (x * x + y * y) * P.inv_w0sq;
+  const R mag = (P.amp_unit * mul) * exp2_r(fma(a * q.re, R(-kLog2e), l2));
+  const R ang = reduce_angle<R>(L.psi - a * q.im);
+  R sn, cs;
+  sincos_r(ang, &sn, &cs);
+  const Cx<R> U = cmul(q, Cx<R>{mag * cs, mag * sn});
+  const Cx<R> W = cmul(q, U);
+  const R g = R(-2) * P.inv_w0sq;
+  R f[6], F[6], Fb[6];
+  {
+    R E[3], B[3];
+    finish_beam_pol<POL>(P, x, y, U, W, g, LON, E, B);
+    for (int c = 0; c < 3; ++c) {
+      f[c] = E[c];
+      f[c + 3] = B[c];
+    }
+  }
+  for (int c = 0; c < 6; ++c) F[c] = a0 * f[c];
+  grid.add(F);
+  boris_cotangent<R>(F, u, dt, adv_xy, lx, lu, Fb);
+  grid.contract(Fb, lx);
+  R sa0 = Fb[0] * f[0];
+  for (int c = 1; c < 6; ++c) sa0 = fma(Fb[c], f[c], sa0);
+  // shared factors: i q and i q (1 - a q)
+  const Cx<R> iq{-q.im, q.re};
+  const Cx<R> Q1 = cmul(iq, Cx<R>{R(1) - a * q.re, -a * q.im});
+  const R L1 = envelope_dlog(P, L.eta, mul);
+  const R w2 = R(2) * P.inv_w0sq, m2w = R(-2) * P.inv_w0;
+  R zj[NT], aj[NT], ej[NT], pj[NT], sj[NT];
+  zj[0] = R(0); aj[0] = w2 * x; ej[0] = R(0); pj[0] = R(0);
+  zj[1] = R(0); aj[1] = w2 * y; ej[1] = R(0); pj[1] = R(0);
+  zj[2] = P.inv_zR; aj[2] = R(0); ej[2] = -P.inv_vg * L1; pj[2] = -R(P.k);
+  zj[3] = m2w * zeta; aj[3] = m2w * a; ej[3] = R(0); pj[3] = R(0);
+  if constexpr (NT == 5) {
+    zj[4] = fma(-L.T, P.inv_zR, zeta * P.inv_1mb);
+    aj[4] = R(0); ej[4] = R(0); pj[4] = R(0);
+  }
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const Cx<R> al{zj[j] * Q1.re - aj[j] * q.re + ej[j], zj[j] * Q1.im - aj[j] * q.im + pj[j]};
+    const Cx<R> be{al.re + zj[j] * iq.re, al.im + zj[j] * iq.im};
+    R Ej[3], Bj[3];
+    finish_beam_pol<POL>(P, x, y, cmul(U, al), cmul(W, be), g, LON, Ej, Bj);
+    R t = Fb[0] * Ej[0];
+    t = fma(Fb[1], Ej[1], t);
+    t = fma(Fb[2], Ej[2], t);
+    t = fma(Fb[3], Bj[0], t);
+    t = fma(Fb[4], Bj[1], t);
+    sj[j] = fma(Fb[5], Bj[2], t);
+  }
+  if constexpr (LON) {
+    // the longitudinal terms' own x, y and g factors (components E_z, B_z)
+    const Cx<R> zero{R(0), R(0)};
+    R Ex[3], Bx[3], Ey[3], By[3], Eg[3], Bg[3];
+    finish_beam_pol<POL>(P, R(1), R(0), zero, W, g, true, Ex, Bx);
+    finish_beam_pol<POL>(P, R(0), R(1), zero, W, g, true, Ey, By);
+    finish_beam_pol<POL>(P, x, y, zero, W, g, true, Eg, Bg);
+    sj[0] = fma(Fb[2], Ex[2], fma(Fb[5], Bx[2], sj[0]));
+    sj[1] = fma(Fb[2], Ey[2], fma(Fb[5], By[2], sj[1]));
+    sj[3] = fma(m2w, fma(Fb[2], Eg[2], Fb[5] * Bg[2]), sj[3]);
+  }
+  lx[0] = fma(a0, sj[0], lx[0]);
+  lx[1] = fma(a0, sj[1], lx[1]);
+  lx[2] = fma(a0, sj[2], lx[2]);
+  gr[0] += sa0;
+  gr[1] = fma(a0, sj[3], gr[1]);
+  gr[2] = fma(-a0, sj[2], gr[2]);
+  if constexpr (NT == 5) gr[3] = fma(a0, sj[4], gr[3]);
+}
+
+// beam_reverse_t with the polarisation and the longitudinal switch (uniform
+// over a set) selected once rather than in each of its field assemblies.
+template <bool MOVING, class PT, typename R, class GP>
+__device__ __forceinline__ void beam_reverse(const PT &P, const Local<R> &L, R a0, const R u[3], R dt,
+                                             R adv_xy, R lx[3], R lu[3], R gr[kNp], const GP &grid) {
+  const bool lon = P.lon != 0;
+#define APT_BEAM_REV(POLV)                                                                    \
+  if (lon) beam_reverse_t<POLV, true, MOVING>(P, L, a0, u, dt, adv_xy, lx, lu, gr, grid);   \
+  else beam_reverse_t<POLV, false, MOVING>(P, L, a0, u, dt, adv_xy, lx, lu, gr, grid)
+  switch (P.pol) {
+    case AP_LIN_X: APT_BEAM_REV(AP_LIN_X); break;
+    case AP_LIN_Y: APT_BEAM_REV(AP_LIN_Y); break;
+    case AP_CIRC_P: APT_BEAM_REV(AP_CIRC_P); break;
+    default: APT_BEAM_REV(AP_CIRC_M); break;
+  }
+#undef APT_BEAM_REV
+}
+
+// One reverse step.  State before the step (pos, u), step value st, adjoints
+// lx, lu of the state after the step (updated in place to the state before),
+// gradient accumulators g[0..3] = d/d(a0, w0, z_f, beta_f).
+template <int KIND, int PREC, bool GRID>
+__device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P,
+                                             const PulseAD<Real<PREC>, tangents<KIND>()> &A,
+                                             const AdjArgs &aa, const typename TimeBase<PREC>::Step &st,
+                                             const Pos<PREC> &pos, const Real<PREC> u[3],
+                                             Real<PREC> lx[3], Real<PREC> lu[3], Real<PREC> g[kNp],
+                                             GridCache<Real<PREC>> &gc) {
+  using R = Real<PREC>;
+  constexpr int NT = tangents<KIND>();
+  using DR = Dual<R, NT>;
+  const R dt = (R)aa.base.dt;
+  const R a0 = P.a0;
+  const R adv = P.adv_xy;
+  // fields with derivatives in (x, y, z - z_f, w0, beta_f)
+  const Local<R> L = local_coords<PREC>(P, st, pos);
+  auto run = [&](const auto &grid) {
+    if constexpr (KIND == AP_GAUSS || KIND == AP_FLYING_CF) {
+      beam_reverse<KIND == AP_FLYING_CF>(P, L, a0, u, dt, adv, lx, lu, g, grid);
+    } else {
+      // the other kinds: dual numbers through the generic field functions
+      R F[6], dFx[6][3], dFth[6][kNp];  // field, d/dx, d/d(a0, w0, z_f, beta_f)
+      Local<DR> LD;
+      LD.x = DR::seed(L.x, 0);
+      LD.y = DR::seed(L.y, 1);
+      LD.dz = DR::seed(L.dz, 2);
+      LD.psi = DR(L.psi);
+      LD.psi.d[2] = -R(P.k);  // psi = C - k (z - z_f)
+      LD.eta = DR(L.eta);
+      LD.eta.d[2] = -P.inv_vg;  // eta = T - (z - z_f) / v_g
+      LD.T = DR(L.T);
+      LD.phi_hi = DR(R(0));
+      LD.phi_lo = DR(R(0));
+      DR Ed[3], Bd[3];
+      fields_ad<KIND, R, NT>(A, LD, Ed, Bd);
+      const DR *Fd[6] = {&Ed[0], &Ed[1], &Ed[2], &Bd[0], &Bd[1], &Bd[2]};
+      for (int c = 0; c < 6; ++c) {
+        const DR &f = *Fd[c];
+        F[c] = a0 * f.v;
+        dFx[c][0] = a0 * f.d[0];
+        dFx[c][1] = a0 * f.d[1];
+        dFx[c][2] = a0 * f.d[2];
+        dFth[c][0] = f.v;
+        dFth[c][1] = a0 * f.d[3];
+        dFth[c][2] = -a0 * f.d[2];
+        if constexpr (NT == 5) dFth[c][3] = a0 * f.d[4];
+        else dFth[c][3] = R(0);
+      }
+      grid.add(F);
+      R Fb[6];
+      boris_cotangent<R>(F, u, dt, adv, lx, lu, Fb);
+      grid.contract(Fb, lx);
+      for (int c = 0; c < 6; ++c) {
+        for (int k = 0; k < 3; ++k) lx[k] += Fb[c] * dFx[c][k];
+        for (int k = 0; k < kNp; ++k) g[k] += Fb[c] * dFth[c][k];
+      }
+    }
+  };
+  if constexpr (GRID) {
+    GridPart<R> gp;
+    grid_value_grad<R>(aa.base.grid, gc, L.x, L.y, pos.zr(), gp.gg);
+    run(gp);
+  } else {
+    run(NoGridPart{});
   }
 }
 
@@ -622,6 +673,220 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const Pulse<Real<PRE
   }
 }
 
+// ------------------------------------------------- two particles per thread
+// The float-float adjoint of the Gaussian kinds without a grid, with each
+// thread carrying two particles in the two halves of packed (f32x2) values,
+// as the two-particle push does: the forward sweep, the recomputation, the
+// closed-form field Jacobian and the Boris reverse all run on pairs.  Tiles
+// hold 2 kAdjBlock particles of one set (thread t: t and t + kAdjBlock).
+// Checkpoints and the tape keep the layout of the one-particle kernel with
+// the two particles of a thread side by side: [..][W][thread slots] float2,
+// the same bytes for half as many thread slots.
+constexpr int kAdjPairBlocksPerSm = 3;  // 156-162 registers, no spills
+
+struct PairIO {
+  static constexpr int W = 9;
+  __device__ static void put(float2 *b, size_t s, const Pos2 &p, const F2 u[3]) {
+    b[0 * s] = make_float2(p.x.hi.x, p.x.hi.y); b[1 * s] = make_float2(p.x.lo.x, p.x.lo.y);
+    b[2 * s] = make_float2(p.y.hi.x, p.y.hi.y); b[3 * s] = make_float2(p.y.lo.x, p.y.lo.y);
+    b[4 * s] = make_float2(p.dz.hi.x, p.dz.hi.y); b[5 * s] = make_float2(p.dz.lo.x, p.dz.lo.y);
+    b[6 * s] = make_float2(u[0].x, u[0].y); b[7 * s] = make_float2(u[1].x, u[1].y);
+    b[8 * s] = make_float2(u[2].x, u[2].y);
+  }
+  __device__ static void get(const float2 *b, size_t s, Pos2 &p, F2 u[3]) {
+    float2 v;
+    v = b[0 * s]; p.x.hi = F2(v.x, v.y); v = b[1 * s]; p.x.lo = F2(v.x, v.y);
+    v = b[2 * s]; p.y.hi = F2(v.x, v.y); v = b[3 * s]; p.y.lo = F2(v.x, v.y);
+    v = b[4 * s]; p.dz.hi = F2(v.x, v.y); v = b[5 * s]; p.dz.lo = F2(v.x, v.y);
+    v = b[6 * s]; u[0] = F2(v.x, v.y); v = b[7 * s]; u[1] = F2(v.x, v.y);
+    v = b[8 * s]; u[2] = F2(v.x, v.y);
+  }
+};
+
+// reverse_step for a thread's two particles (Gaussian kinds, no grid)
+template <int KIND>
+__device__ __forceinline__ void reverse_step_pair(const Pulse<float> &P, float dt, const StepFF &st,
+                                                  const Pos2 &pos, const F2 u[3], F2 lx[3], F2 lu[3],
+                                                  F2 g[kNp]) {
+  const Local<F2> L = local_coords2(P, st, pos);
+  beam_reverse<KIND == AP_FLYING_CF>(P, L, F2(P.a0), u, F2(dt), F2(P.adv_xy), lx, lu, g, NoGridPart{});
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kAdjBlock, kAdjPairBlocksPerSm)
+    adjoint_kernel_pair(const Pulse<float> *__restrict__ sets, const __grid_constant__ AdjArgs aa) {
+  static_assert(KIND == AP_GAUSS || KIND == AP_FLYING_CF, "closed-form Jacobian kinds");
+  __shared__ long long s_tile;
+  __shared__ int s_set;
+  __shared__ double s_red[32];
+  __shared__ StepFF s_steps[kAdjMaxK];
+  __shared__ __align__(16) unsigned char s_pulse_raw[sizeof(Pulse<float>)];
+  __shared__ long long s_prefix[AP_MAX_SETS + 1];
+  // dynamic: the next reverse step's tape entry, [2][W][kAdjBlock] float2
+  extern __shared__ __align__(16) unsigned char s_adj_dyn[];
+  float2 *s_next = reinterpret_cast<float2 *>(s_adj_dyn);
+  Pulse<float> &P = *reinterpret_cast<Pulse<float> *>(s_pulse_raw);
+  const PushArgs &a = aa.base;
+  constexpr int kPer = 2 * kAdjBlock;  // particles per tile
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    for (int s = 0; s < aa.n_sets; ++s) {
+      s_prefix[s] = acc;
+      long long ns = aa.set_offsets ? aa.set_offsets[s + 1] - aa.set_offsets[s] : a.n;
+      if (ns < 0) ns = 0;
+      acc += (ns + kPer - 1) / kPer;
+    }
+    s_prefix[aa.n_sets] = acc;
+    s_set = -1;
+  }
+  __syncthreads();
+  const long long total = s_prefix[aa.n_sets];
+  const size_t slot = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)(aa.nslots / 2);  // thread slots
+  float2 *ck = static_cast<float2 *>(aa.ckpt) + slot;
+  float2 *tp = static_cast<float2 *>(aa.tape) + slot;
+  const float *uxs = static_cast<const float *>(a.ux);
+  const float *uys = static_cast<const float *>(a.uy);
+  const float *uzs = static_cast<const float *>(a.uz);
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(aa.tile_counter, 1u);
+    __syncthreads();
+    const long long tile = s_tile;
+    if (tile >= total) break;
+    int lo = 0, hi = aa.n_sets;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (s_prefix[mid] <= tile) lo = mid; else hi = mid;
+    }
+    const int set = lo;
+    if (set != s_set) {
+      const int words = (int)(sizeof(Pulse<float>) / 4);
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(sets + set);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(s_pulse_raw);
+      for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+      __syncthreads();
+      if (threadIdx.x == 0) s_set = set;
+    }
+    __syncthreads();
+    const long long off0 = aa.set_offsets ? aa.set_offsets[set] : 0;
+    const long long off1 = aa.set_offsets ? aa.set_offsets[set + 1] : a.n;
+    const long long i0 = off0 + (tile - s_prefix[set]) * kPer + threadIdx.x;
+    const long long i1 = i0 + kAdjBlock;
+    const bool v0 = i0 >= 0 && i0 < off1 && i0 < a.n;
+    const bool v1 = i1 >= 0 && i1 < off1 && i1 < a.n;
+    const double Ns = (double)(off1 - off0);
+    // ---- forward pass with checkpoints
+    double X[2] = {0.0, 0.0}, Y[2] = {0.0, 0.0}, Z[2] = {0.0, 0.0};
+    float ua[3] = {0.0f, 0.0f, 0.0f}, ub[3] = {0.0f, 0.0f, 0.0f};
+    if (v0) {
+      X[0] = a.x[i0]; Y[0] = a.y[i0]; Z[0] = a.z[i0];
+      ua[0] = uxs[i0]; ua[1] = uys[i0]; ua[2] = uzs[i0];
+    }
+    if (v1) {
+      X[1] = a.x[i1]; Y[1] = a.y[i1]; Z[1] = a.z[i1];
+      ub[0] = uxs[i1]; ub[1] = uys[i1]; ub[2] = uzs[i1];
+    }
+    Pos2 pos;
+    pos.load(X, Y, Z, P.z_f);
+    F2 u[3] = {F2(ua[0], ub[0]), F2(ua[1], ub[1]), F2(ua[2], ub[2])};
+    TimeBase<AP_FP32_PHASEFF> tb;
+    tb.init(P, a.t0, a.dt);
+    const float dts = (float)a.dt;
+    const F2 dtR = dts, dtxy = dts * P.adv_xy;
+    for (int seg = 0; seg < aa.n_seg; ++seg) {
+      const long long s0 = (long long)seg * aa.K;
+      const int cnt = (int)(a.n_steps - s0 < aa.K ? a.n_steps - s0 : aa.K);
+      PairIO::put(ck + (size_t)seg * PairIO::W * stride, stride, pos, u);
+      __syncthreads();
+      for (int k = threadIdx.x; k < cnt; k += blockDim.x) s_steps[k] = tb.at(s0 + k);
+      __syncthreads();
+      for (int k = 0; k < cnt; ++k) {
+        const Local<F2> L = local_coords2(P, s_steps[k], pos);
+        F2 E[3], B[3];
+        analytic_fields<KIND, AP_FP32_PHASEFF, F2>(P, L, E, B);
+        const F2 ig = boris(u, E, B, dtR);
+        pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtxy, dtR);
+      }
+    }
+    // ---- objective and seed, per particle
+    const float uf[2][3] = {{u[0].x, u[1].x, u[2].x}, {u[0].y, u[1].y, u[2].y}};
+    double gN[2], Jv = 0.0;
+    float sd[2][3];
+    for (int h = 0; h < 2; ++h) {
+      const bool vh = h ? v1 : v0;
+      gN[h] = sqrt(1.0 + (double)uf[h][0] * uf[h][0] + (double)uf[h][1] * uf[h][1] +
+                   (double)uf[h][2] * uf[h][2]);
+      for (int k = 0; k < 3; ++k) sd[h][k] = vh ? (float)((double)uf[h][k] / (gN[h] * Ns)) : 0.0f;
+      if (vh) Jv += gN[h] / Ns;
+    }
+    F2 lx[3] = {F2(0.0f), F2(0.0f), F2(0.0f)};
+    F2 lu[3] = {F2(sd[0][0], sd[1][0]), F2(sd[0][1], sd[1][1]), F2(sd[0][2], sd[1][2])};
+    double gacc[kNp] = {0.0, 0.0, 0.0, 0.0};
+    // ---- reverse sweep over segments
+    for (int seg = aa.n_seg - 1; seg >= 0; --seg) {
+      const long long s0 = (long long)seg * aa.K;
+      const int cnt = (int)(a.n_steps - s0 < aa.K ? a.n_steps - s0 : aa.K);
+      PairIO::get(ck + (size_t)seg * PairIO::W * stride, stride, pos, u);
+      __syncthreads();
+      for (int k = threadIdx.x; k < cnt; k += blockDim.x) s_steps[k] = tb.at(s0 + k);
+      __syncthreads();
+      for (int k = 0; k < cnt; ++k) {
+        PairIO::put(tp + (size_t)k * PairIO::W * stride, stride, pos, u);
+        const Local<F2> L = local_coords2(P, s_steps[k], pos);
+        F2 E[3], B[3];
+        analytic_fields<KIND, AP_FP32_PHASEFF, F2>(P, L, E, B);
+        const F2 ig = boris(u, E, B, dtR);
+        pos.advance(u[0] * ig, u[1] * ig, u[2] * ig, dtxy, dtR);
+      }
+      // the tape entries this thread just stored are read back by its own
+      // asynchronous copies
+      __threadfence_block();
+      auto stage = [&](int k) {
+        const float2 *src = tp + (size_t)k * PairIO::W * stride;
+#pragma unroll
+        for (int w = 0; w < PairIO::W; ++w)
+          cp_async8((unsigned)__cvta_generic_to_shared(s_next + ((k & 1) * PairIO::W + w) * kAdjBlock +
+                                                       threadIdx.x),
+                    src + (size_t)w * stride);
+      };
+      F2 gs[kNp] = {F2(0.0f), F2(0.0f), F2(0.0f), F2(0.0f)};
+      stage(cnt - 1);
+      for (int k = cnt - 1; k >= 0; --k) {
+        cp_async_wait_all();
+        PairIO::get(s_next + (k & 1) * PairIO::W * kAdjBlock + threadIdx.x, kAdjBlock, pos, u);
+        if (k > 0) stage(k - 1);
+        reverse_step_pair<KIND>(P, dts, s_steps[k], pos, u, lx, lu, gs);
+      }
+      for (int k = 0; k < kNp; ++k)
+        gacc[k] += (v0 ? (double)gs[k].x : 0.0) + (v1 ? (double)gs[k].y : 0.0);
+    }
+    if ((v0 || v1) && !(isfinite(gacc[0]) && isfinite(gacc[1]) && isfinite(gacc[2]) && isfinite(gacc[3])))
+      atomicOr(a.status, kStatusNonfinite);
+    // per-set reduction (every particle of the tile belongs to `set`)
+    for (int k = 0; k < kNp; ++k) {
+      double t = block_sum(gacc[k], s_red);
+      if (threadIdx.x == 0) atomicAdd(aa.dJ + (size_t)set * AP_NPARAM + k, t);
+    }
+    if (aa.J) {
+      double t = block_sum(Jv, s_red);
+      if (threadIdx.x == 0) atomicAdd(aa.J + set, t);
+    }
+    __syncthreads();
+  }
+}
+
+template <int KIND>
+int launch_adjoint_pair(const Pulse<float> *sets, const AdjArgs &aa, void *stream) {
+  auto kern = adjoint_kernel_pair<KIND>;
+  const size_t dyn = 2 * (size_t)PairIO::W * kAdjBlock * sizeof(float2);
+  // static (about 40 KB) plus dynamic shared memory passes 48 KB: opt in
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+    return AP_ERR_CUDA;
+  const int grid = (int)(aa.nslots / (2 * kAdjBlock));
+  kern<<<grid, kAdjBlock, dyn, static_cast<cudaStream_t>(stream)>>>(sets, aa);
+  return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+}
+
 template <int KIND, int PREC, bool GRID>
 int launch_adjoint_t(const Pulse<Real<PREC>> *sets, const AdjArgs &aa, int grid, void *stream) {
   auto kern = adjoint_kernel<KIND, PREC, GRID>;
@@ -640,9 +905,12 @@ int launch_adjoint_k(int precision, const Pulse<double> *dpd, const Pulse<float>
   if (precision == AP_FP64)
     return gr ? launch_adjoint_t<KIND, AP_FP64, true>(dpd, aa, grid, stream)
               : launch_adjoint_t<KIND, AP_FP64, false>(dpd, aa, grid, stream);
-  if (precision == AP_FP32_PHASEFF)
+  if (precision == AP_FP32_PHASEFF) {
+    if constexpr (KIND == AP_GAUSS || KIND == AP_FLYING_CF)
+      if (!gr) return launch_adjoint_pair<KIND>(dpf, aa, stream);
     return gr ? launch_adjoint_t<KIND, AP_FP32_PHASEFF, true>(dpf, aa, grid, stream)
               : launch_adjoint_t<KIND, AP_FP32_PHASEFF, false>(dpf, aa, grid, stream);
+  }
   return AP_ERR_UNSUPPORTED;
 }
 
@@ -658,8 +926,12 @@ int handle_push_args(ap_handle h, const ap_particles *p, const ap_grid *g, doubl
 }  // namespace apt
 
 namespace {
+// particle slots of the workspace: the larger of the one-particle kernel's
+// (kAdjBlocksPerSm blocks of kAdjBlock per SM) and the two-particle
+// kernel's (kAdjPairBlocksPerSm blocks of 2 kAdjBlock particles)
 long long adj_slots(int sm_count) {
-  return (long long)sm_count * apt::kAdjBlocksPerSm * apt::kAdjBlock;
+  const int a = apt::kAdjBlocksPerSm * apt::kAdjBlock, b = apt::kAdjPairBlocksPerSm * 2 * apt::kAdjBlock;
+  return (long long)sm_count * (a > b ? a : b);
 }
 }  // namespace
 
@@ -722,7 +994,7 @@ int ap_push_adjoint(ap_handle h, const ap_particles *p0, const ap_grid *g, doubl
   aa.nslots = slots;
   aa.dJ = dJ_dparams;
   aa.J = J_out;
-  const int grid = (int)(slots / apt::kAdjBlock);
+  const int grid = sm * apt::kAdjBlocksPerSm;  // the one-particle kernel's launch
   switch (uk) {
     case AP_PLANE: return apt::launch_adjoint_k<AP_PLANE>(precision, dpd, dpf, aa, grid, stream);
     case AP_GAUSS: return apt::launch_adjoint_k<AP_GAUSS>(precision, dpd, dpf, aa, grid, stream);
