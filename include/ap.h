@@ -384,9 +384,10 @@ int ap_batch_graph_create(ap_handle h, const ap_particles *p, const ap_grid *g, 
 int ap_graph_launch(ap_graph gr, void *stream);
 void ap_graph_destroy(ap_graph gr);
 
-/* Workspace for ap_push_adjoint: one checkpoint of the state (36 B per
- * particle) every ckpt_every steps plus the per-particle tape of the
- * recomputed segment.  Returns 0 for invalid arguments. */
+/* Workspace for ap_push_adjoint: one checkpoint of the state every
+ * ckpt_every steps plus the tape of the recomputed segment, each for every
+ * resident particle slot of the adjoint kernels (48 B per state, 768 slots
+ * per SM), independent of n.  Returns 0 for invalid arguments. */
 size_t ap_adjoint_workspace_bytes(ap_handle h, int64_t n, int64_t n_steps, int32_t ckpt_every);
 
 /* Discrete adjoint of the gather + push (row a13): gradient of the per-set
