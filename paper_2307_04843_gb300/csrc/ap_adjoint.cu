@@ -502,7 +502,11 @@ __device__ __forceinline__ void reverse_step(const Pulse<Real<PREC>> &P,
 }
 
 template <int KIND, int PREC, bool GRID>
-__global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const Pulse<Real<PREC>> *__restrict__ sets,
+// residency target: kAdjBlocksPerSm blocks for the float kernels without a
+// grid, two for the larger FP64 and grid ones (without a minimum the FP64
+// kernel was held at 128 registers and spilled)
+__global__ void __launch_bounds__(kAdjBlock, (PREC == AP_FP64 || GRID) ? 2 : kAdjBlocksPerSm)
+    adjoint_kernel(const Pulse<Real<PREC>> *__restrict__ sets,
                                                             const __grid_constant__ AdjArgs aa) {
   using R = Real<PREC>;
   using IO = StateIO<PREC>;
