@@ -64,15 +64,15 @@ U_KEYS = ("ux", "uy", "uz")
 K_DIRECTIONS = 16
 
 
-def perturbed(parts, seed, momenta=False):
-    """Initial positions (and momenta) perturbed by 1e-7 relative, with floors
+def perturbed(parts, seed, momenta=False, rel=1e-7):
+    """Initial positions (and momenta) perturbed by `rel` relative, with floors
     of one wavelength and of m c (xi uniform in [-1, 1], seeded)."""
     rng = np.random.default_rng(seed)
     out = dict(parts)
     for k in ("x", "y", "z") + (U_KEYS if momenta else ()):
         v = np.asarray(parts[k], dtype=np.float64)
         floor = L if k in ("x", "y", "z") else 1.0
-        out[k] = v + 1e-7 * np.maximum(np.abs(v), floor) * rng.uniform(-1.0, 1.0, v.size)
+        out[k] = v + rel * np.maximum(np.abs(v), floor) * rng.uniform(-1.0, 1.0, v.size)
     return out
 
 
