@@ -13,7 +13,7 @@
 //
 // with seed lu^N = u^N / (gamma^N N_s), lx^N = 0.  dF/dx and dF/dtheta are
 // the derivatives in (x, y, z - z_f, w0, beta_f): in closed form for the
-// Gaussian beam and the closed-form flying focus (beam_jacobian), and from
+// Gaussian beam and the closed-form flying focus (beam_reverse), and from
 // the field functions instantiated with forward-mode dual numbers for the
 // other kinds; a0 enters linearly (dF/da0 = F / a0) and z_f only through
 // z - z_f (dF/dz_f = -dF/dz for the analytic part).
@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(kAdjBlock, (PREC == AP_FP64 || GRID) ? 2 : kAd
 // The float-float adjoint of the Gaussian kinds without a grid, with each
 // thread carrying two particles in the two halves of packed (f32x2) values,
 // as the two-particle push does: the forward sweep, the recomputation, the
-// closed-form field Jacobian and the Boris reverse all run on pairs.  Tiles
+// closed-form field derivatives and the Boris reverse all run on pairs.  Tiles
 // hold 2 kAdjBlock particles of one set (thread t: t and t + kAdjBlock).
 // Checkpoints and the tape keep the layout of the one-particle kernel with
 // the two particles of a thread side by side: [..][W][thread slots] float2,
@@ -719,7 +719,7 @@ __device__ __forceinline__ void reverse_step_pair(const Pulse<float> &P, float d
 template <int KIND>
 __global__ void __launch_bounds__(kAdjBlock, kAdjPairBlocksPerSm)
     adjoint_kernel_pair(const Pulse<float> *__restrict__ sets, const __grid_constant__ AdjArgs aa) {
-  static_assert(KIND == AP_GAUSS || KIND == AP_FLYING_CF, "closed-form Jacobian kinds");
+  static_assert(KIND == AP_GAUSS || KIND == AP_FLYING_CF, "kinds with closed-form field derivatives");
   __shared__ long long s_tile;
   __shared__ int s_set;
   __shared__ double s_red[32];
