@@ -182,6 +182,32 @@ def test_adjoint_beam_polarisations_envelopes_vs_oracle_fd(kind, pol, env):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("n,n_steps,K", [(1, 1, 1), (3, 257, 256), (257, 7, 2), (300, 64, 64)])
+def test_adjoint_edge_sizes_vs_oracle_fd(n, n_steps, K):
+    """Edge sizes of the adjoint (the two-particle kernel takes tiles of 256
+    in FP32, the one-particle kernel tiles of 128 in FP64): a single electron
+    and step, the largest segment with a last segment of one step, a ragged
+    second tile with two-step segments, one whole segment."""
+    pulse = dict(kind="gauss", pol="cp", env="gauss", env_len=10.0, a0=8.0, w0=2.0 * L, z_focus=0.3,
+                 t_focus=0.0, longitudinal=True)
+    rng = np.random.default_rng(41 + n)
+    parts = dict(x=rng.uniform(-1, 1, n) * L, y=rng.uniform(-1, 1, n) * L, z=rng.uniform(-1, 1, n) * L,
+                 ux=rng.normal(0, 0.1, n), uy=rng.normal(0, 0.1, n), uz=rng.normal(0, 0.1, n))
+    off = np.array([0, n], dtype=np.int64)
+    t0, dt = -2.0, 0.02
+    g = oracle.grad_fd(pulse, parts, t0, dt, n_steps, names=NAMES, rel_h=1e-4, scale=dict(z_focus=L))
+    gmax = max(abs(g[k]) for k in NAMES)
+    for precision in ("fp64", "fp32"):
+        J, dJ = _run_adjoint([pulse], off, parts, t0, dt, n_steps, K, precision)
+        assert J[0] == pytest.approx(oracle.mean_gamma(pulse, parts, t0, dt, n_steps),
+                                     rel=1e-12 if precision == "fp64" else 1e-5)
+        tol = 1e-5 if precision == "fp64" else 1e-3
+        for k, name in enumerate(NAMES):
+            assert abs(dJ[0, k] - g[name]) <= tol * max(abs(g[name]), 1e-2 * gmax), \
+                (precision, n, n_steps, K, name, dJ[0, k], g[name])
+
+
+@pytest.mark.gpu
 def test_adjoint_one_d_lines_vs_oracle_fd():
     """1D-3V set (transverse position held): the position update and its
     reverse use dt only along z."""
