@@ -56,22 +56,6 @@ __device__ __forceinline__ NodeFF node_ff(const Pulse<float> &P, const LineArgs 
   return {kd.hi, kd.lo, __fadd_rn(dz.hi, dz.lo)};
 }
 
-__device__ __forceinline__ Local<float> node_local_ff(const Pulse<float> &P, const StepFF &st, float kd_hi,
-                                                      float kd_lo, float dz) {
-  Local<float> L;
-  const FF ps = two_sum(st.C, -kd_hi);
-  L.psi = reduce_ff(ps.hi, __fsub_rn(ps.lo, kd_lo));
-  L.x = 0.0f;
-  L.y = 0.0f;
-  L.dz = dz;
-  const float Tf = __fadd_rn(st.Th, st.Tl);
-  L.eta = fmaf(-dz, P.inv_vg, Tf);
-  L.T = Tf;
-  L.phi_hi = 0.0f;
-  L.phi_lo = 0.0f;
-  return L;
-}
-
 // E1 at t_n and J1 at t_n + dt/2 at two nodes of the float split line at once
 // (the halves of every packed value, ap_pair.cuh: one issue slot per FP32
 // operation for both nodes, the MUFU operations one per node), for a plane
@@ -203,12 +187,7 @@ __global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant_
     for (int k = t; k < nz; k += bd) {
       const T ek = e[k];
       T drive = ek;
-      R j1 = R(0);
-      if constexpr (kFF) {
-        float e1;
-        line_sources_ff(P, st_e, kdh[k], kdl[k], dzn[k], sdl, cdl, hdt, e1, j1);
-        drive = l_add(e1, ek);
-      } else if constexpr (APT) {
+      if constexpr (APT) {
         R E1[3], B1[3];
         const Local<R> L = node_local<PREC>(P, a, st_e, k);
         analytic_fields<AP_PLANE, PREC>(P, L, E1, B1);
@@ -218,9 +197,7 @@ __global__ void __launch_bounds__(kLineBlock) line_kernel(const __grid_constant_
       j[k] = jk;
       if (k >= 1) {
         T src = jk;
-        if constexpr (kFF) {
-          src = l_sub(jk, (T)j1);
-        } else if constexpr (APT) {
+        if constexpr (APT) {
           R J1[3];
           const Local<R> L = node_local<PREC>(P, a, st_j, k);
           current_plane(P, L, J1);
