@@ -208,6 +208,25 @@ def test_adjoint_edge_sizes_vs_oracle_fd(n, n_steps, K):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adjoint_single_set_without_offsets(precision):
+    """One set given without offsets (the whole array is the set) gives the
+    same objective and gradient, bit for bit, as the same set with offsets
+    [0, n]; the FP32 call takes the two-particle kernel, with an odd count so
+    the last thread carries one particle."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    from paper_2307_04843_gb300.autograd import adjoint
+    sets, off, parts = _sets_case(n_sets=1, per=250, seed=13)  # 255: at most two tiles (sum order)
+    t0, dt, n_steps, K = -8.0, 0.02, 230, 50
+    dev = _lib.to_device(parts, precision)
+    J0, d0 = adjoint(sets, dev, None, t0, dt, n_steps, ckpt_every=K, precision=precision)
+    J1, d1 = adjoint(sets, dev, torch.as_tensor(off).cuda(), t0, dt, n_steps, ckpt_every=K, precision=precision)
+    assert torch.equal(J0, J1) and torch.equal(d0, d1)
+    assert torch.all(d0[0, :3] != 0)
+
+
+@pytest.mark.gpu
 def test_adjoint_one_d_lines_vs_oracle_fd():
     """1D-3V set (transverse position held): the position update and its
     reverse use dt only along z."""
