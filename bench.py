@@ -520,6 +520,16 @@ def roofline_frac(idx, rate):
     return ALGO[idx]["fp32"] * rate / (SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6)
 
 
+def _auxiliary(fn, *args):
+    """An auxiliary measurement of the line (grid-node legs, the other
+    workloads): a failure there is recorded in its key instead of losing the
+    headline, which is already measured."""
+    try:
+        return fn(*args)
+    except Exception as exc:  # noqa: BLE001 - any failure is reported, none is hidden
+        return {"error": "%s: %s" % (type(exc).__name__, str(exc)[:300])}
+
+
 def other_workloads(args, stream):
     """Every other workload at its full configuration, autotuned, one timed
     call each (after one untimed call): rate, kernel milliseconds and the
@@ -719,14 +729,14 @@ def run_ours(args):
     # grid (six float arrays), and independent 1-D vacuum Yee lines
     grid_node = None
     if rank == 0 and not args.no_variants and args.workload == 2:
-        grid_node = grid_node_rates(wl, stream)
+        grid_node = _auxiliary(grid_node_rates, wl, stream)
     # every other workload at its full configuration
     others = None
     if rank == 0 and not args.no_variants and args.workload == 2:
         wl_h_status = wl.h.status()
         if wl_h_status != 0:
             raise RuntimeError("device status before the other workloads: %d" % wl_h_status)
-        others = other_workloads(args, stream)
+        others = _auxiliary(other_workloads, args, stream)
 
     # the adjoint of the batched workload: forward + reverse sweep
     adjoint = None
