@@ -105,8 +105,9 @@ def test_adjoint_vs_gpu_fp64_central_differences():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("kind", ["lg", "plane"])
-def test_adjoint_other_kinds_vs_oracle_fd(kind):
+def test_adjoint_other_kinds_vs_oracle_fd(kind, precision):
     if kind == "lg":
         pulse = dict(kind="lg", pol="cp", env="gauss", env_len=20.0, a0=4.0, w0=2.5 * L, lg_p=1, lg_l=2,
                      z_focus=3.0, t_focus=0.0, longitudinal=True)
@@ -118,12 +119,14 @@ def test_adjoint_other_kinds_vs_oracle_fd(kind):
                  ux=np.zeros(n), uy=np.zeros(n), uz=np.zeros(n))
     off = np.array([0, n], dtype=np.int64)
     t0, dt, n_steps, K = -5.0 if kind == "lg" else 0.0, 0.02, 350, 128
-    _, dJ = _run_adjoint([pulse], off, parts, t0, dt, n_steps, K, "fp64")
+    _, dJ = _run_adjoint([pulse], off, parts, t0, dt, n_steps, K, precision)
     names = NAMES if kind == "lg" else ("a0", "z_focus")
     g = oracle.grad_fd(pulse, parts, t0, dt, n_steps, names=names, rel_h=1e-4, scale=dict(z_focus=L))
+    gmax = max(abs(g[k]) for k in names)
     for name in names:
         k = NAMES.index(name)
-        assert abs(dJ[0, k] - g[name]) <= 1e-3 * max(abs(g[name]), 1e-8), (kind, name, dJ[0, k], g[name])
+        floor = 1e-8 if precision == "fp64" else 1e-2 * gmax
+        assert abs(dJ[0, k] - g[name]) <= 1e-3 * max(abs(g[name]), floor), (kind, precision, name, dJ[0, k], g[name])
 
 
 @pytest.mark.gpu
