@@ -248,7 +248,8 @@ def test_adjoint_one_d_lines_vs_oracle_fd():
 
 
 @pytest.mark.gpu
-def test_adjoint_with_linear_grid_field():
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adjoint_with_linear_grid_field(precision):
     """A grid holding linear fields (trilinear interpolation is then exact and
     smooth across cells) enters the trajectory and the position adjoint."""
     sets, off, parts = _sets_case(n_sets=1, per=20, seed=5)
@@ -263,9 +264,30 @@ def test_adjoint_with_linear_grid_field():
     import torch
     g_dev = (torch.as_tensor(grid).cuda(), lo, hi)
     t0, dt, n_steps, K = -8.0, 0.02, 300, 100
-    _, dJ = _run_adjoint(sets, off, parts, t0, dt, n_steps, K, "fp64", grid=g_dev)
+    _, dJ = _run_adjoint(sets, off, parts, t0, dt, n_steps, K, precision, grid=g_dev)
     ref = _oracle_grads(sets, off, parts, t0, dt, n_steps, grid=(grid, lo, hi))
     assert np.max(_rel(dJ[:, :3], ref)) <= 1e-3, (dJ[:, :3], ref)
+
+
+@pytest.mark.gpu
+def test_adjoint_packed_grid_same_as_arrays():
+    """A grid passed with its per-cell coefficient copy (the push's fast
+    layout) gives the adjoint exactly the result of the plain arrays: the
+    adjoint interpolates the raw corners either way."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    sets, off, parts = _sets_case(n_sets=2, per=40, seed=17)
+    nx, ny, nz = 12, 10, 14
+    lo, hi = (-25.0, -25.0, -60.0), (25.0, 25.0, 60.0)
+    rng = np.random.default_rng(3)
+    grid = (0.01 * rng.standard_normal((6, nz, ny, nx))).astype(np.float32)
+    g = torch.as_tensor(grid).cuda()
+    t0, dt, n_steps, K = -8.0, 0.02, 150, 50
+    _, d_arr = _run_adjoint(sets, off, parts, t0, dt, n_steps, K, "fp32", grid=(g, lo, hi))
+    packed = _lib.pack_grid((g, lo, hi), layout="cells")
+    _, d_pk = _run_adjoint(sets, off, parts, t0, dt, n_steps, K, "fp32", grid=packed)
+    assert np.array_equal(d_arr, d_pk)
+    assert np.all(d_arr[:, :3] != 0)
 
 
 @pytest.mark.gpu
