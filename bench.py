@@ -57,10 +57,12 @@ ALGO = {
     5: dict(fp32=125, mufu=7),
     6: dict(fp32=125, mufu=7),
 }
-# DRAM bytes per particle-step of the workload-2 kernel from the committed
-# ncu capture of the 1.6e6-particle x 4000-step case, scaled by particle-steps
-# (an upper bound at 1e7 particles: more particles share each cached cell);
-# None when the kernel changed after the capture.
+# FP32 operations per particle-step of the adjoint of workload 5 (Gaussian,
+# longitudinal terms, linear polarisation, no grid), from its formulas: the
+# forward sweep 125, the recomputation 125 and the reverse step 307 (local
+# coordinates and phase 34, envelope 2, field value 28, F = a0 f 4, the Boris
+# cotangent 123, the closed-form field derivatives contracted with it 116).
+ADJ_OPS = 557
 # DRAM bytes per particle-step of the workload-2 push kernel from the committed
 # ncu capture of the 1.6e6-particle x 4000-step case, scaled by particle-steps
 # (an upper bound at 1e7 particles: more particles share each cached cell);
@@ -570,7 +572,10 @@ def other_workloads(args, stream):
             b.record(stream)
             torch.cuda.synchronize()
             asec = a.elapsed_time(b) / 1e3
-            r["adjoint"] = {"value": wl.n * wl.n_steps / asec, "unit": UNIT, "seconds": asec,
+            arate = wl.n * wl.n_steps / asec
+            r["adjoint"] = {"value": arate, "unit": UNIT, "seconds": asec,
+                            "roofline_frac": ADJ_OPS * arate / (SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6),
+                            "algo_ops_per_particle_step": ADJ_OPS,
                             "vs_forward": asec / sec, "ckpt_every": wl.cfg["ckpt_every"]}
         res[str(idx)] = r
         wl.close()
@@ -752,6 +757,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         sec = a.elapsed_time(b) / 1e3
         adjoint = {"value": units_rank / sec, "unit": UNIT, "seconds": sec,
+                   "roofline_frac": ADJ_OPS * units_rank / sec / (SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6),
+                   "algo_ops_per_particle_step": ADJ_OPS,
                    "vs_forward": sec / kern, "ckpt_every": wl.cfg["ckpt_every"]}
 
     # CPU oracle baseline on rank 0 (bounded sample of the same workload)
