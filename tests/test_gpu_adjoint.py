@@ -230,6 +230,31 @@ def test_adjoint_single_set_without_offsets(precision):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adjoint_empty_sets(precision):
+    """Empty sets before, between and after populated ones: their objective
+    and gradient rows are zero, and a populated set's row equals that set run
+    alone, bit for bit."""
+    import torch
+    from paper_2307_04843_gb300 import _lib
+    from paper_2307_04843_gb300.autograd import adjoint
+    sets, _, parts = _sets_case(n_sets=2, per=20, seed=23)
+    n0 = 20
+    four = [sets[0], sets[0], sets[1], sets[1]]
+    off = np.array([0, 0, n0, n0, parts["x"].size], dtype=np.int64)  # sets 0 and 2 empty
+    t0, dt, n_steps, K = -8.0, 0.02, 120, 40
+    dev = _lib.to_device(parts, precision)
+    J, dJ = adjoint(four, dev, torch.as_tensor(off).cuda(), t0, dt, n_steps, ckpt_every=K, precision=precision)
+    J, dJ = J.cpu().numpy(), dJ.cpu().numpy()
+    assert J[0] == 0.0 and J[2] == 0.0 and np.all(dJ[0] == 0.0) and np.all(dJ[2] == 0.0)
+    for s, (lo, hi) in ((1, (0, n0)), (3, (n0, parts["x"].size))):
+        sub = {k: v[lo:hi] for k, v in parts.items()}
+        d1 = _lib.to_device(sub, precision)
+        J1, dJ1 = adjoint([four[s]], d1, None, t0, dt, n_steps, ckpt_every=K, precision=precision)
+        assert J[s] == float(J1[0]) and np.array_equal(dJ[s], dJ1[0].cpu().numpy()), s
+
+
+@pytest.mark.gpu
 def test_adjoint_one_d_lines_vs_oracle_fd():
     """1D-3V set (transverse position held): the position update and its
     reverse use dt only along z."""
